@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of offloaded silicon-pixel local reconstruction on GB300.
+
+One step = one pass of the whole reconstruction (decode, bucket, calibrate,
+threshold, 8-connected clustering, charge/centroid reduction, ordered output,
+labels) over one batch of the ``batched`` workload: 256 events of uneven size
+(digi counts uniform in 10k-200k, ~27M digis) on the 64-module 160 x 416
+geometry, seeded synthetic data.
+
+  value        events/s, device-resident inputs (CUDA-event timed on the
+               launching stream; inputs and working set exceed the 129 MB L2)
+  e2e          the same through the public enqueue API with pinned host
+               buffers: host-to-device copy of the inputs, the pass, and the
+               results back in host memory, every step
+  per_event    the plain per-event path on the ``full`` workload (one
+               1856-module event of ~60k digis per launch, one stream)
+  roofline     the dominant kernel's algorithmic bytes / its mean duration
+  cpu_baseline the CPU oracle timed on this host's cores (reported baseline)
+
+``--impl reference`` times the CPU oracle (the reference arm) instead.
+Under torchrun each rank runs an independent replica on its own GPU (events
+shard by rank, no collective on the data path); value sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_04334_gb300 import synth  # noqa: E402
+
+METRIC = "events/s & Mdigis/s at 1 GB300 (batched vs per-event, % HBM peak); p50/p99 latency"
+WORKLOAD = "batched"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--per-event-steps", type=int, default=200)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(n_digis, n_events, n_modules, n_clusters, labels=True):
+    """Bytes the method must move at least: inputs read once (word + module id),
+    calibration read once per event, labels and cluster records written once."""
+    return 6 * n_digis + 8 * n_modules * n_events + (4 * n_digis if labels else 0) + 24 * n_clusters
+
+
+# Per-kernel algorithmic bytes (intermediates such as buckets are not counted).
+def kernel_bytes(name, n_digis, n_events, n_modules, n_clusters):
+    if name == "hist_kernel":
+        return 2 * n_digis
+    if name == "scatter_kernel":
+        return 6 * n_digis
+    if name == "cc_kernel":
+        return 4 * n_digis + 24 * n_clusters + 8 * n_modules * n_events
+    if name == "fused_kernel":
+        return algorithmic_bytes(n_digis, n_events, n_modules, n_clusters)
+    return 0
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("hp_kernels.cu", "hp_internal.h"):
+        with open(os.path.join(ROOT, "paper_2004_04334_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, n_digis):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:  # noqa: BLE001
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != _kernel_source_hash():
+        return None
+    return int(e["dram_bytes_per_digi"] * n_digis)
+
+
+def cpu_oracle(w, events=None, threads=None):
+    """Time the CPU oracle over events of w (one oracle call per event, run on
+    `threads` host threads; the oracle releases the GIL)."""
+    from oracle import oracle
+
+    events = list(range(w.n_events)) if events is None else events
+    threads = threads or os.cpu_count() or 1
+
+    def one(e):
+        words, mods = w.event(e)
+        oracle.reconstruct_event(words, mods, w.n_modules, w.gain, w.pedestal)
+
+    oracle.build()
+    t0 = time.perf_counter()
+    if threads == 1:
+        for e in events:
+            one(e)
+    else:
+        with cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(one, events))
+    dt = time.perf_counter() - t0
+    nd = sum(int(w.offsets[e + 1] - w.offsets[e]) for e in events)
+    return len(events) / dt, nd / dt / 1e6, dt, threads
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    w = synth.workload(a.workload)
+    sample = list(range(min(32, w.n_events)))
+    for _ in range(a.warmup):
+        cpu_oracle(w, sample[:2])
+    vals = []
+    t_all = 0.0
+    for _ in range(a.steps):
+        ev_s, md_s, dt, cores = cpu_oracle(w, sample)
+        vals.append(ev_s)
+        t_all += dt
+    value = len(sample) * a.steps / t_all
+    nd = sum(int(w.offsets[e + 1] - w.offsets[e]) for e in sample)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t_all / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{a.workload} (first {len(sample)} of {w.n_events} events per step)",
+                       "events_per_step": len(sample), "digis_per_step": nd, "n_modules": w.n_modules},
+            "mdigis_per_s": nd * a.steps / t_all / 1e6,
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(sample)} events ({nd} digis) of the {a.workload} workload per step"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+
+    from paper_2004_04334_gb300 import build, hp
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    build.build()
+
+    # each rank reconstructs its own shard of events (a replica), seeded by rank
+    seed = None if world == 1 else synth.BASE_SEED + 3 + 1000 * rank
+    w = synth.workload(a.workload, seed=seed)
+    E, N, M = w.n_events, w.n_digis, w.n_modules
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        ev_s, md_s, dt, cores = cpu_oracle(w)
+        cpu = {"value": ev_s, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"all {E} events ({N} digis) of the {a.workload} workload, one pass, "
+                         f"{cores} threads (one oracle call per event)", "mdigis_per_s": md_s, "seconds": dt}
+
+    ctx = hp.Context(M, w.gain, w.pedestal, device=local, want_labels=True)
+    d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
+    d_mods = torch.from_numpy(w.modules.view(np.int16)).to(dev)
+    d_offs = torch.from_numpy(w.offsets.view(np.int64)).to(dev)
+    out = hp.DeviceOutputs(E, N, dev)
+    stream = torch.cuda.Stream(dev)
+
+    def step():
+        ctx.reconstruct_device(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
+                               stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, a.warmup)):
+            step()
+    torch.cuda.synchronize(dev)
+    n_clusters = int(out.cluster_offsets[-1].item())
+    assert int((out.event_status != 0).sum().item()) == 0, "device reported an error status"
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # device-resident timed region
+    launches0 = ctx.stats()["kernel_launches"]
+    ctx.profile_enable(a.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    t_dev = e0.elapsed_time(e1) / 1000.0
+    gpu_launches = ctx.stats()["kernel_launches"] - launches0
+    prof = ctx.profile_read()
+    ctx.profile_enable(0)
+    if world > 1:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = world * E * a.steps / t_dev
+    mdigis = world * N * a.steps / t_dev / 1e6
+
+    # dominant kernel roofline
+    name, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_s = ms / max(cnt, 1) / 1000.0
+    kb = kernel_bytes(name, N, E, M, n_clusters)
+    peak, peak_kind = _peaks()
+    achieved = kb / per_launch_s / 1e9
+    path_bytes = algorithmic_bytes(N, E, M, n_clusters)
+    shares = {k: round(v[1] / max(1e-12, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
+
+    # end to end through the public enqueue API: pinned host inputs, H2D, pass, results in host memory
+    pw = torch.from_numpy(w.words.view(np.int32)).pin_memory()
+    pm = torch.from_numpy(w.modules.view(np.int16)).pin_memory()
+    for _ in range(2):
+        ev = ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY)
+        ev.wait(120)
+        ev.release()
+    barrier()
+    t0 = time.perf_counter()
+    inflight = []
+    for _ in range(a.steps):
+        inflight.append(ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY))
+        if len(inflight) >= 2:
+            ev = inflight.pop(0)
+            ev.wait(120)
+            r = ev.fetch()
+            ev.release()
+    for ev in inflight:
+        ev.wait(120)
+        r = ev.fetch()
+        ev.release()
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    assert r.status == hp.HP_OK and r.n_clusters == n_clusters
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * E * a.steps / t_e2e, "unit": "events/s",
+           "h2d_bytes_per_step": 6 * N + 8 * (E + 1),
+           "d2h_bytes_per_step": 4 * N + 24 * n_clusters + 8 * (E + 1) + 4 * E,
+           "mdigis_per_s": world * N * a.steps / t_e2e / 1e6}
+
+    # plain per-event path: one full-size event per launch, one stream
+    pe = synth.workload("full")
+    pctx = hp.Context(pe.n_modules, pe.gain, pe.pedestal, device=local, want_labels=True)
+    pw1, pm1 = pe.event(0)
+    dw = torch.from_numpy(pw1.view(np.int32)).to(dev)
+    dm = torch.from_numpy(pm1.view(np.int16)).to(dev)
+    do = torch.from_numpy(pe.offsets.view(np.int64)).to(dev)
+    pout = hp.DeviceOutputs(1, len(pw1), dev)
+
+    def pstep():
+        pctx.reconstruct_device(1, len(pw1), do.data_ptr(), dw.data_ptr(), dm.data_ptr(), pout, stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(10):
+            pstep()
+    barrier()
+    e0.record(stream)
+    for _ in range(a.per_event_steps):
+        pstep()
+    e1.record(stream)
+    barrier()
+    t_pe = e0.elapsed_time(e1) / 1000.0
+    lat = []
+    for i in range(a.per_event_steps):
+        ev = pctx.enqueue_event(pw1, pm1)
+        ev.wait(60)
+        lat.append(ev.latency_ns / 1e6)
+        ev.release()
+    per_event = {"workload": f"full: 1 event, {pe.n_modules} modules, {len(pw1)} digis",
+                 "value": a.per_event_steps / t_pe, "unit": "events/s",
+                 "mdigis_per_s": a.per_event_steps * len(pw1) / t_pe / 1e6,
+                 "e2e_latency_ms_p50": float(np.percentile(lat, 50)),
+                 "e2e_latency_ms_p99": float(np.percentile(lat, 99))}
+    pctx.close()
+    ctx.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * t_dev / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {E} events of uneven size (10k-200k digis), {M} modules "
+                                   f"of 160x416, {N} digis, labels on",
+                       "events_per_step": E, "digis_per_step": N, "clusters_per_step": n_clusters,
+                       "l2": "inputs (6 B/digi) and working set larger than the 129 MB L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "mdigis_per_s": mdigis,
+            "path_algorithmic_GBps": path_bytes * a.steps / t_dev / 1e9,
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": _traffic(name, N), "algorithmic_bytes_per_launch": kb,
+                         "mean_launch_ms": per_launch_s * 1000, "kernel_shares": shares},
+            "e2e": e2e,
+            "per_event": per_event,
+            "batched_vs_per_event": value / per_event["value"],
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * libhp — offloaded silicon-pixel local reconstruction on one GB300 (sm_103a).
+ *
+ * C ABI of the library.  The calls map onto the External Worker pattern of
+ * "Bringing heterogeneity to the CMS software framework" (arXiv:2004.04334):
+ *
+ *   hp_enqueue_event / hp_enqueue_batch   the non-blocking acquire() (Sec. 2):
+ *        read the inputs, queue all device work on a stream and return
+ *        without waiting for the device;
+ *   hp_on_complete                        the holder that resumes the caller
+ *        (Sec. 2; Sec. 4.1: a callback queued into the stream, errors
+ *        delivered with it);
+ *   hp_fetch_clusters                     produce() (Sec. 2): collect the
+ *        result once the stream has signalled completion;
+ *   hp_event_* accessors                  the Product<T> wrapper of Sec. 4.2:
+ *        device id, stream and CUDA event of the work that made the result.
+ *
+ * The device work is the raw -> clusters step of the paper's Fig. 1: decode
+ * digi words, bucket them by module, calibrate q = adc * gain[m] - pedestal[m]
+ * and keep pixels with q >= pixel_thr, label 8-connected clusters of the kept
+ * pixels of each module, and reduce each cluster to its integer charge Q,
+ * pixel count and charge-weighted centroid; keep clusters with
+ * Q >= cluster_thr, ordered by (event, module, id) where id is the smallest
+ * linear pixel index row * cols + col of the cluster.
+ *
+ * Conventions
+ *   - Every call returns an hp_status.  HP_ECUDA means a CUDA runtime call
+ *     failed; the context is then unusable and every later call on it
+ *     returns HP_ECUDA.
+ *   - Threading: all calls may be made from any thread.  Callbacks run on a
+ *     CUDA host-function thread (or on the registering thread if the event is
+ *     already complete) and must not call CUDA; hp_fetch_clusters,
+ *     hp_event_query and hp_release_event make no CUDA call and are safe in a
+ *     callback.
+ *   - Digi word layout: bits 0-7 row, bits 8-16 column, bits 17-24 ADC,
+ *     bits 25-31 zero.  Module ids are uint16.
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hp_status {
+    HP_OK = 0,
+    HP_EAGAIN = 1,    /* over the device budget or the in-flight limit: retry after a completion */
+    HP_ENOTREADY = 2, /* the event has not completed yet */
+    HP_EINVAL = 3,    /* invalid argument or configuration */
+    HP_EBADDIGI = 4,  /* an event holds an invalid digi word or module id */
+    HP_EDUP = 5,      /* an event holds the same (module, row, col) twice */
+    HP_ECAPACITY = 6, /* an output did not fit the capacity the caller gave */
+    HP_ENOMEM = 7,    /* a device or pinned host allocation failed */
+    HP_ETIMEOUT = 8,  /* a bounded wait inside a kernel gave up (results invalid) */
+    HP_ECUDA = 9      /* a CUDA runtime call failed; the context is unusable */
+} hp_status;
+
+/* flags of hp_config.flags and of the enqueue calls */
+#define HP_WANT_LABELS 0x1u  /* compute and return one label per input digi */
+#define HP_INPUT_NOCOPY 0x2u /* enqueue: the input arrays are pinned host (or device)
+                                memory that stays valid until the event completes;
+                                they are read directly instead of being staged */
+
+/*
+ * Context configuration.  gain and pedestal are host arrays of n_modules
+ * entries, copied at hp_create.  Requirements (else HP_EINVAL):
+ * 1 <= n_modules <= 65536, 1 <= rows <= 256, 1 <= cols <= 512,
+ * rows * cols <= 131072, pixel_thr >= 1, and for every module gain >= 0 and
+ * 255 * gain - pedestal <= INT32_MAX / (rows * cols), so that every cluster
+ * charge fits in int32.
+ */
+typedef struct hp_config {
+    int device;                 /* CUDA device ordinal */
+    uint32_t n_modules;         /* modules per event (1856 for the full detector) */
+    uint32_t rows, cols;        /* module geometry (160 x 416) */
+    int32_t pixel_thr;          /* keep pixels with q >= pixel_thr (1000 e) */
+    int32_t cluster_thr;        /* keep clusters with Q >= cluster_thr (4000 e) */
+    const int32_t *gain;        /* [n_modules] e per ADC count */
+    const int32_t *pedestal;    /* [n_modules] e */
+    size_t device_budget_bytes; /* pooled device bytes that in-flight events may hold; 0 = no limit */
+    uint32_t max_inflight;      /* events (or batches) in flight; 0 = 256 */
+    uint32_t n_streams;         /* stream pool size; 0 = 4 */
+    uint32_t flags;             /* default flags for enqueue (HP_WANT_LABELS) */
+} hp_config;
+
+typedef struct hp_ctx hp_ctx;
+typedef struct hp_event hp_event;
+
+/* Completion callback: called exactly once per event with its final status. */
+typedef void (*hp_callback)(void *user, hp_event *ev, hp_status st);
+
+/*
+ * Host view of a completed event (library-owned pinned memory, valid until
+ * hp_release_event).  Clusters of event e are [cluster_offsets[e],
+ * cluster_offsets[e+1]).  An event whose event_status is not HP_OK has an
+ * unspecified cluster slice and labels; the others are exact.
+ */
+typedef struct hp_clusters {
+    uint32_t n_events;
+    uint64_t n_digis;
+    uint64_t n_clusters;
+    uint64_t tag;
+    const uint64_t *cluster_offsets; /* [n_events + 1] */
+    const int32_t *event_status;     /* [n_events] hp_status of each event */
+    const uint32_t *module;          /* [n_clusters] module index */
+    const int32_t *id;               /* smallest linear index row * cols + col */
+    const int32_t *charge;           /* Q = sum of q over the cluster (e) */
+    const int32_t *npix;             /* pixels in the cluster */
+    const float *x;                  /* charge-weighted mean row */
+    const float *y;                  /* charge-weighted mean column */
+    const int32_t *label;            /* [n_digis] cluster id, -1 (pixel below threshold),
+                                        -2 (cluster below threshold); NULL without HP_WANT_LABELS */
+} hp_clusters;
+
+/*
+ * Output arrays of hp_reconstruct_device, all device pointers owned by the
+ * caller.  capacity is the room in the six cluster arrays; a batch never
+ * has more clusters than digis, so capacity >= n_digis always suffices.
+ */
+typedef struct hp_device_clusters {
+    uint64_t capacity;
+    uint32_t *module;
+    int32_t *id, *charge, *npix;
+    float *x, *y;
+    uint64_t *cluster_offsets; /* [n_events + 1] */
+    int32_t *event_status;     /* [n_events] hp_status of each event */
+    int32_t *label;            /* [n_digis] or NULL (labels not computed) */
+} hp_device_clusters;
+
+/* Counters of the context (monotonic unless stated). */
+typedef struct hp_stats {
+    uint64_t device_mallocs;    /* cudaMalloc calls made by the caching pool */
+    uint64_t host_mallocs;      /* cudaHostAlloc calls made by the caching pool */
+    uint64_t pool_hits;         /* allocations served from the cache */
+    uint64_t device_bytes_in_use; /* current: bytes held by in-flight work */
+    uint64_t device_bytes_cached; /* current: bytes held by the pool in total */
+    uint64_t events_enqueued;
+    uint64_t events_completed;
+    uint64_t inflight;          /* current */
+    uint64_t h2d_bytes, d2h_bytes; /* bytes moved by cudaMemcpyAsync */
+    uint64_t kernel_launches;   /* kernels launched by the library */
+} hp_stats;
+
+const char *hp_status_string(hp_status st);
+
+/*
+ * Create a context on cfg->device: stream pool, caching allocator, device
+ * copies of the calibration tables.  *out receives the context.
+ * Errors: HP_EINVAL (see hp_config), HP_ENOMEM, HP_ECUDA.
+ */
+hp_status hp_create(const hp_config *cfg, hp_ctx **out);
+
+/*
+ * Drain every in-flight event (this blocks: teardown is outside event
+ * processing), then free all memory.  Events not yet released are released.
+ */
+hp_status hp_destroy(hp_ctx *ctx);
+
+/*
+ * acquire() for one event (Sec. 2): n_digis digis, words[i] with module id
+ * module_ids[i], in any order.  Unless HP_INPUT_NOCOPY is set the inputs are
+ * copied into pooled pinned staging before the call returns, so the caller
+ * may reuse them at once.  The call queues the host-to-device copy, the
+ * kernels, the device-to-host transfer and a completion callback on one
+ * stream of the pool and returns without waiting for the device.
+ * flags: HP_WANT_LABELS, HP_INPUT_NOCOPY (ORed with hp_config.flags).
+ * Errors: HP_EINVAL (NULL pointers with n_digis > 0, n_digis >= 2^32 - 1),
+ * HP_EAGAIN (budget or in-flight limit), HP_ENOMEM, HP_ECUDA.
+ */
+hp_status hp_enqueue_event(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_ids, uint64_t n_digis,
+                           uint64_t tag, uint32_t flags, hp_event **out);
+
+/*
+ * acquire() for a batch of n_events independent events concatenated in
+ * words/module_ids: event e owns digis [offsets[e], offsets[e+1]), offsets
+ * has n_events + 1 entries, offsets[0] == 0 and is non-decreasing.  The whole
+ * batch runs as one device pass; completion, callback and view are per
+ * batch, with per-event status and cluster offsets.
+ * Errors: as hp_enqueue_event, plus HP_EINVAL for bad offsets.
+ */
+hp_status hp_enqueue_batch(hp_ctx *ctx, uint32_t n_events, const uint64_t *offsets, const uint32_t *words,
+                           const uint16_t *module_ids, uint64_t tag, uint32_t flags, hp_event **out);
+
+/*
+ * Register the completion callback (the holder of Sec. 2 / Sec. 4.1).  It is
+ * called exactly once: on the CUDA host-function thread when the event
+ * completes, or right here on the calling thread if it already has.  At most
+ * one callback per event (else HP_EINVAL).
+ */
+hp_status hp_on_complete(hp_event *ev, hp_callback cb, void *user);
+
+/* Non-blocking: HP_ENOTREADY while running, else the event's final status. */
+hp_status hp_event_query(hp_event *ev);
+
+/*
+ * produce() (Sec. 2): fill *view with the event's results.  HP_ENOTREADY if
+ * the event has not completed; otherwise returns the event's status (the
+ * view is filled in every case once complete).  Makes no CUDA call.
+ */
+hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *view);
+
+/*
+ * Return the event's buffers to the pool.  Before completion the release is
+ * deferred until the event completes (after its callback).  The event
+ * pointer and its views are invalid afterwards.  Makes no CUDA call.
+ */
+hp_status hp_release_event(hp_event *ev);
+
+/* Product<T> metadata (Sec. 4.2): device ordinal, producing stream
+ * (cudaStream_t) and the CUDA event recorded after the work. */
+int hp_event_device(const hp_event *ev);
+void *hp_event_stream(const hp_event *ev);
+void *hp_event_cuda_event(const hp_event *ev);
+/* Host wall-clock nanoseconds from enqueue to completion (0 before). */
+uint64_t hp_event_latency_ns(const hp_event *ev);
+
+/*
+ * Device-resident entry: inputs are already in device memory and outputs go
+ * to caller-owned device memory; the work is queued on `stream` (a
+ * cudaStream_t, NULL for the legacy default stream) and the call returns
+ * without waiting.  d_words is 4-byte aligned, d_module_ids 2-byte aligned,
+ * d_offsets has n_events + 1 entries with offsets[n_events] == n_digis.
+ * Scratch comes from a per-stream workspace of the context; the first call on
+ * a stream, or a call that needs more scratch than earlier ones, allocates
+ * it (and synchronises that stream); later calls allocate nothing, so the
+ * call can be captured in a CUDA graph once warmed up.  Errors found on the
+ * device are reported per event in out->event_status.
+ * Errors: HP_EINVAL, HP_ENOMEM, HP_ECUDA.
+ */
+hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                                const uint32_t *d_words, const uint16_t *d_module_ids,
+                                const hp_device_clusters *out, void *stream);
+
+hp_status hp_get_stats(hp_ctx *ctx, hp_stats *out);
+
+/*
+ * Stage timers (tracing).  After hp_profile_enable(ctx, n), the next n
+ * launches of the context record a CUDA event before and after each of their
+ * kernels on the launching stream (asynchronous, no host wait); n = 0 stops
+ * and clears.  hp_profile_read waits for the recorded events (a blocking
+ * call: use it outside event processing) and returns, per kernel name, the
+ * number of timed launches and their summed device time in milliseconds.
+ * names[i] are static strings.  *n_kernels receives the number of kernels
+ * (at most cap are written).
+ */
+hp_status hp_profile_enable(hp_ctx *ctx, uint32_t max_launches);
+hp_status hp_profile_read(hp_ctx *ctx, uint32_t cap, const char **names, double *total_ms, uint64_t *launches,
+                          uint32_t *n_kernels);
+
+/*
+ * Test hook (host-side fault injection): the next `count` pool allocations
+ * of the context fail with HP_ENOMEM.
+ */
+hp_status hp_debug_fail_allocations(hp_ctx *ctx, uint32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HP_H */

@@ -1,0 +1,97 @@
+// Internal interface between the libhp host runtime and its sm_103a kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace hp {
+
+// Error bits accumulated on the device (per event, and per launch).
+constexpr uint32_t kErrBadDigi = 1u;
+constexpr uint32_t kErrDup = 2u;
+constexpr uint32_t kErrCapacity = 4u;
+constexpr uint32_t kErrTimeout = 8u;
+
+// Tuning constants of the kernels.
+constexpr int kChunk = 4096;         // digis per histogram / scatter block
+constexpr int kHistThreads = 256;
+constexpr int kHistCap = 4096;       // (event, module) bins a block can histogram in shared memory
+constexpr int kCCThreads = 256;      // threads of a clustering block
+constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue ticket, one per warp
+constexpr int kWarpMax = 32;         // items with at most this many digis are clustered by one warp
+constexpr int kSmemSlots = 2048;     // surviving pixels a block clusters in shared memory
+
+// A cluster parked between the clustering phase and the ordered write.
+struct StagedCluster {
+    int32_t id, charge, npix;
+    float x, y;
+    int32_t pad;
+};
+
+struct Geometry {
+    uint32_t M, R, C;
+    int32_t pixel_thr, cluster_thr;
+    const int32_t *gain; // device [M]
+    const int32_t *ped;  // device [M]
+};
+
+struct Outputs {
+    uint64_t capacity;
+    uint32_t *module;
+    int32_t *id, *charge, *npix;
+    float *x, *y;
+    uint64_t *cluster_offsets; // [E+1]
+    int32_t *label;            // [N] or null
+    int32_t *event_status;     // [E] written by the finalize kernel
+};
+
+// Scratch of one launch.  The first `zero_bytes` bytes must be zero before
+// the first kernel (one memset): control words, per-event error bits,
+// per-item counts and the chained-scan state.
+struct Workspace {
+    uint32_t *ctl;        // [16]: 0 group ticket, 1 launch error bits, 2 arena bump
+    uint32_t *event_err;  // [E]
+    uint32_t *count;      // [E*M]
+    unsigned long long *chain; // [n_groups]
+    size_t zero_bytes;
+    uint32_t *boff;       // [E*M] bucket start of each item
+    uint32_t *cursor;     // [E*M] scatter cursor
+    uint32_t *bucket_w;   // [N]
+    uint32_t *bucket_i;   // [N] index of the digi within its event
+    StagedCluster *staging; // [N]
+    unsigned char *big;   // scratch of items too large for shared memory
+    uint64_t big_slots;   // slots per block (slab mode) or in total (arena mode)
+    int big_arena;        // 1: bump-allocated arena, 0: one slab per block
+};
+
+struct Launch {
+    Geometry g;
+    uint32_t E;
+    uint64_t N;
+    const uint64_t *offsets; // device [E+1]
+    const uint32_t *words;   // device [N]
+    const uint16_t *modules; // device [N]
+    Outputs out;
+    Workspace ws;
+    int cc_grid;             // blocks of the clustering kernel
+};
+
+// Bytes of one big-tier slot: parent, linear index, three 64-bit accumulators.
+constexpr size_t kBigSlotBytes = 4 + 4 + 8 * 3;
+
+size_t cc_smem_bytes(uint32_t R, uint32_t C);
+// Lay out the workspace for (E, M, N) in `base` (nullptr: only compute size).
+size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
+                       Workspace *ws);
+// Configure kernel attributes once per device; returns blocks per SM of the clustering kernel.
+cudaError_t init_kernels(int device, uint32_t R, uint32_t C, int *cc_blocks_per_sm);
+// Kernels of one launch, in order; marks[i] (if given) is recorded before
+// kernel i and marks[kNumKernels] after the last one.
+constexpr int kNumKernels = 5;
+extern const char *const kKernelNames[kNumKernels];
+// Queue the whole reconstruction of one launch on `stream` (memset + kernels).
+cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count,
+                               cudaEvent_t *marks = nullptr);
+
+} // namespace hp

@@ -1,0 +1,806 @@
+// sm_103a kernels of libhp: silicon-pixel local reconstruction.
+//
+// One launch reconstructs a batch of E independent events (a single event is
+// E = 1).  The unit of clustering work is an item = (event, module); there
+// are E * M items, in (event, module) order.
+//
+//   hist_kernel     module histogram: count[item] (shared-memory bins per
+//                   block of 4096 digis, flushed with global atomics);
+//                   validates module ids
+//   scan_kernel     one block per event: exclusive prefix sum of the event's
+//                   M counts -> bucket start of every item (the event's digi
+//                   offset is the base, so events scan independently)
+//   scatter_kernel  bucket scatter: each digi's word and in-event index go to
+//                   its item's bucket (block-local ranks in shared memory,
+//                   one global atomic per non-empty bin to reserve a range)
+//   cc_kernel       persistent clustering: blocks take tickets of kGroup
+//                   consecutive items; items of <= 32 digis are clustered by
+//                   one warp in registers, larger items by the whole block on
+//                   a shared-memory pixel bitmap with rank-addressed
+//                   union-find (items beyond the shared-memory capacity keep
+//                   their slot arrays in global scratch); clusters are then
+//                   written in (event, module, id) order through a chained
+//                   scan over the tickets
+//   finalize_kernel per-event status codes
+//
+// Clustering of one module (block tier): set a bit per digi in an occupancy
+// bitmap (a bit already set is a duplicate) and a bit per surviving pixel in
+// a survivor bitmap; an exclusive prefix popcount over the survivor bitmap
+// gives every surviving pixel a dense slot = its rank in row-major order, so
+// slot order is linear-pixel order.  Each surviving pixel unions with its
+// surviving backward 8-neighbours (left, and the three above) by atomicMin
+// linking of roots (smaller slot wins), so every root is the smallest slot,
+// i.e. the smallest linear index, of its cluster.  Charges, pixel counts and
+// moments relative to the root pixel accumulate in 64-bit integers; the
+// ordinal of a kept cluster is the rank of its root among kept roots in slot
+// order, so the per-module output is already sorted by id.
+#include <climits>
+#include <cstdint>
+
+#include "hp_internal.h"
+
+namespace hp {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+struct BlockShared {
+    uint32_t flag;
+    uint32_t scan_tmp[kCCThreads / 32 + 1];
+    uint32_t big_off;
+};
+
+struct ItemCtx {
+    uint32_t e, m, b, n;
+    int32_t gain, ped;
+    int32_t *label_e;  // label of the event's first digi, or null
+    uint32_t *err_e;   // the event's error bits
+};
+
+struct SlotArrays {
+    unsigned long long *qn; // (Q << 17) + npix of a root slot
+    unsigned long long *sr; // sum q * (row - root row)
+    unsigned long long *sc; // sum q * (col - root col), two's complement
+    uint32_t *parent;
+    uint32_t *slin;         // linear pixel index of a slot
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Largest e in [lo, hi] with off[e] <= k (requires off[lo] <= k).
+__device__ __forceinline__ uint32_t find_event(const uint64_t *off, uint32_t lo, uint32_t hi, uint64_t k)
+{
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Exclusive scan of one value per thread over a block of T threads.
+template <int T>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t wv = lane < T / 32 ? tmp[lane] : 0u;
+        uint32_t ws = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, ws, o);
+            if (lane >= o) ws += y;
+        }
+        if (lane < T / 32) tmp[lane] = ws - wv;
+        if (lane == T / 32 - 1) tmp[T / 32] = ws;
+    }
+    __syncthreads();
+    const uint32_t r = tmp[warp] + x - v;
+    *total = tmp[T / 32];
+    __syncthreads();
+    return r;
+}
+
+// s / Q as a float offset, with s an exact integer moment: exact operands and
+// one rounding when they fit the float mantissa, else integer quotient plus a
+// rounded remainder fraction.
+__device__ __forceinline__ float centroid(int32_t origin, long long s, int32_t Q)
+{
+    if (s > -16777216LL && s < 16777216LL && Q < 16777216)
+        return (float)origin + (float)s / (float)Q;
+    const long long qt = s / Q;
+    const long long rem = s - qt * Q;
+    return (float)(origin + qt) + (float)rem / (float)Q;
+}
+
+__device__ __forceinline__ ItemCtx make_item(const Launch &L, uint64_t item, uint32_t b, uint32_t n)
+{
+    ItemCtx it;
+    it.e = (uint32_t)(item / L.g.M);
+    it.m = (uint32_t)(item - (uint64_t)it.e * L.g.M);
+    it.b = b;
+    it.n = n;
+    it.gain = L.g.gain[it.m];
+    it.ped = L.g.ped[it.m];
+    it.label_e = L.out.label ? L.out.label + L.offsets[it.e] : nullptr;
+    it.err_e = L.ws.event_err + it.e;
+    return it;
+}
+
+// ---------------------------------------------------------------- histogram
+
+__global__ void __launch_bounds__(kHistThreads) hist_kernel(const Launch L)
+{
+    extern __shared__ uint32_t sh[];
+    __shared__ uint32_t s_ef, s_el;
+    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk;
+    const uint64_t c1 = min(L.N, c0 + (uint64_t)kChunk);
+    if (threadIdx.x == 0) {
+        s_ef = find_event(L.offsets, 0, L.E - 1, c0);
+        s_el = find_event(L.offsets, s_ef, L.E - 1, c1 - 1);
+    }
+    __syncthreads();
+    const uint32_t ef = s_ef, el = s_el, M = L.g.M;
+    const uint64_t nkeys64 = (uint64_t)(el - ef + 1) * M;
+    const bool use_sh = nkeys64 <= (uint64_t)kHistCap;
+    const uint32_t nkeys = use_sh ? (uint32_t)nkeys64 : 0u;
+    const uint64_t keybase = (uint64_t)ef * M;
+    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) sh[i] = 0;
+    __syncthreads();
+    for (uint64_t k = c0 + threadIdx.x; k < c1; k += kHistThreads) {
+        const uint32_t e = ef == el ? ef : find_event(L.offsets, ef, el, k);
+        const uint32_t m = L.modules[k];
+        if (m >= M) {
+            atomicOr(&L.ws.event_err[e], kErrBadDigi);
+            continue;
+        }
+        const uint64_t key = (uint64_t)e * M + m;
+        if (use_sh)
+            atomicAdd(&sh[key - keybase], 1u);
+        else
+            atomicAdd(&L.ws.count[key], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) {
+        const uint32_t v = sh[i];
+        if (v) atomicAdd(&L.ws.count[keybase + i], v);
+    }
+}
+
+// ---------------------------------------------------------------- scan
+
+__global__ void __launch_bounds__(256) scan_kernel(const Launch L)
+{
+    __shared__ uint32_t tmp[256 / 32 + 1];
+    const uint32_t e = blockIdx.x, M = L.g.M;
+    const uint64_t kb = (uint64_t)e * M;
+    const uint32_t per = (M + 255) / 256;
+    const uint32_t m0 = min(M, threadIdx.x * per), m1 = min(M, m0 + per);
+    uint32_t local = 0;
+    for (uint32_t m = m0; m < m1; ++m) local += L.ws.count[kb + m];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<256>(local, tmp, &total) + (uint32_t)L.offsets[e];
+    for (uint32_t m = m0; m < m1; ++m) {
+        L.ws.boff[kb + m] = run;
+        L.ws.cursor[kb + m] = run;
+        run += L.ws.count[kb + m];
+    }
+}
+
+// ---------------------------------------------------------------- scatter
+
+__global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
+{
+    extern __shared__ uint32_t sh[];
+    uint32_t *cnt = sh;
+    uint32_t *bas = sh + kHistCap;
+    __shared__ uint32_t s_ef, s_el;
+    constexpr int PER = kChunk / kHistThreads;
+    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk;
+    const uint64_t c1 = min(L.N, c0 + (uint64_t)kChunk);
+    if (threadIdx.x == 0) {
+        s_ef = find_event(L.offsets, 0, L.E - 1, c0);
+        s_el = find_event(L.offsets, s_ef, L.E - 1, c1 - 1);
+    }
+    __syncthreads();
+    const uint32_t ef = s_ef, el = s_el, M = L.g.M;
+    const uint64_t nkeys64 = (uint64_t)(el - ef + 1) * M;
+    const bool use_sh = nkeys64 <= (uint64_t)kHistCap;
+    const uint32_t nkeys = use_sh ? (uint32_t)nkeys64 : 0u;
+    const uint64_t keybase = (uint64_t)ef * M;
+    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) cnt[i] = 0;
+    __syncthreads();
+    uint32_t pos[PER], keyl[PER], evt[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t k = c0 + threadIdx.x + (uint64_t)j * kHistThreads;
+        pos[j] = 0xFFFFFFFFu;
+        keyl[j] = 0;
+        evt[j] = ef;
+        if (k < c1) {
+            const uint32_t e = ef == el ? ef : find_event(L.offsets, ef, el, k);
+            const uint32_t m = L.modules[k];
+            evt[j] = e;
+            if (m < M) {
+                const uint64_t key = (uint64_t)e * M + m;
+                if (use_sh) {
+                    keyl[j] = (uint32_t)(key - keybase);
+                    pos[j] = atomicAdd(&cnt[keyl[j]], 1u);
+                } else {
+                    pos[j] = atomicAdd(&L.ws.cursor[key], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) {
+        const uint32_t v = cnt[i];
+        if (v) bas[i] = atomicAdd(&L.ws.cursor[keybase + i], v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if (pos[j] == 0xFFFFFFFFu) continue;
+        const uint64_t k = c0 + threadIdx.x + (uint64_t)j * kHistThreads;
+        const uint32_t p = use_sh ? bas[keyl[j]] + pos[j] : pos[j];
+        L.ws.bucket_w[p] = L.words[k];
+        L.ws.bucket_i[p] = (uint32_t)(k - L.offsets[evt[j]]);
+    }
+}
+
+// ---------------------------------------------------------------- clustering
+
+__device__ __forceinline__ uint32_t uf_find(const uint32_t *parent, uint32_t x)
+{
+    const volatile uint32_t *p = parent;
+    uint32_t y = p[x];
+    while (y != x) {
+        x = y;
+        y = p[x];
+    }
+    return x;
+}
+
+// Lock-free union of the trees of a and b: the larger root is linked under
+// the smaller with atomicMin; a lost race re-runs with the new parent.
+__device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t b)
+{
+    for (;;) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        if (a < b) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        const uint32_t old = atomicMin(&parent[a], b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+__device__ __forceinline__ uint32_t rank_of(const uint32_t *sbits, const uint32_t *spre, uint32_t lin)
+{
+    return spre[lin >> 5] + __popc(sbits[lin >> 5] & ((1u << (lin & 31)) - 1u));
+}
+
+__device__ __forceinline__ bool has_bit(const uint32_t *bits, uint32_t lin)
+{
+    return (bits[lin >> 5] >> (lin & 31)) & 1u;
+}
+
+// One item of at most 32 digis, clustered by one warp in registers: lane i
+// holds digi i; adjacency is a 32-bit mask per lane; the cluster id (the
+// smallest linear index) spreads over the adjacency by min-propagation.
+// Returns the number of kept clusters (all lanes).
+__device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int R = (int)L.g.R, C = (int)L.g.C;
+    const uint32_t n = it.n;
+    const bool have = lane < n;
+    uint32_t w = 0, idx = 0;
+    if (have) {
+        w = L.ws.bucket_w[it.b + lane];
+        idx = L.ws.bucket_i[it.b + lane];
+    }
+    const int r = (int)(w & 0xFFu), c = (int)((w >> 8) & 0x1FFu), adc = (int)((w >> 17) & 0xFFu);
+    const bool valid = r < R && c < C && adc > 0 && (w >> 25) == 0;
+    if (__any_sync(kFull, have && !valid)) {
+        if (lane == 0) atomicOr(it.err_e, kErrBadDigi);
+        return 0;
+    }
+    const int lin = have ? r * C + c : -1 - (int)lane;
+    const uint32_t same = __match_any_sync(kFull, lin);
+    if (__any_sync(kFull, have && __popc(same) > 1)) {
+        if (lane == 0) atomicOr(it.err_e, kErrDup);
+        return 0;
+    }
+    const int q = adc * it.gain - it.ped;
+    const bool surv = have && q >= L.g.pixel_thr;
+    const uint32_t smask = __ballot_sync(kFull, surv);
+    uint32_t adj = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        const int rj = __shfl_sync(kFull, r, j), cj = __shfl_sync(kFull, c, j);
+        if (((smask >> j) & 1u) && j != lane && abs(rj - r) <= 1 && abs(cj - c) <= 1) adj |= 1u << j;
+    }
+    if (!surv) adj = 0;
+    int lab = surv ? lin : INT_MAX;
+    for (uint32_t round = 0; round < n; ++round) {
+        int nl = lab;
+        for (uint32_t j = 0; j < n; ++j) {
+            const int lj = __shfl_sync(kFull, lab, j);
+            if ((adj >> j) & 1u) nl = min(nl, lj);
+        }
+        const bool changed = nl != lab;
+        lab = nl;
+        if (!__any_sync(kFull, changed)) break;
+    }
+    const uint32_t grp = __match_any_sync(kFull, surv ? lab : -1 - (int)lane);
+    const int rr = surv ? lab / C : 0;
+    const int rc = surv ? lab - rr * C : 0;
+    int Q = 0, np = 0, Sr = 0, Sc = 0; // |sums| < 32 * 32263 * 31 < 2^31
+    for (uint32_t j = 0; j < n; ++j) {
+        const int qj = __shfl_sync(kFull, q, j), rj = __shfl_sync(kFull, r, j), cj = __shfl_sync(kFull, c, j);
+        if ((grp >> j) & 1u) {
+            Q += qj;
+            ++np;
+            Sr += qj * (rj - rr);
+            Sc += qj * (cj - rc);
+        }
+    }
+    const bool leader = surv && lin == lab;
+    const bool kept = surv && Q >= L.g.cluster_thr;
+    const uint32_t kl = __ballot_sync(kFull, leader && kept);
+    uint32_t ord = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        const int lj = __shfl_sync(kFull, lin, j);
+        if (((kl >> j) & 1u) && lj < lin) ++ord;
+    }
+    if (leader && kept) {
+        StagedCluster s;
+        s.id = lab;
+        s.charge = Q;
+        s.npix = np;
+        s.x = centroid(rr, Sr, Q);
+        s.y = centroid(rc, Sc, Q);
+        s.pad = 0;
+        L.ws.staging[it.b + ord] = s;
+    }
+    if (it.label_e && have) it.label_e[idx] = !surv ? -1 : (kept ? lab : -2);
+    return __popc(kl);
+}
+
+// One item clustered by the whole block (see the file comment).  kBig: the
+// slot arrays live in global scratch instead of shared memory.  Returns the
+// number of kept clusters (uniform over the block).
+template <bool kBig>
+__device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits,
+                               uint32_t *spre, const SlotArrays &sa, BlockShared &bs)
+{
+    const uint32_t R = L.g.R, C = L.g.C, nwords = (R * C + 31) >> 5;
+    const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t *bw = L.ws.bucket_w + it.b;
+    const uint32_t *bi = L.ws.bucket_i + it.b;
+
+    for (uint32_t i = tid; i < nwords; i += kCCThreads) {
+        abits[i] = 0;
+        sbits[i] = 0;
+    }
+    if (tid == 0) bs.flag = 0;
+    __syncthreads();
+
+    // occupancy and survivor bitmaps; validation and duplicate detection
+    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
+        const uint32_t w = bw[k];
+        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, adc = (w >> 17) & 0xFFu;
+        if (r >= R || c >= C || adc == 0 || (w >> 25) != 0) {
+            atomicOr(&bs.flag, kErrBadDigi);
+            continue;
+        }
+        const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
+        const uint32_t old = atomicOr(&abits[lin >> 5], bit);
+        if (old & bit) atomicOr(&bs.flag, kErrDup);
+        if ((int32_t)adc * it.gain - it.ped >= thr) atomicOr(&sbits[lin >> 5], bit);
+    }
+    __syncthreads();
+    const uint32_t flag = bs.flag;
+    if (flag) {
+        if (tid == 0) atomicOr(it.err_e, flag);
+        __syncthreads();
+        return 0;
+    }
+
+    // exclusive prefix popcount of the survivor bitmap -> dense slots
+    const uint32_t per = (nwords + kCCThreads - 1) / kCCThreads;
+    const uint32_t w0 = min(nwords, tid * per), w1 = min(nwords, w0 + per);
+    uint32_t local = 0;
+    for (uint32_t i = w0; i < w1; ++i) local += __popc(sbits[i]);
+    uint32_t S;
+    uint32_t run = block_exclusive_scan<kCCThreads>(local, bs.scan_tmp, &S);
+    for (uint32_t i = w0; i < w1; ++i) {
+        spre[i] = run;
+        run += __popc(sbits[i]);
+    }
+    __syncthreads();
+
+    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
+        const uint32_t w = bw[k];
+        const uint32_t lin = (w & 0xFFu) * C + ((w >> 8) & 0x1FFu);
+        if (!has_bit(sbits, lin)) continue;
+        const uint32_t s = rank_of(sbits, spre, lin);
+        sa.parent[s] = s;
+        sa.slin[s] = lin;
+        sa.qn[s] = 0;
+        sa.sr[s] = 0;
+        sa.sc[s] = 0;
+    }
+    __syncthreads();
+
+    // union with the surviving backward neighbours
+    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
+        const uint32_t w = bw[k];
+        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu;
+        const uint32_t lin = r * C + c;
+        if (!has_bit(sbits, lin)) continue;
+        const uint32_t s = rank_of(sbits, spre, lin);
+        if (c > 0 && has_bit(sbits, lin - 1)) uf_union(sa.parent, s, rank_of(sbits, spre, lin - 1));
+        if (r > 0) {
+            const uint32_t up = lin - C;
+            if (c > 0 && has_bit(sbits, up - 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up - 1));
+            if (has_bit(sbits, up)) uf_union(sa.parent, s, rank_of(sbits, spre, up));
+            if (c + 1 < C && has_bit(sbits, up + 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up + 1));
+        }
+    }
+    __syncthreads();
+
+    // charge, size and moments about the root pixel
+    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
+        const uint32_t w = bw[k];
+        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu;
+        const uint32_t lin = r * C + c;
+        if (!has_bit(sbits, lin)) continue;
+        const uint32_t s = rank_of(sbits, spre, lin);
+        const uint32_t root = uf_find(sa.parent, s);
+        sa.parent[s] = root;
+        const uint32_t rl = sa.slin[root];
+        const int32_t rr = (int32_t)(rl / C), rc = (int32_t)(rl - (uint32_t)rr * C);
+        const int32_t q = (int32_t)((w >> 17) & 0xFFu) * it.gain - it.ped;
+        atomicAdd(&sa.qn[root], ((unsigned long long)q << 17) | 1ull);
+        atomicAdd(&sa.sr[root], (unsigned long long)(long long)(q * ((int32_t)r - rr)));
+        atomicAdd(&sa.sc[root], (unsigned long long)(long long)(q * ((int32_t)c - rc)));
+    }
+    __syncthreads();
+
+    if (it.label_e) {
+        for (uint32_t k = tid; k < it.n; k += kCCThreads) {
+            const uint32_t w = bw[k];
+            const uint32_t lin = (w & 0xFFu) * C + ((w >> 8) & 0x1FFu);
+            int32_t lab = -1;
+            if (has_bit(sbits, lin)) {
+                const uint32_t root = sa.parent[rank_of(sbits, spre, lin)];
+                lab = (int32_t)(sa.qn[root] >> 17) >= cthr ? (int32_t)sa.slin[root] : -2;
+            }
+            it.label_e[bi[k]] = lab;
+        }
+    }
+
+    // kept roots in slot order -> ordinals -> staging
+    const uint32_t sper = (S + kCCThreads - 1) / kCCThreads;
+    const uint32_t s0 = min(S, tid * sper), s1 = min(S, s0 + sper);
+    uint32_t cnt = 0;
+    for (uint32_t s = s0; s < s1; ++s)
+        if (sa.parent[s] == s && (int32_t)(sa.qn[s] >> 17) >= cthr) ++cnt;
+    uint32_t K;
+    uint32_t ord = block_exclusive_scan<kCCThreads>(cnt, bs.scan_tmp, &K);
+    for (uint32_t s = s0; s < s1; ++s) {
+        if (sa.parent[s] != s) continue;
+        const unsigned long long qn = sa.qn[s];
+        const int32_t Q = (int32_t)(qn >> 17);
+        if (Q < cthr) continue;
+        const uint32_t id = sa.slin[s];
+        const int32_t rr = (int32_t)(id / C), rc = (int32_t)(id - (uint32_t)rr * C);
+        StagedCluster o;
+        o.id = (int32_t)id;
+        o.charge = Q;
+        o.npix = (int32_t)(qn & 0x1FFFFull);
+        o.x = centroid(rr, (long long)sa.sr[s], Q);
+        o.y = centroid(rc, (long long)sa.sc[s], Q);
+        o.pad = 0;
+        L.ws.staging[it.b + ord++] = o;
+    }
+    return K;
+}
+
+// Decoupled look-back over tickets: publish this ticket's aggregate, sum the
+// predecessors' values back to the first inclusive prefix, publish ours.
+// Every predecessor ticket is held by a running block that publishes its
+// aggregate without waiting, so the wait ends; it is bounded regardless.
+__device__ unsigned long long chain_lookback(unsigned long long *chain, uint64_t g, unsigned long long agg,
+                                             uint32_t *launch_err)
+{
+    const unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62, kMask = kAgg - 1;
+    if (g == 0) {
+        st_release(&chain[0], kInc | agg);
+        return 0;
+    }
+    st_release(&chain[g], kAgg | agg);
+    unsigned long long excl = 0;
+    long long j = (long long)g - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        const unsigned long long v = ld_acquire(&chain[j]);
+        if ((v >> 62) == 0) {
+            if (++spins > kSpinLimit) {
+                atomicOr(launch_err, kErrTimeout);
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        excl += v & kMask;
+        if ((v >> 62) == 2) break;
+        --j;
+    }
+    st_release(&chain[g], kInc | (excl + agg));
+    return excl;
+}
+
+__global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ BlockShared bs;
+    __shared__ uint32_t s_n[kGroup], s_b[kGroup], s_K[kGroup], s_pref[kGroup + 1];
+    __shared__ uint32_t s_ticket;
+    __shared__ unsigned long long s_prefix;
+
+    const uint32_t R = L.g.R, C = L.g.C, M = L.g.M;
+    const uint32_t nwords = (R * C + 31) >> 5;
+    const uint32_t tid = threadIdx.x;
+    SlotArrays sm;
+    sm.qn = reinterpret_cast<unsigned long long *>(dsm);
+    sm.sr = sm.qn + kSmemSlots;
+    sm.sc = sm.sr + kSmemSlots;
+    sm.parent = reinterpret_cast<uint32_t *>(sm.sc + kSmemSlots);
+    sm.slin = sm.parent + kSmemSlots;
+    uint32_t *abits = sm.slin + kSmemSlots;
+    uint32_t *sbits = abits + nwords;
+    uint32_t *spre = sbits + nwords;
+
+    const uint64_t EM = (uint64_t)L.E * M;
+    const uint64_t ngroups = (EM + kGroup - 1) / kGroup;
+
+    for (;;) {
+        if (tid == 0) s_ticket = atomicAdd(&L.ws.ctl[0], 1u);
+        __syncthreads();
+        const uint64_t g = s_ticket;
+        if (g >= ngroups) break;
+        const uint64_t item0 = g * kGroup;
+        if (tid < (uint32_t)kGroup) {
+            const uint64_t item = item0 + tid;
+            const bool ok = item < EM;
+            s_n[tid] = ok ? L.ws.count[item] : 0u;
+            s_b[tid] = ok ? L.ws.boff[item] : 0u;
+            s_K[tid] = 0;
+        }
+        __syncthreads();
+
+        {   // warp tier: one warp per small item
+            const uint32_t wi = tid >> 5;
+            const uint32_t n = s_n[wi];
+            if (n > 0 && n <= (uint32_t)kWarpMax) {
+                const ItemCtx it = make_item(L, item0 + wi, s_b[wi], n);
+                const uint32_t K = warp_item(L, it);
+                if ((tid & 31) == 0) s_K[wi] = K;
+            }
+        }
+        __syncthreads();
+
+        for (int i = 0; i < kGroup; ++i) { // block tier: larger items one at a time
+            const uint32_t n = s_n[i];
+            if (n <= (uint32_t)kWarpMax) continue;
+            const ItemCtx it = make_item(L, item0 + i, s_b[i], n);
+            uint32_t K;
+            if (n <= (uint32_t)kSmemSlots) {
+                K = block_item<false>(L, it, abits, sbits, spre, sm, bs);
+            } else {
+                if (tid == 0) {
+                    bs.big_off = 0;
+                    if (L.ws.big_arena) {
+                        const uint32_t off = atomicAdd(&L.ws.ctl[2], n);
+                        bs.big_off = off;
+                        if ((uint64_t)off + n > L.ws.big_slots) atomicOr(&L.ws.ctl[1], kErrCapacity);
+                    }
+                }
+                __syncthreads();
+                SlotArrays ga;
+                uint64_t cap;
+                unsigned char *base;
+                if (L.ws.big_arena) {
+                    cap = n;
+                    base = L.ws.big + (uint64_t)bs.big_off * kBigSlotBytes;
+                } else {
+                    cap = L.ws.big_slots;
+                    base = L.ws.big + (uint64_t)blockIdx.x * L.ws.big_slots * kBigSlotBytes;
+                }
+                const bool fits = L.ws.big_arena ? (uint64_t)bs.big_off + n <= L.ws.big_slots
+                                                 : (uint64_t)min(n, R * C) <= L.ws.big_slots;
+                ga.qn = reinterpret_cast<unsigned long long *>(base);
+                ga.sr = ga.qn + cap;
+                ga.sc = ga.sr + cap;
+                ga.parent = reinterpret_cast<uint32_t *>(ga.sc + cap);
+                ga.slin = ga.parent + cap;
+                K = fits ? block_item<true>(L, it, abits, sbits, spre, ga, bs) : 0u;
+                if (!fits && tid == 0) atomicOr(&L.ws.ctl[1], kErrCapacity);
+            }
+            if (tid == 0) s_K[i] = K;
+            __syncthreads();
+        }
+
+        // ordered write of the ticket's clusters
+        if (tid == 0) {
+            uint32_t p = 0;
+            for (int i = 0; i < kGroup; ++i) {
+                s_pref[i] = p;
+                p += s_K[i];
+            }
+            s_pref[kGroup] = p;
+            s_prefix = chain_lookback(L.ws.chain, g, p, &L.ws.ctl[1]);
+        }
+        __syncthreads();
+        const unsigned long long P = s_prefix;
+        const uint32_t tot = s_pref[kGroup];
+        for (uint32_t o = tid; o < tot; o += kCCThreads) {
+            int i = 0;
+            while (i + 1 < kGroup && s_pref[i + 1] <= o) ++i;
+            const StagedCluster s = L.ws.staging[s_b[i] + (o - s_pref[i])];
+            const unsigned long long d = P + o;
+            if (d < L.out.capacity) {
+                L.out.module[d] = (uint32_t)((item0 + i) % M);
+                L.out.id[d] = s.id;
+                L.out.charge[d] = s.charge;
+                L.out.npix[d] = s.npix;
+                L.out.x[d] = s.x;
+                L.out.y[d] = s.y;
+            }
+        }
+        if (tid == 0 && P + tot > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
+        if (tid < (uint32_t)kGroup) {
+            const uint64_t item = item0 + tid;
+            if (item < EM && item % M == 0) L.out.cluster_offsets[item / M] = P + s_pref[tid];
+        }
+        if (tid == 0 && g == ngroups - 1) L.out.cluster_offsets[L.E] = P + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void finalize_kernel(const Launch L)
+{
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L.E) return;
+    const uint32_t bits = L.ws.event_err[e] | L.ws.ctl[1];
+    int32_t st = 0;                          // HP_OK
+    if (bits & kErrTimeout) st = 8;          // HP_ETIMEOUT
+    else if (bits & kErrCapacity) st = 6;    // HP_ECAPACITY
+    else if (bits & kErrBadDigi) st = 4;     // HP_EBADDIGI
+    else if (bits & kErrDup) st = 5;         // HP_EDUP
+    L.out.event_status[e] = st;
+}
+
+} // namespace
+
+size_t cc_smem_bytes(uint32_t R, uint32_t C)
+{
+    const size_t nwords = ((size_t)R * C + 31) / 32;
+    return (size_t)kSmemSlots * (8 * 3 + 4 * 2) + nwords * 4 * 3;
+}
+
+size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
+                       Workspace *ws)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> unsigned char * {
+        off = (off + 255) & ~(size_t)255;
+        const size_t o = off;
+        off += bytes;
+        return base ? static_cast<unsigned char *>(base) + o : nullptr;
+    };
+    const uint64_t EM = (uint64_t)E * M;
+    const uint64_t ngroups = (EM + kGroup - 1) / kGroup;
+    Workspace w{};
+    w.ctl = reinterpret_cast<uint32_t *>(take(64));
+    w.event_err = reinterpret_cast<uint32_t *>(take(4ull * E));
+    w.count = reinterpret_cast<uint32_t *>(take(4ull * EM));
+    w.chain = reinterpret_cast<unsigned long long *>(take(8ull * ngroups));
+    off = (off + 255) & ~(size_t)255;
+    w.zero_bytes = off;
+    w.boff = reinterpret_cast<uint32_t *>(take(4ull * EM));
+    w.cursor = reinterpret_cast<uint32_t *>(take(4ull * EM));
+    w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
+    w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
+    w.staging = reinterpret_cast<StagedCluster *>(take(sizeof(StagedCluster) * N));
+    const uint64_t slab_slots = std::min<uint64_t>((uint64_t)R * C, N);
+    const uint64_t slab_total = slab_slots * (uint64_t)(cc_grid > 0 ? cc_grid : 1);
+    w.big_arena = N <= slab_total ? 1 : 0;
+    w.big_slots = w.big_arena ? N : slab_slots;
+    w.big = take(kBigSlotBytes * (w.big_arena ? N : slab_total));
+    off = (off + 255) & ~(size_t)255;
+    if (ws) *ws = w;
+    return off;
+}
+
+cudaError_t init_kernels(int device, uint32_t R, uint32_t C, int *cc_blocks_per_sm)
+{
+    cudaError_t err = cudaSetDevice(device);
+    if (err != cudaSuccess) return err;
+    const size_t smem = cc_smem_bytes(R, C);
+    err = cudaFuncSetAttribute(cc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int nb = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cc_kernel, kCCThreads, smem);
+    if (err != cudaSuccess) return err;
+    *cc_blocks_per_sm = nb > 0 ? nb : 1;
+    return cudaSuccess;
+}
+
+const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel", "scatter_kernel", "cc_kernel",
+                                                "finalize_kernel"};
+
+cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count, cudaEvent_t *marks)
+{
+    cudaError_t err = cudaMemsetAsync(L.ws.ctl, 0, L.ws.zero_bytes, stream);
+    if (err != cudaSuccess) return err;
+    auto mark = [&](int i) {
+        if (marks && err == cudaSuccess) err = cudaEventRecord(marks[i], stream);
+    };
+    uint64_t nk = 0;
+    const uint64_t nchunks = (L.N + kChunk - 1) / kChunk;
+    mark(0);
+    if (L.N > 0) {
+        hist_kernel<<<(unsigned)nchunks, kHistThreads, kHistCap * sizeof(uint32_t), stream>>>(L);
+        ++nk;
+    }
+    mark(1);
+    scan_kernel<<<L.E, 256, 0, stream>>>(L);
+    ++nk;
+    mark(2);
+    if (L.N > 0) {
+        scatter_kernel<<<(unsigned)nchunks, kHistThreads, 2 * kHistCap * sizeof(uint32_t), stream>>>(L);
+        ++nk;
+    }
+    mark(3);
+    cc_kernel<<<L.cc_grid, kCCThreads, cc_smem_bytes(L.g.R, L.g.C), stream>>>(L);
+    ++nk;
+    mark(4);
+    finalize_kernel<<<(L.E + 255) / 256, 256, 0, stream>>>(L);
+    ++nk;
+    mark(5);
+    if (kernel_count) *kernel_count += nk;
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
+} // namespace hp

@@ -1,0 +1,841 @@
+// Host runtime of libhp: contexts, the stream pool, the caching allocators,
+// events with exactly-once completion callbacks, and the C ABI of hp.h.
+//
+// Execution model (arXiv:2004.04334 Sec. 2 and Sec. 4.1): an enqueue call
+// is the non-blocking acquire(): it stages the inputs in pooled pinned
+// memory, queues copies and kernels on one stream of the pool and a host
+// function after them, and returns.  The host function (the holder of
+// Sec. 2) runs when the device work is done, marks the event complete and
+// fires the user's callback; produce() is hp_fetch_clusters on the pinned
+// results.  No allocation, synchronisation or device assert happens on this
+// path once the pools are warm (Sec. 4.1): every buffer comes from a
+// caching pool whose cudaMalloc / cudaHostAlloc calls only happen while it
+// grows.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "hp.h"
+#include "hp_internal.h"
+
+namespace {
+
+uint64_t now_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// Bin sizes: four bins per power of two, 4 KiB minimum (at most 25% slack).
+size_t round_bin(size_t bytes)
+{
+    if (bytes <= 4096) return 4096;
+    int lg = 63 - __builtin_clzll((unsigned long long)bytes);
+    size_t step = ((size_t)1 << lg) / 4;
+    return (bytes + step - 1) / step * step;
+}
+
+struct Block {
+    void *ptr = nullptr;  // host address (host pool) or device address
+    void *dptr = nullptr; // device alias of the block
+    size_t bytes = 0;
+};
+
+// Caching allocator for device or mapped pinned host memory.  Blocks return
+// to a per-size free list and are reused by later requests of the same bin;
+// the backend is only called when no cached block fits.  free() makes no
+// CUDA call, so blocks can be returned from a CUDA host-function thread.
+class Pool {
+  public:
+    explicit Pool(bool host) : host_(host) {}
+
+    hp_status alloc(size_t bytes, Block *out)
+    {
+        const size_t b = round_bin(bytes);
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            if (fail_next_ > 0) {
+                --fail_next_;
+                return HP_ENOMEM;
+            }
+            auto it = free_.find(b);
+            if (it != free_.end()) {
+                *out = it->second;
+                free_.erase(it);
+                ++hits_;
+                return HP_OK;
+            }
+        }
+        Block blk;
+        if (!backend_alloc(b, &blk)) {
+            trim();
+            if (!backend_alloc(b, &blk)) return HP_ENOMEM;
+        }
+        std::lock_guard<std::mutex> g(mu_);
+        ++backend_allocs_;
+        total_ += b;
+        *out = blk;
+        return HP_OK;
+    }
+
+    void free(const Block &b)
+    {
+        if (!b.ptr) return;
+        std::lock_guard<std::mutex> g(mu_);
+        free_.emplace(b.bytes, b);
+    }
+
+    // Release every cached block (CUDA calls; never on the event path).
+    void trim()
+    {
+        std::multimap<size_t, Block> f;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            f.swap(free_);
+            for (auto &kv : f) total_ -= kv.first;
+        }
+        for (auto &kv : f) {
+            if (host_)
+                cudaFreeHost(kv.second.ptr);
+            else
+                cudaFree(kv.second.ptr);
+        }
+    }
+
+    void fail_next(uint32_t n)
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        fail_next_ = n;
+    }
+    uint64_t backend_allocs()
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        return backend_allocs_;
+    }
+    uint64_t hits()
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        return hits_;
+    }
+    uint64_t total_bytes()
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        return total_;
+    }
+
+  private:
+    bool backend_alloc(size_t b, Block *blk)
+    {
+        void *p = nullptr;
+        cudaError_t e = host_ ? cudaHostAlloc(&p, b, cudaHostAllocMapped | cudaHostAllocPortable) : cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        void *d = p;
+        if (host_ && cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(p);
+            return false;
+        }
+        blk->ptr = p;
+        blk->dptr = d;
+        blk->bytes = b;
+        return true;
+    }
+
+    bool host_;
+    std::mutex mu_;
+    std::multimap<size_t, Block> free_;
+    uint64_t backend_allocs_ = 0, hits_ = 0, total_ = 0;
+    uint32_t fail_next_ = 0;
+};
+
+constexpr uint32_t kDone = 1u, kCbSet = 2u, kCbDone = 4u, kReleaseReq = 8u;
+
+} // namespace
+
+struct hp_ctx {
+    hp_config cfg{};
+    int device = 0;
+    int sm_count = 0;
+    int cc_per_sm = 1;
+    int cc_grid = 1;
+    int32_t *d_gain = nullptr, *d_ped = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::atomic<uint32_t> next_stream{0};
+    Pool dpool{false}, hpool{true};
+    std::atomic<uint64_t> inflight{0}, dev_in_use{0};
+    std::atomic<int> failed{0};
+    std::atomic<uint64_t> enqueued{0}, completed{0}, h2d{0}, d2h{0}, kernels{0}, ws_mallocs{0};
+    std::mutex live_mu;
+    std::set<hp_event *> live;
+    std::mutex cev_mu;
+    std::vector<cudaEvent_t> cev_free;
+    std::mutex ws_mu;
+    std::map<cudaStream_t, Block> stream_ws;
+    // stage timers (hp_profile_enable / hp_profile_read)
+    struct ProfRec {
+        cudaEvent_t ev[hp::kNumKernels + 1];
+    };
+    std::mutex prof_mu;
+    uint32_t prof_left = 0;
+    std::vector<ProfRec> prof_used;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+struct hp_event {
+    hp_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    Block dev, host;
+    size_t dev_charge = 0;
+    uint32_t E = 0;
+    uint64_t N = 0;
+    uint32_t flags = 0;
+    uint64_t tag = 0;
+    uint64_t *h_coff = nullptr;
+    int32_t *h_status = nullptr;
+    uint32_t *h_module = nullptr;
+    int32_t *h_id = nullptr, *h_charge = nullptr, *h_npix = nullptr, *h_label = nullptr;
+    float *h_x = nullptr, *h_y = nullptr;
+    std::atomic<uint32_t> state{0};
+    hp_status status = HP_OK;
+    hp_callback cb = nullptr;
+    void *user = nullptr;
+    uint64_t t_enq = 0, t_done = 0;
+};
+
+namespace {
+
+hp_status fail(hp_ctx *ctx)
+{
+    ctx->failed.store(1);
+    return HP_ECUDA;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Free the host side of a completed, released event (no CUDA call).
+void destroy_event(hp_event *ev)
+{
+    hp_ctx *ctx = ev->ctx;
+    ctx->hpool.free(ev->host);
+    {
+        std::lock_guard<std::mutex> g(ctx->cev_mu);
+        ctx->cev_free.push_back(ev->done);
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->live_mu);
+        ctx->live.erase(ev);
+    }
+    delete ev;
+}
+
+// Runs on the CUDA host-function thread once the event's stream work is done.
+void CUDART_CB trampoline(void *p)
+{
+    hp_event *ev = static_cast<hp_event *>(p);
+    hp_ctx *ctx = ev->ctx;
+    hp_status st = HP_OK;
+    for (uint32_t e = 0; e < ev->E; ++e)
+        if (ev->h_status[e] != 0) {
+            st = (hp_status)ev->h_status[e];
+            break;
+        }
+    ev->status = st;
+    ev->t_done = now_ns();
+    ctx->dpool.free(ev->dev);
+    ev->dev = Block();
+    ctx->dev_in_use.fetch_sub(ev->dev_charge);
+    ctx->inflight.fetch_sub(1);
+    ctx->completed.fetch_add(1);
+    const uint32_t prev = ev->state.fetch_or(kDone, std::memory_order_acq_rel);
+    if (prev & kCbSet) {
+        ev->cb(ev->user, ev, st);
+        const uint32_t p2 = ev->state.fetch_or(kCbDone, std::memory_order_acq_rel);
+        if (p2 & kReleaseReq) destroy_event(ev);
+    } else if (prev & kReleaseReq) {
+        destroy_event(ev);
+    }
+}
+
+cudaEvent_t take_cuda_event(hp_ctx *ctx)
+{
+    {
+        std::lock_guard<std::mutex> g(ctx->cev_mu);
+        if (!ctx->cev_free.empty()) {
+            cudaEvent_t e = ctx->cev_free.back();
+            ctx->cev_free.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+hp_status validate_config(const hp_config *c)
+{
+    if (!c || !c->gain || !c->pedestal) return HP_EINVAL;
+    if (c->n_modules < 1 || c->n_modules > 65536) return HP_EINVAL;
+    if (c->rows < 1 || c->rows > 256 || c->cols < 1 || c->cols > 512) return HP_EINVAL;
+    if ((uint64_t)c->rows * c->cols > 131072) return HP_EINVAL;
+    if (c->pixel_thr < 1) return HP_EINVAL;
+    const int64_t qmax_allowed = (int64_t)INT32_MAX / ((int64_t)c->rows * c->cols);
+    for (uint32_t m = 0; m < c->n_modules; ++m) {
+        if (c->gain[m] < 0) return HP_EINVAL;
+        if (255 * (int64_t)c->gain[m] - c->pedestal[m] > qmax_allowed) return HP_EINVAL;
+    }
+    return HP_OK;
+}
+
+hp::Geometry geometry(const hp_ctx *ctx)
+{
+    hp::Geometry g;
+    g.M = ctx->cfg.n_modules;
+    g.R = ctx->cfg.rows;
+    g.C = ctx->cfg.cols;
+    g.pixel_thr = ctx->cfg.pixel_thr;
+    g.cluster_thr = ctx->cfg.cluster_thr;
+    g.gain = ctx->d_gain;
+    g.ped = ctx->d_ped;
+    return g;
+}
+
+int cc_grid_for(const hp_ctx *ctx, uint32_t E)
+{
+    const uint64_t groups = ((uint64_t)E * ctx->cfg.n_modules + hp::kGroup - 1) / hp::kGroup;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(groups, (uint64_t)ctx->cc_grid));
+}
+
+bool device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Timing marks for the next launch, or null when stage timers are off.
+cudaEvent_t *profile_marks(hp_ctx *ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    if (ctx->prof_left == 0) return nullptr;
+    hp_ctx::ProfRec rec;
+    for (int i = 0; i <= hp::kNumKernels; ++i) {
+        if (!ctx->prof_pool.empty()) {
+            rec.ev[i] = ctx->prof_pool.back();
+            ctx->prof_pool.pop_back();
+        } else if (cudaEventCreate(&rec.ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < i; ++j) ctx->prof_pool.push_back(rec.ev[j]);
+            return nullptr;
+        }
+    }
+    --ctx->prof_left;
+    ctx->prof_used.push_back(rec);
+    return ctx->prof_used.back().ev;
+}
+
+hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_t n_single, const uint32_t *words,
+                       const uint16_t *mods, uint64_t tag, uint32_t flags, hp_event **out)
+{
+    if (!ctx || !out) return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    if (E < 1) return HP_EINVAL;
+    uint64_t N = n_single;
+    if (offsets) {
+        if (offsets[0] != 0) return HP_EINVAL;
+        for (uint32_t e = 0; e < E; ++e)
+            if (offsets[e + 1] < offsets[e]) return HP_EINVAL;
+        N = offsets[E];
+    }
+    if (N >= 0xFFFFFFFFull) return HP_EINVAL;
+    if (N > 0 && (!words || !mods)) return HP_EINVAL;
+    const uint64_t EM = (uint64_t)E * ctx->cfg.n_modules;
+    if (EM > (1ull << 31)) return HP_EINVAL;
+    flags |= ctx->cfg.flags;
+    const bool labels = (flags & HP_WANT_LABELS) != 0;
+    const bool nocopy = (flags & HP_INPUT_NOCOPY) != 0;
+
+    // device block: inputs, labels, workspace
+    const int grid = cc_grid_for(ctx, E);
+    const size_t ws_bytes = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols,
+                                                grid, nullptr);
+    size_t doff = 0;
+    const size_t d_words = doff;
+    doff = align_up(doff + 4 * N, 256);
+    const size_t d_mods = doff;
+    doff = align_up(doff + 2 * N, 256);
+    const size_t d_offs = doff;
+    doff = align_up(doff + 8 * (E + 1), 256);
+    const size_t d_label = doff;
+    if (labels) doff = align_up(doff + 4 * N, 256);
+    const size_t d_ws = doff;
+    doff += ws_bytes;
+    const size_t dev_bytes = round_bin(doff);
+
+    // pinned host block: staged inputs, outputs
+    size_t hoff = 0;
+    const size_t h_words = hoff;
+    hoff = align_up(hoff + (nocopy ? 0 : 4 * N), 256);
+    const size_t h_mods = hoff;
+    hoff = align_up(hoff + (nocopy ? 0 : 2 * N), 256);
+    const size_t h_offs = hoff;
+    hoff = align_up(hoff + 8 * (E + 1), 256);
+    const size_t h_coff = hoff;
+    hoff = align_up(hoff + 8 * (E + 1), 256);
+    const size_t h_status = hoff;
+    hoff = align_up(hoff + 4 * E, 256);
+    size_t h_arr[6];
+    for (int i = 0; i < 6; ++i) {
+        h_arr[i] = hoff;
+        hoff = align_up(hoff + 4 * N, 256);
+    }
+    const size_t h_label = hoff;
+    if (labels) hoff = align_up(hoff + 4 * N, 256);
+
+    // admission: in-flight limit and device budget (non-blocking: HP_EAGAIN)
+    const uint64_t maxin = ctx->cfg.max_inflight ? ctx->cfg.max_inflight : 256;
+    if (ctx->inflight.fetch_add(1) >= maxin) {
+        ctx->inflight.fetch_sub(1);
+        return HP_EAGAIN;
+    }
+    const uint64_t used = ctx->dev_in_use.fetch_add(dev_bytes);
+    if (ctx->cfg.device_budget_bytes && used + dev_bytes > ctx->cfg.device_budget_bytes && used > 0) {
+        ctx->dev_in_use.fetch_sub(dev_bytes);
+        ctx->inflight.fetch_sub(1);
+        return HP_EAGAIN;
+    }
+    auto rollback = [&](hp_status st) {
+        ctx->dev_in_use.fetch_sub(dev_bytes);
+        ctx->inflight.fetch_sub(1);
+        return st;
+    };
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return rollback(fail(ctx));
+
+    hp_event *ev = new (std::nothrow) hp_event();
+    if (!ev) return rollback(HP_ENOMEM);
+    ev->ctx = ctx;
+    ev->E = E;
+    ev->N = N;
+    ev->flags = flags;
+    ev->tag = tag;
+    ev->dev_charge = dev_bytes;
+    if (ctx->dpool.alloc(doff, &ev->dev) != HP_OK) {
+        delete ev;
+        return rollback(HP_ENOMEM);
+    }
+    if (ctx->hpool.alloc(hoff, &ev->host) != HP_OK) {
+        ctx->dpool.free(ev->dev);
+        delete ev;
+        return rollback(HP_ENOMEM);
+    }
+    ev->done = take_cuda_event(ctx);
+    if (!ev->done) {
+        ctx->dpool.free(ev->dev);
+        ctx->hpool.free(ev->host);
+        delete ev;
+        return rollback(fail(ctx));
+    }
+    unsigned char *hb = static_cast<unsigned char *>(ev->host.ptr);
+    unsigned char *hd = static_cast<unsigned char *>(ev->host.dptr);
+    unsigned char *db = static_cast<unsigned char *>(ev->dev.ptr);
+    uint64_t *hoffs = reinterpret_cast<uint64_t *>(hb + h_offs);
+    if (offsets)
+        std::memcpy(hoffs, offsets, 8 * (size_t)(E + 1));
+    else {
+        hoffs[0] = 0;
+        hoffs[1] = N;
+    }
+    const void *src_words = words, *src_mods = mods;
+    bool dev_input = false;
+    if (!nocopy) {
+        if (N) {
+            std::memcpy(hb + h_words, words, 4 * N);
+            std::memcpy(hb + h_mods, mods, 2 * N);
+        }
+        src_words = hb + h_words;
+        src_mods = hb + h_mods;
+    } else if (N) {
+        dev_input = device_pointer(words) && device_pointer(mods);
+    }
+    ev->h_coff = reinterpret_cast<uint64_t *>(hb + h_coff);
+    ev->h_status = reinterpret_cast<int32_t *>(hb + h_status);
+    ev->h_module = reinterpret_cast<uint32_t *>(hb + h_arr[0]);
+    ev->h_id = reinterpret_cast<int32_t *>(hb + h_arr[1]);
+    ev->h_charge = reinterpret_cast<int32_t *>(hb + h_arr[2]);
+    ev->h_npix = reinterpret_cast<int32_t *>(hb + h_arr[3]);
+    ev->h_x = reinterpret_cast<float *>(hb + h_arr[4]);
+    ev->h_y = reinterpret_cast<float *>(hb + h_arr[5]);
+    ev->h_label = labels ? reinterpret_cast<int32_t *>(hb + h_label) : nullptr;
+
+    hp::Launch L;
+    L.g = geometry(ctx);
+    L.E = E;
+    L.N = N;
+    L.offsets = reinterpret_cast<const uint64_t *>(db + d_offs);
+    L.words = dev_input ? static_cast<const uint32_t *>(words) : reinterpret_cast<const uint32_t *>(db + d_words);
+    L.modules = dev_input ? static_cast<const uint16_t *>(mods) : reinterpret_cast<const uint16_t *>(db + d_mods);
+    // cluster outputs go straight to mapped pinned host memory (written once by the kernel)
+    L.out.capacity = N;
+    L.out.module = reinterpret_cast<uint32_t *>(hd + h_arr[0]);
+    L.out.id = reinterpret_cast<int32_t *>(hd + h_arr[1]);
+    L.out.charge = reinterpret_cast<int32_t *>(hd + h_arr[2]);
+    L.out.npix = reinterpret_cast<int32_t *>(hd + h_arr[3]);
+    L.out.x = reinterpret_cast<float *>(hd + h_arr[4]);
+    L.out.y = reinterpret_cast<float *>(hd + h_arr[5]);
+    L.out.cluster_offsets = reinterpret_cast<uint64_t *>(hd + h_coff);
+    L.out.event_status = reinterpret_cast<int32_t *>(hd + h_status);
+    L.out.label = labels ? reinterpret_cast<int32_t *>(db + d_label) : nullptr;
+    hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, &L.ws);
+    L.cc_grid = grid;
+
+    const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
+    cudaStream_t s = ctx->streams[si];
+    ev->stream = s;
+    ev->t_enq = now_ns();
+    {
+        std::lock_guard<std::mutex> g(ctx->live_mu);
+        ctx->live.insert(ev);
+    }
+    uint64_t h2d = 8ull * (E + 1);
+    cudaError_t err = cudaMemcpyAsync(db + d_offs, hoffs, 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess && N && !dev_input) {
+        err = cudaMemcpyAsync(db + d_words, src_words, 4 * N, cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(db + d_mods, src_mods, 2 * N, cudaMemcpyHostToDevice, s);
+        h2d += 6 * N;
+    }
+    uint64_t nk = 0;
+    if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
+    if (err == cudaSuccess && labels && N) {
+        err = cudaMemcpyAsync(ev->h_label, db + d_label, 4 * N, cudaMemcpyDeviceToHost, s);
+        ctx->d2h.fetch_add(4 * N);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev->done, s);
+    if (err == cudaSuccess) err = cudaLaunchHostFunc(s, trampoline, ev);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx); // the context is unusable; its memory is reclaimed by hp_destroy
+    }
+    ctx->h2d.fetch_add(h2d);
+    ctx->kernels.fetch_add(nk);
+    ctx->enqueued.fetch_add(1);
+    *out = ev;
+    return HP_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *hp_status_string(hp_status st)
+{
+    switch (st) {
+    case HP_OK: return "HP_OK";
+    case HP_EAGAIN: return "HP_EAGAIN";
+    case HP_ENOTREADY: return "HP_ENOTREADY";
+    case HP_EINVAL: return "HP_EINVAL";
+    case HP_EBADDIGI: return "HP_EBADDIGI";
+    case HP_EDUP: return "HP_EDUP";
+    case HP_ECAPACITY: return "HP_ECAPACITY";
+    case HP_ENOMEM: return "HP_ENOMEM";
+    case HP_ETIMEOUT: return "HP_ETIMEOUT";
+    case HP_ECUDA: return "HP_ECUDA";
+    }
+    return "HP_UNKNOWN";
+}
+
+hp_status hp_create(const hp_config *cfg, hp_ctx **out)
+{
+    if (!out) return HP_EINVAL;
+    *out = nullptr;
+    hp_status st = validate_config(cfg);
+    if (st != HP_OK) return st;
+    hp_ctx *ctx = new (std::nothrow) hp_ctx();
+    if (!ctx) return HP_ENOMEM;
+    ctx->cfg = *cfg;
+    ctx->cfg.gain = nullptr;
+    ctx->cfg.pedestal = nullptr;
+    ctx->device = cfg->device;
+    auto bail = [&](hp_status s) {
+        if (ctx->d_gain) cudaFree(ctx->d_gain);
+        for (cudaStream_t x : ctx->streams) cudaStreamDestroy(x);
+        delete ctx;
+        cudaGetLastError();
+        return s;
+    };
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(HP_ECUDA);
+    if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
+        return bail(HP_ECUDA);
+    if (hp::init_kernels(cfg->device, cfg->rows, cfg->cols, &ctx->cc_per_sm) != cudaSuccess) return bail(HP_ECUDA);
+    ctx->cc_grid = ctx->sm_count * ctx->cc_per_sm;
+    const size_t M = cfg->n_modules;
+    if (cudaMalloc(&ctx->d_gain, 8 * M) != cudaSuccess) return bail(HP_ENOMEM);
+    ctx->d_ped = ctx->d_gain + M;
+    if (cudaMemcpy(ctx->d_gain, cfg->gain, 4 * M, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_ped, cfg->pedestal, 4 * M, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(HP_ECUDA);
+    const uint32_t ns = cfg->n_streams ? cfg->n_streams : 4;
+    for (uint32_t i = 0; i < ns; ++i) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(HP_ECUDA);
+        ctx->streams.push_back(s);
+    }
+    *out = ctx;
+    return HP_OK;
+}
+
+hp_status hp_destroy(hp_ctx *ctx)
+{
+    if (!ctx) return HP_EINVAL;
+    cudaSetDevice(ctx->device);
+    for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+    {
+        std::lock_guard<std::mutex> g(ctx->ws_mu);
+        for (auto &kv : ctx->stream_ws) {
+            cudaStreamSynchronize(kv.first);
+            cudaFree(kv.second.ptr);
+        }
+        ctx->stream_ws.clear();
+    }
+    std::vector<hp_event *> left;
+    {
+        std::lock_guard<std::mutex> g(ctx->live_mu);
+        left.assign(ctx->live.begin(), ctx->live.end());
+    }
+    for (hp_event *ev : left) destroy_event(ev);
+    ctx->dpool.trim();
+    ctx->hpool.trim();
+    for (cudaEvent_t e : ctx->cev_free) cudaEventDestroy(e);
+    for (auto &r : ctx->prof_used)
+        for (cudaEvent_t e : r.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
+    cudaFree(ctx->d_gain);
+    const bool failed = ctx->failed.load() != 0;
+    delete ctx;
+    cudaGetLastError();
+    return failed ? HP_ECUDA : HP_OK;
+}
+
+hp_status hp_enqueue_event(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_ids, uint64_t n_digis,
+                           uint64_t tag, uint32_t flags, hp_event **out)
+{
+    return enqueue_impl(ctx, 1, nullptr, n_digis, words, module_ids, tag, flags, out);
+}
+
+hp_status hp_enqueue_batch(hp_ctx *ctx, uint32_t n_events, const uint64_t *offsets, const uint32_t *words,
+                           const uint16_t *module_ids, uint64_t tag, uint32_t flags, hp_event **out)
+{
+    if (!offsets) return HP_EINVAL;
+    return enqueue_impl(ctx, n_events, offsets, 0, words, module_ids, tag, flags, out);
+}
+
+hp_status hp_on_complete(hp_event *ev, hp_callback cb, void *user)
+{
+    if (!ev || !cb) return HP_EINVAL;
+    if (ev->cb) return HP_EINVAL;
+    ev->cb = cb;
+    ev->user = user;
+    const uint32_t prev = ev->state.fetch_or(kCbSet, std::memory_order_acq_rel);
+    if (prev & kCbSet) return HP_EINVAL;
+    if (prev & kDone) {
+        cb(user, ev, ev->status);
+        const uint32_t p2 = ev->state.fetch_or(kCbDone, std::memory_order_acq_rel);
+        if (p2 & kReleaseReq) destroy_event(ev);
+    }
+    return HP_OK;
+}
+
+hp_status hp_event_query(hp_event *ev)
+{
+    if (!ev) return HP_EINVAL;
+    if (!(ev->state.load(std::memory_order_acquire) & kDone)) return HP_ENOTREADY;
+    return ev->status;
+}
+
+hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *v)
+{
+    if (!ev || !v) return HP_EINVAL;
+    if (!(ev->state.load(std::memory_order_acquire) & kDone)) return HP_ENOTREADY;
+    v->n_events = ev->E;
+    v->n_digis = ev->N;
+    v->n_clusters = ev->h_coff[ev->E];
+    if (v->n_clusters > ev->N) v->n_clusters = ev->N;
+    v->tag = ev->tag;
+    v->cluster_offsets = ev->h_coff;
+    v->event_status = ev->h_status;
+    v->module = ev->h_module;
+    v->id = ev->h_id;
+    v->charge = ev->h_charge;
+    v->npix = ev->h_npix;
+    v->x = ev->h_x;
+    v->y = ev->h_y;
+    v->label = ev->h_label;
+    return ev->status;
+}
+
+hp_status hp_release_event(hp_event *ev)
+{
+    if (!ev) return HP_EINVAL;
+    const uint32_t prev = ev->state.fetch_or(kReleaseReq, std::memory_order_acq_rel);
+    if (prev & kReleaseReq) return HP_EINVAL;
+    if ((prev & kDone) && (!(prev & kCbSet) || (prev & kCbDone))) destroy_event(ev);
+    return HP_OK;
+}
+
+int hp_event_device(const hp_event *ev) { return ev ? ev->ctx->device : -1; }
+void *hp_event_stream(const hp_event *ev) { return ev ? (void *)ev->stream : nullptr; }
+void *hp_event_cuda_event(const hp_event *ev) { return ev ? (void *)ev->done : nullptr; }
+uint64_t hp_event_latency_ns(const hp_event *ev)
+{
+    if (!ev || !(ev->state.load(std::memory_order_acquire) & kDone)) return 0;
+    return ev->t_done - ev->t_enq;
+}
+
+hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                                const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
+                                void *stream)
+{
+    if (!ctx || !out || !d_offsets || n_events < 1) return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    if (n_digis >= 0xFFFFFFFFull) return HP_EINVAL;
+    if (n_digis > 0 && (!d_words || !d_module_ids)) return HP_EINVAL;
+    if (((uintptr_t)d_words & 3) || ((uintptr_t)d_module_ids & 1) || ((uintptr_t)d_offsets & 7)) return HP_EINVAL;
+    if (!out->module || !out->id || !out->charge || !out->npix || !out->x || !out->y || !out->cluster_offsets ||
+        !out->event_status)
+        return HP_EINVAL;
+    const uint64_t EM = (uint64_t)n_events * ctx->cfg.n_modules;
+    if (EM > (1ull << 31)) return HP_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = cc_grid_for(ctx, n_events);
+    const size_t need = hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
+                                            ctx->cfg.cols, grid, nullptr);
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->ws_mu);
+        Block &b = ctx->stream_ws[s];
+        if (b.bytes < need) {
+            if (b.ptr) {
+                if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ctx);
+                cudaFree(b.ptr);
+                b = Block();
+            }
+            void *p = nullptr;
+            if (cudaMalloc(&p, need) != cudaSuccess) {
+                cudaGetLastError();
+                return HP_ENOMEM;
+            }
+            ctx->ws_mallocs.fetch_add(1);
+            b.ptr = b.dptr = p;
+            b.bytes = need;
+        }
+        base = b.ptr;
+    }
+    hp::Launch L;
+    L.g = geometry(ctx);
+    L.E = n_events;
+    L.N = n_digis;
+    L.offsets = d_offsets;
+    L.words = d_words;
+    L.modules = d_module_ids;
+    L.out.capacity = out->capacity;
+    L.out.module = out->module;
+    L.out.id = out->id;
+    L.out.charge = out->charge;
+    L.out.npix = out->npix;
+    L.out.x = out->x;
+    L.out.y = out->y;
+    L.out.cluster_offsets = out->cluster_offsets;
+    L.out.event_status = out->event_status;
+    L.out.label = out->label;
+    hp::carve_workspace(base, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows, ctx->cfg.cols, grid, &L.ws);
+    L.cc_grid = grid;
+    uint64_t nk = 0;
+    cudaError_t err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx);
+    }
+    ctx->kernels.fetch_add(nk);
+    return HP_OK;
+}
+
+hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)
+{
+    if (!ctx || !o) return HP_EINVAL;
+    o->device_mallocs = ctx->dpool.backend_allocs() + ctx->ws_mallocs.load();
+    o->host_mallocs = ctx->hpool.backend_allocs();
+    o->pool_hits = ctx->dpool.hits() + ctx->hpool.hits();
+    o->device_bytes_in_use = ctx->dev_in_use.load();
+    o->device_bytes_cached = ctx->dpool.total_bytes();
+    o->events_enqueued = ctx->enqueued.load();
+    o->events_completed = ctx->completed.load();
+    o->inflight = ctx->inflight.load();
+    o->h2d_bytes = ctx->h2d.load();
+    o->d2h_bytes = ctx->d2h.load();
+    o->kernel_launches = ctx->kernels.load();
+    return ctx->failed.load() ? HP_ECUDA : HP_OK;
+}
+
+hp_status hp_profile_enable(hp_ctx *ctx, uint32_t max_launches)
+{
+    if (!ctx) return HP_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    ctx->prof_left = max_launches;
+    if (max_launches == 0) {
+        for (auto &r : ctx->prof_used)
+            for (cudaEvent_t e : r.ev) ctx->prof_pool.push_back(e);
+        ctx->prof_used.clear();
+    }
+    return HP_OK;
+}
+
+hp_status hp_profile_read(hp_ctx *ctx, uint32_t cap, const char **names, double *total_ms, uint64_t *launches,
+                          uint32_t *n_kernels)
+{
+    if (!ctx || !n_kernels) return HP_EINVAL;
+    double ms[hp::kNumKernels] = {0};
+    uint64_t cnt[hp::kNumKernels] = {0};
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    for (auto &r : ctx->prof_used) {
+        if (cudaEventSynchronize(r.ev[hp::kNumKernels]) != cudaSuccess) return fail(ctx);
+        for (int i = 0; i < hp::kNumKernels; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.ev[i], r.ev[i + 1]) != cudaSuccess) return fail(ctx);
+            ms[i] += t;
+            cnt[i] += 1;
+        }
+    }
+    *n_kernels = hp::kNumKernels;
+    for (uint32_t i = 0; i < cap && i < (uint32_t)hp::kNumKernels; ++i) {
+        if (names) names[i] = hp::kKernelNames[i];
+        if (total_ms) total_ms[i] = ms[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    return HP_OK;
+}
+
+hp_status hp_debug_fail_allocations(hp_ctx *ctx, uint32_t count)
+{
+    if (!ctx) return HP_EINVAL;
+    ctx->dpool.fail_next(count);
+    return HP_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,361 @@
+"""Python binding of libhp (ctypes, argument marshalling only).
+
+Every step of the reconstruction runs in the library's CUDA kernels; this
+module converts numpy arrays / torch tensors to pointers and back.  There is
+no CPU fallback: importing it without a built ``libhp.so`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhp.so")
+
+HP_OK, HP_EAGAIN, HP_ENOTREADY, HP_EINVAL, HP_EBADDIGI, HP_EDUP, HP_ECAPACITY, HP_ENOMEM, HP_ETIMEOUT, HP_ECUDA = \
+    range(10)
+HP_WANT_LABELS = 0x1
+HP_INPUT_NOCOPY = 0x2
+
+# Every function that include/hp.h declares.
+EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "hp_enqueue_batch", "hp_on_complete",
+           "hp_event_query", "hp_fetch_clusters", "hp_release_event", "hp_event_device", "hp_event_stream",
+           "hp_event_cuda_event", "hp_event_latency_ns", "hp_reconstruct_device", "hp_get_stats",
+           "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations")
+
+
+class HPError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}" if what else status_string(status))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("n_modules", ctypes.c_uint32), ("rows", ctypes.c_uint32),
+                ("cols", ctypes.c_uint32), ("pixel_thr", ctypes.c_int32), ("cluster_thr", ctypes.c_int32),
+                ("gain", ctypes.c_void_p), ("pedestal", ctypes.c_void_p), ("device_budget_bytes", ctypes.c_size_t),
+                ("max_inflight", ctypes.c_uint32), ("n_streams", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class ClustersView(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint32), ("n_digis", ctypes.c_uint64), ("n_clusters", ctypes.c_uint64),
+                ("tag", ctypes.c_uint64), ("cluster_offsets", ctypes.c_void_p), ("event_status", ctypes.c_void_p),
+                ("module", ctypes.c_void_p), ("id", ctypes.c_void_p), ("charge", ctypes.c_void_p),
+                ("npix", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("label", ctypes.c_void_p)]
+
+
+class DeviceClusters(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_uint64), ("module", ctypes.c_void_p), ("id", ctypes.c_void_p),
+                ("charge", ctypes.c_void_p), ("npix", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("cluster_offsets", ctypes.c_void_p), ("event_status", ctypes.c_void_p),
+                ("label", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "device_mallocs", "host_mallocs", "pool_hits", "device_bytes_in_use", "device_bytes_cached",
+        "events_enqueued", "events_completed", "inflight", "h2d_bytes", "d2h_bytes", "kernel_launches")]
+
+
+CALLBACK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int)
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libhp.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"libhp.so not built at {path}; run paper_2004_04334_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P, V, U32, U64, I = ctypes.POINTER, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        sig = {
+            "hp_status_string": (ctypes.c_char_p, [I]),
+            "hp_create": (I, [P(Config), P(V)]),
+            "hp_destroy": (I, [V]),
+            "hp_enqueue_event": (I, [V, V, V, U64, U64, U32, P(V)]),
+            "hp_enqueue_batch": (I, [V, U32, V, V, V, U64, U32, P(V)]),
+            "hp_on_complete": (I, [V, CALLBACK, V]),
+            "hp_event_query": (I, [V]),
+            "hp_fetch_clusters": (I, [V, P(ClustersView)]),
+            "hp_release_event": (I, [V]),
+            "hp_event_device": (I, [V]),
+            "hp_event_stream": (V, [V]),
+            "hp_event_cuda_event": (V, [V]),
+            "hp_event_latency_ns": (U64, [V]),
+            "hp_reconstruct_device": (I, [V, U32, U64, V, V, V, P(DeviceClusters), V]),
+            "hp_get_stats": (I, [V, P(Stats)]),
+            "hp_profile_enable": (I, [V, U32]),
+            "hp_profile_read": (I, [V, U32, P(ctypes.c_char_p), P(ctypes.c_double), P(U64), P(U32)]),
+            "hp_debug_fail_allocations": (I, [V, U32]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_string(st: int) -> str:
+    return load().hp_status_string(st).decode()
+
+
+def _check(st: int, what: str):
+    if st != HP_OK:
+        raise HPError(st, what)
+
+
+@dataclass
+class Result:
+    """Host copy of an event's clusters (see hp_clusters in include/hp.h)."""
+    status: int
+    n_events: int
+    cluster_offsets: np.ndarray
+    event_status: np.ndarray
+    module: np.ndarray
+    id: np.ndarray
+    charge: np.ndarray
+    npix: np.ndarray
+    x: np.ndarray
+    y: np.ndarray
+    label: np.ndarray | None
+    tag: int
+
+    @property
+    def n_clusters(self) -> int:
+        return len(self.id)
+
+    def event(self, e: int) -> "Result":
+        a, b = int(self.cluster_offsets[e]), int(self.cluster_offsets[e + 1])
+        return Result(int(self.event_status[e]), 1, np.array([0, b - a], np.uint64), self.event_status[e:e + 1],
+                      self.module[a:b], self.id[a:b], self.charge[a:b], self.npix[a:b], self.x[a:b], self.y[a:b],
+                      None, self.tag)
+
+
+def _arr(ptr, n, dtype):
+    if n == 0 or not ptr:
+        return np.empty(0, dtype)
+    buf = (ctypes.c_char * (n * np.dtype(dtype).itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dtype, count=n).copy()
+
+
+# Python-side completion dispatch: one C callback for all events.
+_events: dict = {}
+_events_lock = threading.Lock()
+_ids = itertools.count(1)
+
+
+@CALLBACK
+def _on_complete(user, ev, st):
+    with _events_lock:
+        e = _events.get(user)
+    if e is not None:
+        e._complete(st)
+
+
+class Event:
+    """An enqueued event or batch (a Product<T>-like handle)."""
+
+    def __init__(self, ctx: "Context", handle: int, n_events: int, n_digis: int):
+        self._ctx = ctx
+        self._h = ctypes.c_void_p(handle)
+        self.n_events = n_events
+        self.n_digis = n_digis
+        self._done = threading.Event()
+        self._status = None
+        self._callbacks = []
+        self._cb_lock = threading.Lock()
+        self._id = next(_ids)
+        self._released = False
+        with _events_lock:
+            _events[self._id] = self
+        _check(ctx._lib.hp_on_complete(self._h, _on_complete, ctypes.c_void_p(self._id)), "hp_on_complete")
+
+    def _complete(self, st: int):
+        with self._cb_lock:
+            self._status = st
+            cbs = list(self._callbacks)
+        self._done.set()
+        for fn in cbs:
+            fn(self, st)
+
+    def on_complete(self, fn):
+        """fn(event, status) runs on the CUDA host-function thread (or here if done)."""
+        with self._cb_lock:
+            if self._status is None:
+                self._callbacks.append(fn)
+                return
+        fn(self, self._status)
+
+    def query(self) -> int:
+        return self._ctx._lib.hp_event_query(self._h)
+
+    def wait(self, timeout: float | None = None) -> int:
+        if not self._done.wait(timeout):
+            raise TimeoutError("event did not complete")
+        return self._status
+
+    @property
+    def latency_ns(self) -> int:
+        return int(self._ctx._lib.hp_event_latency_ns(self._h))
+
+    @property
+    def device(self) -> int:
+        return int(self._ctx._lib.hp_event_device(self._h))
+
+    @property
+    def stream(self) -> int:
+        return int(self._ctx._lib.hp_event_stream(self._h) or 0)
+
+    def fetch(self) -> Result:
+        v = ClustersView()
+        st = self._ctx._lib.hp_fetch_clusters(self._h, ctypes.byref(v))
+        if st == HP_ENOTREADY:
+            raise HPError(st, "hp_fetch_clusters")
+        E, N, C = v.n_events, v.n_digis, v.n_clusters
+        return Result(st, E, _arr(v.cluster_offsets, E + 1, np.uint64), _arr(v.event_status, E, np.int32),
+                      _arr(v.module, C, np.uint32), _arr(v.id, C, np.int32), _arr(v.charge, C, np.int32),
+                      _arr(v.npix, C, np.int32), _arr(v.x, C, np.float32), _arr(v.y, C, np.float32),
+                      _arr(v.label, N, np.int32) if v.label else None, int(v.tag))
+
+    def release(self):
+        if not self._released:
+            self._released = True
+            _check(self._ctx._lib.hp_release_event(self._h), "hp_release_event")
+            with _events_lock:
+                _events.pop(self._id, None)
+
+
+class Context:
+    """A libhp context on one device (see hp_create)."""
+
+    def __init__(self, n_modules, gain, pedestal, *, device=0, rows=160, cols=416, pixel_thr=1000,
+                 cluster_thr=4000, budget_bytes=0, max_inflight=0, n_streams=0, want_labels=False):
+        self._lib = load()
+        self.n_modules = int(n_modules)
+        self.gain = np.ascontiguousarray(gain, np.int32)
+        self.pedestal = np.ascontiguousarray(pedestal, np.int32)
+        if len(self.gain) != self.n_modules or len(self.pedestal) != self.n_modules:
+            raise ValueError("gain/pedestal must have n_modules entries")
+        cfg = Config(device, self.n_modules, rows, cols, pixel_thr, cluster_thr, self.gain.ctypes.data,
+                     self.pedestal.ctypes.data, budget_bytes, max_inflight, n_streams,
+                     HP_WANT_LABELS if want_labels else 0)
+        h = ctypes.c_void_p()
+        _check(self._lib.hp_create(ctypes.byref(cfg), ctypes.byref(h)), "hp_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if self._h:
+            st = self._lib.hp_destroy(self._h)
+            self._h = None
+            _check(st, "hp_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def enqueue_event(self, words, modules, tag=0, flags=0) -> Event:
+        words = np.ascontiguousarray(words, np.uint32)
+        modules = np.ascontiguousarray(modules, np.uint16)
+        if len(words) != len(modules):
+            raise ValueError("words and modules differ in length")
+        h = ctypes.c_void_p()
+        _check(self._lib.hp_enqueue_event(self._h, words.ctypes.data, modules.ctypes.data, len(words), tag, flags,
+                                          ctypes.byref(h)), "hp_enqueue_event")
+        return Event(self, h.value, 1, len(words))
+
+    def try_enqueue_batch(self, words, modules, offsets, tag=0, flags=0):
+        """As enqueue_batch, but returns (status, event-or-None) instead of raising."""
+        offsets = np.ascontiguousarray(offsets, np.uint64)
+        E = len(offsets) - 1
+        h = ctypes.c_void_p()
+        wp = words.data_ptr() if hasattr(words, "data_ptr") else np.ascontiguousarray(words, np.uint32).ctypes.data
+        mp = modules.data_ptr() if hasattr(modules, "data_ptr") else \
+            np.ascontiguousarray(modules, np.uint16).ctypes.data
+        st = self._lib.hp_enqueue_batch(self._h, E, offsets.ctypes.data, wp, mp, tag, flags, ctypes.byref(h))
+        if st != HP_OK:
+            return st, None
+        return st, Event(self, h.value, E, int(offsets[-1]))
+
+    def enqueue_batch(self, words, modules, offsets, tag=0, flags=0) -> Event:
+        if not hasattr(words, "data_ptr"):
+            words = np.ascontiguousarray(words, np.uint32)
+            modules = np.ascontiguousarray(modules, np.uint16)
+        st, ev = self.try_enqueue_batch(words, modules, offsets, tag, flags)
+        _check(st, "hp_enqueue_batch")
+        return ev
+
+    def reconstruct_device(self, n_events, n_digis, d_offsets, d_words, d_modules, out: "DeviceOutputs",
+                           stream: int = 0):
+        """Queue the device-resident pass (all pointers are device addresses)."""
+        _check(self._lib.hp_reconstruct_device(self._h, n_events, n_digis, d_offsets, d_words, d_modules,
+                                               ctypes.byref(out.struct), ctypes.c_void_p(stream)),
+               "hp_reconstruct_device")
+
+    def debug_fail_allocations(self, count: int):
+        _check(self._lib.hp_debug_fail_allocations(self._h, count), "hp_debug_fail_allocations")
+
+    def profile_enable(self, max_launches: int):
+        """Record CUDA events around each kernel of the next max_launches launches."""
+        _check(self._lib.hp_profile_enable(self._h, max_launches), "hp_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total ms)} of the timed launches (blocks)."""
+        cap = 16
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_uint64 * cap)()
+        n = ctypes.c_uint32()
+        _check(self._lib.hp_profile_read(self._h, cap, names, ms, cnt, ctypes.byref(n)), "hp_profile_read")
+        return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(min(cap, n.value))}
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.hp_get_stats(self._h, ctypes.byref(s)), "hp_get_stats")
+        return {n: int(getattr(s, n)) for n, _ in Stats._fields_}
+
+
+class DeviceOutputs:
+    """Caller-owned device output tensors for Context.reconstruct_device (torch)."""
+
+    def __init__(self, n_events: int, n_digis: int, device, capacity: int | None = None, labels: bool = True):
+        import torch
+        cap = max(1, n_digis if capacity is None else capacity)
+        kw = dict(device=device)
+        self.module = torch.empty(cap, dtype=torch.int32, **kw)
+        self.id = torch.empty(cap, dtype=torch.int32, **kw)
+        self.charge = torch.empty(cap, dtype=torch.int32, **kw)
+        self.npix = torch.empty(cap, dtype=torch.int32, **kw)
+        self.x = torch.empty(cap, dtype=torch.float32, **kw)
+        self.y = torch.empty(cap, dtype=torch.float32, **kw)
+        self.cluster_offsets = torch.empty(n_events + 1, dtype=torch.int64, **kw)
+        self.event_status = torch.empty(n_events, dtype=torch.int32, **kw)
+        self.label = torch.empty(max(1, n_digis), dtype=torch.int32, **kw) if labels else None
+        self.struct = DeviceClusters(cap, self.module.data_ptr(), self.id.data_ptr(), self.charge.data_ptr(),
+                                     self.npix.data_ptr(), self.x.data_ptr(), self.y.data_ptr(),
+                                     self.cluster_offsets.data_ptr(), self.event_status.data_ptr(),
+                                     self.label.data_ptr() if labels else None)
+
+    def to_result(self, n_digis: int) -> Result:
+        offs = self.cluster_offsets.cpu().numpy().astype(np.uint64)
+        C = int(offs[-1])
+        es = self.event_status.cpu().numpy()
+        return Result(int(next((s for s in es if s), 0)), len(es), offs, es,
+                      self.module[:C].cpu().numpy().astype(np.uint32), self.id[:C].cpu().numpy(),
+                      self.charge[:C].cpu().numpy(), self.npix[:C].cpu().numpy(), self.x[:C].cpu().numpy(),
+                      self.y[:C].cpu().numpy(),
+                      self.label[:n_digis].cpu().numpy() if self.label is not None else None, 0)

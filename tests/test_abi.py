@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+include/hp.h declares; argument validation happens before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2004_04334_gb300 import build, hp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hp_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return hp.load()
+
+
+def test_header_declares_binding_exports():
+    assert sorted(hp.EXPORTS) == _declared()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_library_targets_sm103a(lib):
+    # the fatbin carries sm_103a code: the arch string is in the cubin's ELF header notes
+    data = open(hp.LIB_PATH, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_status_strings(lib):
+    for st in range(10):
+        assert hp.status_string(st).startswith("HP_")
+
+
+def _cfg(**kw):
+    gain = np.full(4, 70, np.int32)
+    ped = np.full(4, 100, np.int32)
+    base = dict(device=0, n_modules=4, rows=160, cols=416, pixel_thr=1000, cluster_thr=4000,
+                gain=gain.ctypes.data, pedestal=ped.ctypes.data, device_budget_bytes=0, max_inflight=0,
+                n_streams=0, flags=0)
+    base.update(kw)
+    return hp.Config(**base), (gain, ped)
+
+
+@pytest.mark.parametrize("bad", [dict(n_modules=0), dict(rows=0), dict(rows=257), dict(cols=513),
+                                 dict(pixel_thr=0), dict(gain=None), dict(rows=256, cols=512 + 1)])
+def test_create_rejects_invalid_config_without_cuda(lib, bad):
+    cfg, keep = _cfg(**bad)
+    h = ctypes.c_void_p()
+    assert lib.hp_create(ctypes.byref(cfg), ctypes.byref(h)) == hp.HP_EINVAL
+    assert not h.value
+
+
+def test_create_rejects_out_of_domain_calibration(lib):
+    gain = np.array([70, 127, 70, 70], np.int32)  # 255 * 127 > INT32_MAX / 66560
+    ped = np.zeros(4, np.int32)
+    cfg, _ = _cfg(gain=gain.ctypes.data, pedestal=ped.ctypes.data)
+    h = ctypes.c_void_p()
+    assert lib.hp_create(ctypes.byref(cfg), ctypes.byref(h)) == hp.HP_EINVAL
+
+
+def test_null_arguments(lib):
+    assert lib.hp_destroy(None) == hp.HP_EINVAL
+    assert lib.hp_enqueue_event(None, None, None, 0, 0, 0, None) == hp.HP_EINVAL
+    assert lib.hp_release_event(None) == hp.HP_EINVAL
+    assert lib.hp_event_query(None) == hp.HP_EINVAL
+    assert lib.hp_get_stats(None, None) == hp.HP_EINVAL
