@@ -55,6 +55,8 @@ def _args():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--per-event-steps", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--device-only", action="store_true",
+                   help="only the device-resident timed loop (for profiler captures)")
     return p.parse_args()
 
 
@@ -242,7 +244,7 @@ def run_ours(a):
     E, N, M = w.n_events, w.n_digis, w.n_modules
 
     cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
+    if rank == 0 and not a.no_cpu_baseline and not a.device_only:
         ev_s, md_s, dt, cores = cpu_oracle(w)
         cpu = {"value": ev_s, "unit": "events/s", "cores": cores, "kind": "oracle",
                "sample": f"all {E} events ({N} digis) of the {a.workload} workload, one pass, "
@@ -305,6 +307,48 @@ def run_ours(a):
     path_bytes = algorithmic_bytes(N, E, M, n_clusters)
     shares = {k: round(v[1] / max(1e-12, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
 
+    e2e = per_event = None
+    if not a.device_only:
+        e2e, per_event = _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world)
+    ctx.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * t_dev / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {E} events of uneven size (10k-200k digis), {M} modules "
+                                   f"of 160x416, {N} digis, labels on",
+                       "events_per_step": E, "digis_per_step": N, "clusters_per_step": n_clusters,
+                       "l2": "inputs (6 B/digi) and working set larger than the 129 MB L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "mdigis_per_s": mdigis,
+            "path_algorithmic_GBps": path_bytes * a.steps / t_dev / 1e9,
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": _traffic(name, N), "algorithmic_bytes_per_launch": kb,
+                         "mean_launch_ms": per_launch_s * 1000, "kernel_shares": shares},
+            "e2e": e2e,
+            "per_event": per_event,
+            "batched_vs_per_event": value / per_event["value"] if per_event else None,
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
+    import torch
+
+    from paper_2004_04334_gb300 import hp
+
+    E, N = w.n_events, w.n_digis
+    local = dev.index
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     # end to end through the public enqueue API: pinned host inputs, H2D, pass, results in host memory
     pw = torch.from_numpy(w.words.view(np.int32)).pin_memory()
     pm = torch.from_numpy(w.modules.view(np.int16)).pin_memory()
@@ -372,34 +416,7 @@ def run_ours(a):
                  "e2e_latency_ms_p50": float(np.percentile(lat, 50)),
                  "e2e_latency_ms_p99": float(np.percentile(lat, 99))}
     pctx.close()
-    ctx.close()
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": 1000 * t_dev / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
-            "config": {"workload": f"{a.workload}: {E} events of uneven size (10k-200k digis), {M} modules "
-                                   f"of 160x416, {N} digis, labels on",
-                       "events_per_step": E, "digis_per_step": N, "clusters_per_step": n_clusters,
-                       "l2": "inputs (6 B/digi) and working set larger than the 129 MB L2; no flush",
-                       "parallelism": f"replicas x{world}"},
-            "mdigis_per_s": mdigis,
-            "path_algorithmic_GBps": path_bytes * a.steps / t_dev / 1e9,
-            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": _traffic(name, N), "algorithmic_bytes_per_launch": kb,
-                         "mean_launch_ms": per_launch_s * 1000, "kernel_shares": shares},
-            "e2e": e2e,
-            "per_event": per_event,
-            "batched_vs_per_event": value / per_event["value"],
-            "gpu_launches": gpu_launches,
-            "clocks": clk,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return e2e, per_event
 
 
 def main():

@@ -15,7 +15,7 @@ constexpr uint32_t kErrTimeout = 8u;
 
 // Tuning constants of the kernels.
 constexpr int kChunk = 4096;         // digis per histogram / scatter block
-constexpr int kHistThreads = 256;
+constexpr int kHistThreads = 512;
 constexpr int kHistCap = 4096;       // (event, module) bins a block can histogram in shared memory
 constexpr int kCCThreads = 256;      // threads of a clustering block
 constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue ticket, one per warp

@@ -148,43 +148,122 @@ __device__ __forceinline__ ItemCtx make_item(const Launch &L, uint64_t item, uin
     return it;
 }
 
-// ---------------------------------------------------------------- histogram
+// ---------------------------------------------------------------- histogram / scatter
+
+// Thread t of a histogram/scatter block owns the kPerThread consecutive digis
+// [c0 + kPerThread * t, ...) of the block's chunk; module ids and words are
+// read with 16-byte vector loads when the arrays are 16-byte aligned.
+constexpr int kPerThread = kChunk / kHistThreads;
+static_assert(kPerThread == 8, "vector loads below assume 8 digis per thread");
+
+__device__ __forceinline__ void load_modules(const Launch &L, uint64_t k0, uint64_t c1, uint32_t m[kPerThread])
+{
+    if (((reinterpret_cast<uintptr_t>(L.modules) & 15) == 0) && k0 + kPerThread <= c1) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(L.modules + k0);
+        m[0] = a.x & 0xFFFFu, m[1] = a.x >> 16, m[2] = a.y & 0xFFFFu, m[3] = a.y >> 16;
+        m[4] = a.z & 0xFFFFu, m[5] = a.z >> 16, m[6] = a.w & 0xFFFFu, m[7] = a.w >> 16;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) m[j] = k0 + j < c1 ? (uint32_t)L.modules[k0 + j] : 0xFFFFFFFFu;
+    }
+}
+
+__device__ __forceinline__ void load_words(const Launch &L, uint64_t k0, uint64_t c1, uint32_t w[kPerThread])
+{
+    if (((reinterpret_cast<uintptr_t>(L.words) & 15) == 0) && k0 + kPerThread <= c1) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(L.words + k0);
+        const uint4 b = *reinterpret_cast<const uint4 *>(L.words + k0 + 4);
+        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w, w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) w[j] = k0 + j < c1 ? L.words[k0 + j] : 0u;
+    }
+}
+
+// Event of each of the thread's digis (events are contiguous, so walk forward
+// from a binary search for the first one).
+__device__ __forceinline__ void digi_events(const Launch &L, uint32_t ef, uint32_t el, uint64_t k0,
+                                            uint32_t e_of[kPerThread])
+{
+    uint32_t e = ef == el ? ef : find_event(L.offsets, ef, el, k0);
+    uint64_t next = e < el ? L.offsets[e + 1] : ~0ull;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        while (k0 + j >= next) {
+            ++e;
+            next = e < el ? L.offsets[e + 1] : ~0ull;
+        }
+        e_of[j] = e;
+    }
+}
+
+// bins[key] += 1 for every active lane with one atomic per distinct key of
+// the warp; returns the old bin value plus the lane's rank among its peers.
+// Must be called by all 32 lanes.
+__device__ __forceinline__ uint32_t warp_bin_add(uint32_t *bins, uint32_t key, bool active)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t k = active ? key : 0xFFFFFFFFu - lane;
+    const uint32_t peers = __match_any_sync(kFull, k);
+    const uint32_t leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (active && lane == leader) base = atomicAdd(&bins[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+struct ChunkInfo {
+    uint64_t c0, c1, keybase;
+    uint32_t ef, el, nkeys;
+    bool use_sh;
+};
+
+__device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint32_t *s_ev)
+{
+    ChunkInfo ci;
+    ci.c0 = (uint64_t)blockIdx.x * kChunk;
+    ci.c1 = min(L.N, ci.c0 + (uint64_t)kChunk);
+    if (threadIdx.x == 0) {
+        s_ev[0] = find_event(L.offsets, 0, L.E - 1, ci.c0);
+        s_ev[1] = find_event(L.offsets, s_ev[0], L.E - 1, ci.c1 - 1);
+    }
+    __syncthreads();
+    ci.ef = s_ev[0];
+    ci.el = s_ev[1];
+    const uint64_t nk = (uint64_t)(ci.el - ci.ef + 1) * L.g.M;
+    ci.use_sh = nk <= (uint64_t)kHistCap;
+    ci.nkeys = ci.use_sh ? (uint32_t)nk : 0u;
+    ci.keybase = (uint64_t)ci.ef * L.g.M;
+    return ci;
+}
 
 __global__ void __launch_bounds__(kHistThreads) hist_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
-    __shared__ uint32_t s_ef, s_el;
-    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk;
-    const uint64_t c1 = min(L.N, c0 + (uint64_t)kChunk);
-    if (threadIdx.x == 0) {
-        s_ef = find_event(L.offsets, 0, L.E - 1, c0);
-        s_el = find_event(L.offsets, s_ef, L.E - 1, c1 - 1);
-    }
+    __shared__ uint32_t s_ev[2];
+    const ChunkInfo ci = chunk_info(L, s_ev);
+    const uint32_t M = L.g.M;
+    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) sh[i] = 0;
     __syncthreads();
-    const uint32_t ef = s_ef, el = s_el, M = L.g.M;
-    const uint64_t nkeys64 = (uint64_t)(el - ef + 1) * M;
-    const bool use_sh = nkeys64 <= (uint64_t)kHistCap;
-    const uint32_t nkeys = use_sh ? (uint32_t)nkeys64 : 0u;
-    const uint64_t keybase = (uint64_t)ef * M;
-    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) sh[i] = 0;
-    __syncthreads();
-    for (uint64_t k = c0 + threadIdx.x; k < c1; k += kHistThreads) {
-        const uint32_t e = ef == el ? ef : find_event(L.offsets, ef, el, k);
-        const uint32_t m = L.modules[k];
-        if (m >= M) {
-            atomicOr(&L.ws.event_err[e], kErrBadDigi);
-            continue;
-        }
-        const uint64_t key = (uint64_t)e * M + m;
-        if (use_sh)
-            atomicAdd(&sh[key - keybase], 1u);
-        else
+    const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
+    uint32_t m[kPerThread], e_of[kPerThread];
+    load_modules(L, k0, ci.c1, m);
+    digi_events(L, ci.ef, ci.el, k0, e_of);
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const bool present = k0 + j < ci.c1;
+        const bool ok = present && m[j] < M;
+        if (present && !ok) atomicOr(&L.ws.event_err[e_of[j]], kErrBadDigi);
+        const uint64_t key = (uint64_t)e_of[j] * M + (ok ? m[j] : 0u);
+        if (ci.use_sh)
+            warp_bin_add(sh, (uint32_t)(key - ci.keybase), ok);
+        else if (ok)
             atomicAdd(&L.ws.count[key], 1u);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) {
+    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
         const uint32_t v = sh[i];
-        if (v) atomicAdd(&L.ws.count[keybase + i], v);
+        if (v) atomicAdd(&L.ws.count[ci.keybase + i], v);
     }
 }
 
@@ -208,64 +287,44 @@ __global__ void __launch_bounds__(256) scan_kernel(const Launch L)
     }
 }
 
-// ---------------------------------------------------------------- scatter
-
 __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
     uint32_t *cnt = sh;
     uint32_t *bas = sh + kHistCap;
-    __shared__ uint32_t s_ef, s_el;
-    constexpr int PER = kChunk / kHistThreads;
-    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk;
-    const uint64_t c1 = min(L.N, c0 + (uint64_t)kChunk);
-    if (threadIdx.x == 0) {
-        s_ef = find_event(L.offsets, 0, L.E - 1, c0);
-        s_el = find_event(L.offsets, s_ef, L.E - 1, c1 - 1);
-    }
+    __shared__ uint32_t s_ev[2];
+    const ChunkInfo ci = chunk_info(L, s_ev);
+    const uint32_t M = L.g.M;
+    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) cnt[i] = 0;
     __syncthreads();
-    const uint32_t ef = s_ef, el = s_el, M = L.g.M;
-    const uint64_t nkeys64 = (uint64_t)(el - ef + 1) * M;
-    const bool use_sh = nkeys64 <= (uint64_t)kHistCap;
-    const uint32_t nkeys = use_sh ? (uint32_t)nkeys64 : 0u;
-    const uint64_t keybase = (uint64_t)ef * M;
-    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) cnt[i] = 0;
-    __syncthreads();
-    uint32_t pos[PER], keyl[PER], evt[PER];
+    const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
+    uint32_t m[kPerThread], e_of[kPerThread], w[kPerThread], rank[kPerThread];
+    load_modules(L, k0, ci.c1, m);
+    load_words(L, k0, ci.c1, w);
+    digi_events(L, ci.ef, ci.el, k0, e_of);
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const uint64_t k = c0 + threadIdx.x + (uint64_t)j * kHistThreads;
-        pos[j] = 0xFFFFFFFFu;
-        keyl[j] = 0;
-        evt[j] = ef;
-        if (k < c1) {
-            const uint32_t e = ef == el ? ef : find_event(L.offsets, ef, el, k);
-            const uint32_t m = L.modules[k];
-            evt[j] = e;
-            if (m < M) {
-                const uint64_t key = (uint64_t)e * M + m;
-                if (use_sh) {
-                    keyl[j] = (uint32_t)(key - keybase);
-                    pos[j] = atomicAdd(&cnt[keyl[j]], 1u);
-                } else {
-                    pos[j] = atomicAdd(&L.ws.cursor[key], 1u);
-                }
-            }
-        }
+    for (int j = 0; j < kPerThread; ++j) {
+        const bool ok = k0 + j < ci.c1 && m[j] < M;
+        const uint64_t key = (uint64_t)e_of[j] * M + (ok ? m[j] : 0u);
+        if (ci.use_sh)
+            rank[j] = warp_bin_add(cnt, (uint32_t)(key - ci.keybase), ok);
+        else
+            rank[j] = ok ? atomicAdd(&L.ws.cursor[key], 1u) : 0u;
+        if (!ok) m[j] = 0xFFFFFFFFu;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nkeys; i += kHistThreads) {
+    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
         const uint32_t v = cnt[i];
-        if (v) bas[i] = atomicAdd(&L.ws.cursor[keybase + i], v);
+        if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        if (pos[j] == 0xFFFFFFFFu) continue;
-        const uint64_t k = c0 + threadIdx.x + (uint64_t)j * kHistThreads;
-        const uint32_t p = use_sh ? bas[keyl[j]] + pos[j] : pos[j];
-        L.ws.bucket_w[p] = L.words[k];
-        L.ws.bucket_i[p] = (uint32_t)(k - L.offsets[evt[j]]);
+    for (int j = 0; j < kPerThread; ++j) {
+        if (m[j] == 0xFFFFFFFFu) continue;
+        const uint64_t key = (uint64_t)e_of[j] * M + m[j];
+        const uint32_t p = ci.use_sh ? bas[key - ci.keybase] + rank[j] : rank[j];
+        L.ws.bucket_w[p] = w[j];
+        L.ws.bucket_i[p] = (uint32_t)(k0 + j - L.offsets[e_of[j]]);
     }
 }
 
@@ -391,6 +450,162 @@ __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
     }
     if (it.label_e && have) it.label_e[idx] = !surv ? -1 : (kept ? lab : -2);
     return __popc(kl);
+}
+
+// One item of at most kSmemSlots digis clustered by the whole block on
+// shared memory (see the file comment).  Each thread keeps its kPer digis
+// (word, in-event index, slot) in registers across the phases.  Returns the
+// number of kept clusters (uniform over the block).
+constexpr int kPer = kSmemSlots / kCCThreads;
+
+__device__ uint32_t block_item_small(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits,
+                                     uint32_t *spre, const SlotArrays &sa, BlockShared &bs)
+{
+    const uint32_t R = L.g.R, C = L.g.C, nwords = (R * C + 31) >> 5;
+    const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t *bw = L.ws.bucket_w + it.b;
+    const uint32_t *bi = L.ws.bucket_i + it.b;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+    uint32_t w[kPer], idx[kPer], slot[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t k = tid + j * kCCThreads;
+        w[j] = k < it.n ? bw[k] : 0u;
+        idx[j] = k < it.n ? bi[k] : kNone;
+    }
+    for (uint32_t i = tid; i < nwords; i += kCCThreads) {
+        abits[i] = 0;
+        sbits[i] = 0;
+    }
+    if (tid == 0) bs.flag = 0;
+    __syncthreads();
+
+    // occupancy and survivor bitmaps; validation and duplicate detection
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        slot[j] = kNone;
+        if (idx[j] == kNone) continue;
+        const uint32_t r = w[j] & 0xFFu, c = (w[j] >> 8) & 0x1FFu, adc = (w[j] >> 17) & 0xFFu;
+        if (r >= R || c >= C || adc == 0 || (w[j] >> 25) != 0) {
+            atomicOr(&bs.flag, kErrBadDigi);
+            continue;
+        }
+        const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
+        if (atomicOr(&abits[lin >> 5], bit) & bit) atomicOr(&bs.flag, kErrDup);
+        if ((int32_t)adc * it.gain - it.ped >= thr) {
+            atomicOr(&sbits[lin >> 5], bit);
+            slot[j] = lin; // provisional: the linear index until ranks exist
+        }
+    }
+    __syncthreads();
+    const uint32_t flag = bs.flag;
+    if (flag) {
+        if (tid == 0) atomicOr(it.err_e, flag);
+        __syncthreads();
+        return 0;
+    }
+
+    // exclusive prefix popcount of the survivor bitmap -> dense slots
+    const uint32_t per = (nwords + kCCThreads - 1) / kCCThreads;
+    const uint32_t w0 = min(nwords, tid * per), w1 = min(nwords, w0 + per);
+    uint32_t local = 0;
+    for (uint32_t i = w0; i < w1; ++i) local += __popc(sbits[i]);
+    uint32_t S;
+    uint32_t run = block_exclusive_scan<kCCThreads>(local, bs.scan_tmp, &S);
+    for (uint32_t i = w0; i < w1; ++i) {
+        spre[i] = run;
+        run += __popc(sbits[i]);
+    }
+    __syncthreads();
+
+    uint32_t lin_of[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        lin_of[j] = slot[j];
+        if (slot[j] == kNone) continue;
+        const uint32_t s = rank_of(sbits, spre, lin_of[j]);
+        slot[j] = s;
+        sa.parent[s] = s;
+        sa.slin[s] = lin_of[j];
+        sa.qn[s] = 0;
+        sa.sr[s] = 0;
+        sa.sc[s] = 0;
+    }
+    __syncthreads();
+
+    // union with the surviving backward neighbours
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (slot[j] == kNone) continue;
+        const uint32_t lin = lin_of[j], s = slot[j];
+        const uint32_t r = w[j] & 0xFFu, c = (w[j] >> 8) & 0x1FFu;
+        if (c > 0 && has_bit(sbits, lin - 1)) uf_union(sa.parent, s, s - 1); // left neighbour is the previous slot
+        if (r > 0) {
+            const uint32_t up = lin - C;
+            if (c > 0 && has_bit(sbits, up - 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up - 1));
+            if (has_bit(sbits, up)) uf_union(sa.parent, s, rank_of(sbits, spre, up));
+            if (c + 1 < C && has_bit(sbits, up + 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up + 1));
+        }
+    }
+    __syncthreads();
+
+    // charge, size and moments about the root pixel
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (slot[j] == kNone) continue;
+        const uint32_t s = slot[j];
+        const uint32_t root = uf_find(sa.parent, s);
+        sa.parent[s] = root;
+        const uint32_t rl = sa.slin[root];
+        const int32_t rr = (int32_t)(rl / C), rc = (int32_t)(rl - (uint32_t)rr * C);
+        const int32_t r = (int32_t)(w[j] & 0xFFu), c = (int32_t)((w[j] >> 8) & 0x1FFu);
+        const int32_t q = (int32_t)((w[j] >> 17) & 0xFFu) * it.gain - it.ped;
+        atomicAdd(&sa.qn[root], ((unsigned long long)q << 17) | 1ull);
+        atomicAdd(&sa.sr[root], (unsigned long long)(long long)(q * (r - rr)));
+        atomicAdd(&sa.sc[root], (unsigned long long)(long long)(q * (c - rc)));
+    }
+    __syncthreads();
+
+    if (it.label_e) {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            if (idx[j] == kNone) continue;
+            int32_t lab = -1;
+            if (slot[j] != kNone) {
+                const uint32_t root = sa.parent[slot[j]];
+                lab = (int32_t)(sa.qn[root] >> 17) >= cthr ? (int32_t)sa.slin[root] : -2;
+            }
+            it.label_e[idx[j]] = lab;
+        }
+    }
+
+    // kept roots in slot order -> ordinals -> staging
+    const uint32_t sper = (S + kCCThreads - 1) / kCCThreads;
+    const uint32_t s0 = min(S, tid * sper), s1 = min(S, s0 + sper);
+    uint32_t cnt = 0;
+    for (uint32_t s = s0; s < s1; ++s)
+        if (sa.parent[s] == s && (int32_t)(sa.qn[s] >> 17) >= cthr) ++cnt;
+    uint32_t K;
+    uint32_t ord = block_exclusive_scan<kCCThreads>(cnt, bs.scan_tmp, &K);
+    for (uint32_t s = s0; s < s1; ++s) {
+        if (sa.parent[s] != s) continue;
+        const unsigned long long qn = sa.qn[s];
+        const int32_t Q = (int32_t)(qn >> 17);
+        if (Q < cthr) continue;
+        const uint32_t id = sa.slin[s];
+        const int32_t rr = (int32_t)(id / C), rc = (int32_t)(id - (uint32_t)rr * C);
+        StagedCluster o;
+        o.id = (int32_t)id;
+        o.charge = Q;
+        o.npix = (int32_t)(qn & 0x1FFFFull);
+        o.x = centroid(rr, (long long)sa.sr[s], Q);
+        o.y = centroid(rc, (long long)sa.sc[s], Q);
+        o.pad = 0;
+        L.ws.staging[it.b + ord++] = o;
+    }
+    return K;
 }
 
 // One item clustered by the whole block (see the file comment).  kBig: the
@@ -535,37 +750,52 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     return K;
 }
 
-// Decoupled look-back over tickets: publish this ticket's aggregate, sum the
-// predecessors' values back to the first inclusive prefix, publish ours.
-// Every predecessor ticket is held by a running block that publishes its
-// aggregate without waiting, so the wait ends; it is bounded regardless.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Decoupled look-back over tickets, run by one full warp: publish this
+// ticket's aggregate, then read the 32 preceding tickets at once; the
+// exclusive prefix is the sum of the values from the nearest inclusive prefix
+// onwards (or of the whole window, which then slides back by 32).  Every
+// predecessor ticket is held by a running block that publishes its aggregate
+// without waiting, so the wait ends; it is bounded regardless (kErrTimeout).
 __device__ unsigned long long chain_lookback(unsigned long long *chain, uint64_t g, unsigned long long agg,
                                              uint32_t *launch_err)
 {
     const unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62, kMask = kAgg - 1;
+    const uint32_t lane = threadIdx.x & 31;
     if (g == 0) {
-        st_release(&chain[0], kInc | agg);
+        if (lane == 0) st_release(&chain[0], kInc | agg);
         return 0;
     }
-    st_release(&chain[g], kAgg | agg);
+    if (lane == 0) st_release(&chain[g], kAgg | agg);
     unsigned long long excl = 0;
-    long long j = (long long)g - 1;
+    long long end = (long long)g - 1;
     uint32_t spins = 0;
-    while (j >= 0) {
-        const unsigned long long v = ld_acquire(&chain[j]);
-        if ((v >> 62) == 0) {
+    for (;;) {
+        const long long j = end - (31 - (long long)lane);
+        const unsigned long long v = j >= 0 ? ld_acquire(&chain[j]) : kInc;
+        const uint32_t flag = (uint32_t)(v >> 62);
+        const uint32_t inc = __ballot_sync(kFull, flag == 2);
+        const int top = inc ? 31 - __clz(inc) : -1;
+        const uint32_t waiting = __ballot_sync(kFull, flag == 0 && (int)lane > top);
+        if (waiting) {
             if (++spins > kSpinLimit) {
-                atomicOr(launch_err, kErrTimeout);
+                if (lane == 0) atomicOr(launch_err, kErrTimeout);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
             continue;
         }
-        excl += v & kMask;
-        if ((v >> 62) == 2) break;
-        --j;
+        excl += warp_sum_u64((int)lane >= top ? (v & kMask) : 0ull);
+        if (inc) break;
+        end -= 32;
     }
-    st_release(&chain[g], kInc | (excl + agg));
+    if (lane == 0) st_release(&chain[g], kInc | (excl + agg));
     return excl;
 }
 
@@ -625,7 +855,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
             const ItemCtx it = make_item(L, item0 + i, s_b[i], n);
             uint32_t K;
             if (n <= (uint32_t)kSmemSlots) {
-                K = block_item<false>(L, it, abits, sbits, spre, sm, bs);
+                K = block_item_small(L, it, abits, sbits, spre, sm, bs);
             } else {
                 if (tid == 0) {
                     bs.big_off = 0;
@@ -661,14 +891,15 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
         }
 
         // ordered write of the ticket's clusters
-        if (tid == 0) {
+        if (tid < 32) {
             uint32_t p = 0;
             for (int i = 0; i < kGroup; ++i) {
-                s_pref[i] = p;
+                if (tid == 0) s_pref[i] = p;
                 p += s_K[i];
             }
-            s_pref[kGroup] = p;
-            s_prefix = chain_lookback(L.ws.chain, g, p, &L.ws.ctl[1]);
+            if (tid == 0) s_pref[kGroup] = p;
+            const unsigned long long pre = chain_lookback(L.ws.chain, g, p, &L.ws.ctl[1]);
+            if (tid == 0) s_prefix = pre;
         }
         __syncthreads();
         const unsigned long long P = s_prefix;
