@@ -20,7 +20,7 @@ constexpr int kHistCap = 4096;       // (event, module) bins a block can histogr
 constexpr int kCCThreads = 256;      // threads of a clustering block
 constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue ticket, one per warp
 constexpr int kWarpMax = 32;         // items with at most this many digis are clustered by one warp
-constexpr int kSmemSlots = 2048;     // surviving pixels a block clusters in shared memory
+constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory
 
 // A cluster parked between the clustering phase and the ordered write.
 struct StagedCluster {
@@ -60,6 +60,7 @@ struct Workspace {
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event
     StagedCluster *staging; // [N]
+    unsigned long long *exact; // [cc_grid * 2 * kSmemSlots] 64-bit moments of heavy clusters
     unsigned char *big;   // scratch of items too large for shared memory
     uint64_t big_slots;   // slots per block (slab mode) or in total (arena mode)
     int big_arena;        // 1: bump-allocated arena, 0: one slab per block
@@ -77,8 +78,9 @@ struct Launch {
     int cc_grid;             // blocks of the clustering kernel
 };
 
-// Bytes of one big-tier slot: parent, linear index, three 64-bit accumulators.
-constexpr size_t kBigSlotBytes = 4 + 4 + 8 * 3;
+// Bytes of one global-tier slot: (Q, npix), two 64-bit and two 32-bit moments,
+// parent, padded to 8-byte multiples so every slot range stays 8-byte aligned.
+constexpr size_t kBigSlotBytes = 8 + 16 + 8 + 4 + 4;
 
 size_t cc_smem_bytes(uint32_t R, uint32_t C);
 // Lay out the workspace for (E, M, N) in `base` (nullptr: only compute size).

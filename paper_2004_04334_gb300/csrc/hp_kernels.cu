@@ -45,25 +45,11 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kSpinLimit = 1u << 24;
 
-struct BlockShared {
-    uint32_t flag;
-    uint32_t scan_tmp[kCCThreads / 32 + 1];
-    uint32_t big_off;
-};
-
 struct ItemCtx {
     uint32_t e, m, b, n;
     int32_t gain, ped;
     int32_t *label_e;  // label of the event's first digi, or null
     uint32_t *err_e;   // the event's error bits
-};
-
-struct SlotArrays {
-    unsigned long long *qn; // (Q << 17) + npix of a root slot
-    unsigned long long *sr; // sum q * (row - root row)
-    unsigned long long *sc; // sum q * (col - root col), two's complement
-    uint32_t *parent;
-    uint32_t *slin;         // linear pixel index of a slot
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
@@ -330,6 +316,31 @@ __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
 
 // ---------------------------------------------------------------- clustering
 
+// After the unions, a root's parent entry holds kMark | its linear pixel index.
+constexpr uint32_t kMark = 0x80000000u;
+// Moments accumulate in 32 bits relative to the root pixel (|drow| < 256,
+// |dcol| < 512): they cannot overflow while Q <= INT32_MAX / 512.  Items with
+// a heavier cluster recompute the moments in 64 bits.
+constexpr int32_t kQSafe32 = 0x7FFFFFFF / 512;
+constexpr int kPer = kSmemSlots / kCCThreads; // digis per thread in the shared-memory tier
+constexpr int kRing = 16;                    // tickets a block may hold before their prefix is known
+
+// Per-item arrays of the block tier: shared memory, or global scratch for
+// items beyond the shared-memory capacity.
+struct Tile {
+    uint32_t *parent;          // union-find parent of a slot; kMark | lin for roots after marking
+    unsigned long long *qn;    // root: (Q << 17) + npix
+    int2 *m;                   // root: sum q*(row - root row), sum q*(col - root col)
+    unsigned long long *exact; // root: the same two moments in 64 bits (heavy clusters only)
+};
+
+struct BlockShared {
+    uint32_t flag;
+    uint32_t heavy;
+    uint32_t big_off;
+    uint32_t scan_tmp[kCCThreads / 32 + 1];
+};
+
 __device__ __forceinline__ uint32_t uf_find(const uint32_t *parent, uint32_t x)
 {
     const volatile uint32_t *p = parent;
@@ -452,195 +463,67 @@ __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
     return __popc(kl);
 }
 
-// One item of at most kSmemSlots digis clustered by the whole block on
-// shared memory (see the file comment).  Each thread keeps its kPer digis
-// (word, in-event index, slot) in registers across the phases.  Returns the
-// number of kept clusters (uniform over the block).
-constexpr int kPer = kSmemSlots / kCCThreads;
-
-__device__ uint32_t block_item_small(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits,
-                                     uint32_t *spre, const SlotArrays &sa, BlockShared &bs)
+// Apply f(k, word) to every digi of the item owned by this thread: from the
+// register copy (shared-memory tier) or from the bucket (global tier).
+template <bool kBig, class F>
+__device__ __forceinline__ void for_digis(const uint32_t (&wreg)[kPer], const uint32_t *bw, uint32_t n, F &&f)
 {
-    const uint32_t R = L.g.R, C = L.g.C, nwords = (R * C + 31) >> 5;
-    const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
-    const uint32_t tid = threadIdx.x;
-    const uint32_t *bw = L.ws.bucket_w + it.b;
-    const uint32_t *bi = L.ws.bucket_i + it.b;
-    constexpr uint32_t kNone = 0xFFFFFFFFu;
-
-    uint32_t w[kPer], idx[kPer], slot[kPer];
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const uint32_t k = tid + j * kCCThreads;
-        w[j] = k < it.n ? bw[k] : 0u;
-        idx[j] = k < it.n ? bi[k] : kNone;
-    }
-    for (uint32_t i = tid; i < nwords; i += kCCThreads) {
-        abits[i] = 0;
-        sbits[i] = 0;
-    }
-    if (tid == 0) bs.flag = 0;
-    __syncthreads();
-
-    // occupancy and survivor bitmaps; validation and duplicate detection
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        slot[j] = kNone;
-        if (idx[j] == kNone) continue;
-        const uint32_t r = w[j] & 0xFFu, c = (w[j] >> 8) & 0x1FFu, adc = (w[j] >> 17) & 0xFFu;
-        if (r >= R || c >= C || adc == 0 || (w[j] >> 25) != 0) {
-            atomicOr(&bs.flag, kErrBadDigi);
-            continue;
-        }
-        const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
-        if (atomicOr(&abits[lin >> 5], bit) & bit) atomicOr(&bs.flag, kErrDup);
-        if ((int32_t)adc * it.gain - it.ped >= thr) {
-            atomicOr(&sbits[lin >> 5], bit);
-            slot[j] = lin; // provisional: the linear index until ranks exist
-        }
-    }
-    __syncthreads();
-    const uint32_t flag = bs.flag;
-    if (flag) {
-        if (tid == 0) atomicOr(it.err_e, flag);
-        __syncthreads();
-        return 0;
-    }
-
-    // exclusive prefix popcount of the survivor bitmap -> dense slots
-    const uint32_t per = (nwords + kCCThreads - 1) / kCCThreads;
-    const uint32_t w0 = min(nwords, tid * per), w1 = min(nwords, w0 + per);
-    uint32_t local = 0;
-    for (uint32_t i = w0; i < w1; ++i) local += __popc(sbits[i]);
-    uint32_t S;
-    uint32_t run = block_exclusive_scan<kCCThreads>(local, bs.scan_tmp, &S);
-    for (uint32_t i = w0; i < w1; ++i) {
-        spre[i] = run;
-        run += __popc(sbits[i]);
-    }
-    __syncthreads();
-
-    uint32_t lin_of[kPer];
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        lin_of[j] = slot[j];
-        if (slot[j] == kNone) continue;
-        const uint32_t s = rank_of(sbits, spre, lin_of[j]);
-        slot[j] = s;
-        sa.parent[s] = s;
-        sa.slin[s] = lin_of[j];
-        sa.qn[s] = 0;
-        sa.sr[s] = 0;
-        sa.sc[s] = 0;
-    }
-    __syncthreads();
-
-    // union with the surviving backward neighbours
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        if (slot[j] == kNone) continue;
-        const uint32_t lin = lin_of[j], s = slot[j];
-        const uint32_t r = w[j] & 0xFFu, c = (w[j] >> 8) & 0x1FFu;
-        if (c > 0 && has_bit(sbits, lin - 1)) uf_union(sa.parent, s, s - 1); // left neighbour is the previous slot
-        if (r > 0) {
-            const uint32_t up = lin - C;
-            if (c > 0 && has_bit(sbits, up - 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up - 1));
-            if (has_bit(sbits, up)) uf_union(sa.parent, s, rank_of(sbits, spre, up));
-            if (c + 1 < C && has_bit(sbits, up + 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up + 1));
-        }
-    }
-    __syncthreads();
-
-    // charge, size and moments about the root pixel
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        if (slot[j] == kNone) continue;
-        const uint32_t s = slot[j];
-        const uint32_t root = uf_find(sa.parent, s);
-        sa.parent[s] = root;
-        const uint32_t rl = sa.slin[root];
-        const int32_t rr = (int32_t)(rl / C), rc = (int32_t)(rl - (uint32_t)rr * C);
-        const int32_t r = (int32_t)(w[j] & 0xFFu), c = (int32_t)((w[j] >> 8) & 0x1FFu);
-        const int32_t q = (int32_t)((w[j] >> 17) & 0xFFu) * it.gain - it.ped;
-        atomicAdd(&sa.qn[root], ((unsigned long long)q << 17) | 1ull);
-        atomicAdd(&sa.sr[root], (unsigned long long)(long long)(q * (r - rr)));
-        atomicAdd(&sa.sc[root], (unsigned long long)(long long)(q * (c - rc)));
-    }
-    __syncthreads();
-
-    if (it.label_e) {
+    if constexpr (!kBig) {
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            if (idx[j] == kNone) continue;
-            int32_t lab = -1;
-            if (slot[j] != kNone) {
-                const uint32_t root = sa.parent[slot[j]];
-                lab = (int32_t)(sa.qn[root] >> 17) >= cthr ? (int32_t)sa.slin[root] : -2;
-            }
-            it.label_e[idx[j]] = lab;
+            const uint32_t k = threadIdx.x + j * kCCThreads;
+            if (k < n) f(k, wreg[j]);
         }
+    } else {
+        for (uint32_t k = threadIdx.x; k < n; k += kCCThreads) f(k, bw[k]);
     }
-
-    // kept roots in slot order -> ordinals -> staging
-    const uint32_t sper = (S + kCCThreads - 1) / kCCThreads;
-    const uint32_t s0 = min(S, tid * sper), s1 = min(S, s0 + sper);
-    uint32_t cnt = 0;
-    for (uint32_t s = s0; s < s1; ++s)
-        if (sa.parent[s] == s && (int32_t)(sa.qn[s] >> 17) >= cthr) ++cnt;
-    uint32_t K;
-    uint32_t ord = block_exclusive_scan<kCCThreads>(cnt, bs.scan_tmp, &K);
-    for (uint32_t s = s0; s < s1; ++s) {
-        if (sa.parent[s] != s) continue;
-        const unsigned long long qn = sa.qn[s];
-        const int32_t Q = (int32_t)(qn >> 17);
-        if (Q < cthr) continue;
-        const uint32_t id = sa.slin[s];
-        const int32_t rr = (int32_t)(id / C), rc = (int32_t)(id - (uint32_t)rr * C);
-        StagedCluster o;
-        o.id = (int32_t)id;
-        o.charge = Q;
-        o.npix = (int32_t)(qn & 0x1FFFFull);
-        o.x = centroid(rr, (long long)sa.sr[s], Q);
-        o.y = centroid(rc, (long long)sa.sc[s], Q);
-        o.pad = 0;
-        L.ws.staging[it.b + ord++] = o;
-    }
-    return K;
 }
 
 // One item clustered by the whole block (see the file comment).  kBig: the
-// slot arrays live in global scratch instead of shared memory.  Returns the
-// number of kept clusters (uniform over the block).
+// tile lives in global scratch instead of shared memory.  Returns the number
+// of kept clusters (uniform over the block).
 template <bool kBig>
-__device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits,
-                               uint32_t *spre, const SlotArrays &sa, BlockShared &bs)
+__device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits, uint32_t *spre,
+                               const Tile &t, BlockShared &bs)
 {
     const uint32_t R = L.g.R, C = L.g.C, nwords = (R * C + 31) >> 5;
     const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
-    const uint32_t tid = threadIdx.x;
+    const uint32_t tid = threadIdx.x, n = it.n;
     const uint32_t *bw = L.ws.bucket_w + it.b;
     const uint32_t *bi = L.ws.bucket_i + it.b;
+    const int32_t gain = it.gain, ped = it.ped;
+    auto lin_of = [C](uint32_t w) { return (w & 0xFFu) * C + ((w >> 8) & 0x1FFu); };
+    auto charge = [gain, ped](uint32_t w) { return (int32_t)((w >> 17) & 0xFFu) * gain - ped; };
 
+    uint32_t wreg[kPer];
+    if constexpr (!kBig) {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t k = tid + j * kCCThreads;
+            wreg[j] = k < n ? bw[k] : 0u;
+        }
+    }
     for (uint32_t i = tid; i < nwords; i += kCCThreads) {
         abits[i] = 0;
         sbits[i] = 0;
     }
-    if (tid == 0) bs.flag = 0;
+    if (tid == 0) {
+        bs.flag = 0;
+        bs.heavy = 0;
+    }
     __syncthreads();
 
     // occupancy and survivor bitmaps; validation and duplicate detection
-    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
-        const uint32_t w = bw[k];
+    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, adc = (w >> 17) & 0xFFu;
         if (r >= R || c >= C || adc == 0 || (w >> 25) != 0) {
             atomicOr(&bs.flag, kErrBadDigi);
-            continue;
+            return;
         }
         const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
-        const uint32_t old = atomicOr(&abits[lin >> 5], bit);
-        if (old & bit) atomicOr(&bs.flag, kErrDup);
-        if ((int32_t)adc * it.gain - it.ped >= thr) atomicOr(&sbits[lin >> 5], bit);
-    }
+        if (atomicOr(&abits[lin >> 5], bit) & bit) atomicOr(&bs.flag, kErrDup);
+        if (charge(w) >= thr) atomicOr(&sbits[lin >> 5], bit);
+    });
     __syncthreads();
     const uint32_t flag = bs.flag;
     if (flag) {
@@ -662,88 +545,142 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     }
     __syncthreads();
 
-    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
-        const uint32_t w = bw[k];
-        const uint32_t lin = (w & 0xFFu) * C + ((w >> 8) & 0x1FFu);
-        if (!has_bit(sbits, lin)) continue;
+    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        const uint32_t lin = lin_of(w);
+        if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
-        sa.parent[s] = s;
-        sa.slin[s] = lin;
-        sa.qn[s] = 0;
-        sa.sr[s] = 0;
-        sa.sc[s] = 0;
-    }
+        t.parent[s] = s;
+        t.qn[s] = 0;
+        t.m[s] = make_int2(0, 0);
+    });
     __syncthreads();
 
-    // union with the surviving backward neighbours
-    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
-        const uint32_t w = bw[k];
-        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu;
-        const uint32_t lin = r * C + c;
-        if (!has_bit(sbits, lin)) continue;
+    // union with the surviving backward neighbours (the left one is the previous slot)
+    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
+        if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
-        if (c > 0 && has_bit(sbits, lin - 1)) uf_union(sa.parent, s, rank_of(sbits, spre, lin - 1));
+        if (c > 0 && has_bit(sbits, lin - 1)) uf_union(t.parent, s, s - 1);
         if (r > 0) {
             const uint32_t up = lin - C;
-            if (c > 0 && has_bit(sbits, up - 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up - 1));
-            if (has_bit(sbits, up)) uf_union(sa.parent, s, rank_of(sbits, spre, up));
-            if (c + 1 < C && has_bit(sbits, up + 1)) uf_union(sa.parent, s, rank_of(sbits, spre, up + 1));
+            if (c > 0 && has_bit(sbits, up - 1)) uf_union(t.parent, s, rank_of(sbits, spre, up - 1));
+            if (has_bit(sbits, up)) uf_union(t.parent, s, rank_of(sbits, spre, up));
+            if (c + 1 < C && has_bit(sbits, up + 1)) uf_union(t.parent, s, rank_of(sbits, spre, up + 1));
         }
-    }
+    });
     __syncthreads();
 
-    // charge, size and moments about the root pixel
-    for (uint32_t k = tid; k < it.n; k += kCCThreads) {
-        const uint32_t w = bw[k];
-        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu;
-        const uint32_t lin = r * C + c;
-        if (!has_bit(sbits, lin)) continue;
+    // mark every root with its linear index (the root is the smallest slot = smallest index)
+    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        const uint32_t lin = lin_of(w);
+        if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
-        const uint32_t root = uf_find(sa.parent, s);
-        sa.parent[s] = root;
-        const uint32_t rl = sa.slin[root];
-        const int32_t rr = (int32_t)(rl / C), rc = (int32_t)(rl - (uint32_t)rr * C);
-        const int32_t q = (int32_t)((w >> 17) & 0xFFu) * it.gain - it.ped;
-        atomicAdd(&sa.qn[root], ((unsigned long long)q << 17) | 1ull);
-        atomicAdd(&sa.sr[root], (unsigned long long)(long long)(q * ((int32_t)r - rr)));
-        atomicAdd(&sa.sc[root], (unsigned long long)(long long)(q * ((int32_t)c - rc)));
-    }
+        if (t.parent[s] == s) t.parent[s] = kMark | lin;
+    });
     __syncthreads();
+
+    // charge, size and 32-bit moments about the root pixel; compress to the root
+    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
+        if (!has_bit(sbits, lin)) return;
+        const uint32_t s = rank_of(sbits, spre, lin);
+        const volatile uint32_t *vp = t.parent;
+        uint32_t x = s, p = vp[s];
+        while (!(p & kMark)) {
+            x = p;
+            p = vp[x];
+        }
+        if (x != s) t.parent[s] = x;
+        const uint32_t rl = p & ~kMark;
+        const int32_t rr = (int32_t)(rl / C), rc = (int32_t)(rl - (uint32_t)rr * C);
+        const int32_t q = charge(w);
+        atomicAdd(&t.qn[x], ((unsigned long long)q << 17) | 1ull);
+        atomicAdd(&t.m[x].x, q * ((int32_t)r - rr));
+        atomicAdd(&t.m[x].y, q * ((int32_t)c - rc));
+    });
+    __syncthreads();
+
+    // heavy clusters: recompute their moments exactly in 64 bits
+    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        const uint32_t lin = lin_of(w);
+        if (!has_bit(sbits, lin)) return;
+        const uint32_t s = rank_of(sbits, spre, lin);
+        if ((t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) > kQSafe32) bs.heavy = 1;
+    });
+    __syncthreads();
+    const bool heavy = bs.heavy != 0;
+    if (heavy) {
+        for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+            const uint32_t lin = lin_of(w);
+            if (!has_bit(sbits, lin)) return;
+            const uint32_t s = rank_of(sbits, spre, lin);
+            if (t.parent[s] & kMark) {
+                t.exact[2 * s] = 0;
+                t.exact[2 * s + 1] = 0;
+            }
+        });
+        __syncthreads();
+        for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+            const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
+            if (!has_bit(sbits, lin)) return;
+            const uint32_t s = rank_of(sbits, spre, lin);
+            const uint32_t p = t.parent[s];
+            const uint32_t x = (p & kMark) ? s : p;
+            const uint32_t rl = t.parent[x] & ~kMark;
+            const long long rr = rl / C, rc = rl - (rl / C) * C;
+            const long long q = charge(w);
+            atomicAdd(&t.exact[2 * x], (unsigned long long)(q * ((long long)r - rr)));
+            atomicAdd(&t.exact[2 * x + 1], (unsigned long long)(q * ((long long)c - rc)));
+        });
+        __syncthreads();
+    }
 
     if (it.label_e) {
-        for (uint32_t k = tid; k < it.n; k += kCCThreads) {
-            const uint32_t w = bw[k];
-            const uint32_t lin = (w & 0xFFu) * C + ((w >> 8) & 0x1FFu);
+        for_digis<kBig>(wreg, bw, n, [&](uint32_t k, uint32_t w) {
+            const uint32_t lin = lin_of(w);
             int32_t lab = -1;
             if (has_bit(sbits, lin)) {
-                const uint32_t root = sa.parent[rank_of(sbits, spre, lin)];
-                lab = (int32_t)(sa.qn[root] >> 17) >= cthr ? (int32_t)sa.slin[root] : -2;
+                const uint32_t s = rank_of(sbits, spre, lin);
+                const uint32_t p = t.parent[s];
+                const uint32_t x = (p & kMark) ? s : p;
+                const uint32_t px = (p & kMark) ? p : t.parent[x];
+                lab = (int32_t)(t.qn[x] >> 17) >= cthr ? (int32_t)(px & ~kMark) : -2;
             }
             it.label_e[bi[k]] = lab;
-        }
+        });
     }
 
-    // kept roots in slot order -> ordinals -> staging
+    // kept roots in slot order (= id order) -> ordinals -> staging
     const uint32_t sper = (S + kCCThreads - 1) / kCCThreads;
     const uint32_t s0 = min(S, tid * sper), s1 = min(S, s0 + sper);
     uint32_t cnt = 0;
     for (uint32_t s = s0; s < s1; ++s)
-        if (sa.parent[s] == s && (int32_t)(sa.qn[s] >> 17) >= cthr) ++cnt;
+        if ((t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) >= cthr) ++cnt;
     uint32_t K;
     uint32_t ord = block_exclusive_scan<kCCThreads>(cnt, bs.scan_tmp, &K);
     for (uint32_t s = s0; s < s1; ++s) {
-        if (sa.parent[s] != s) continue;
-        const unsigned long long qn = sa.qn[s];
+        const uint32_t p = t.parent[s];
+        if (!(p & kMark)) continue;
+        const unsigned long long qn = t.qn[s];
         const int32_t Q = (int32_t)(qn >> 17);
         if (Q < cthr) continue;
-        const uint32_t id = sa.slin[s];
+        const uint32_t id = p & ~kMark;
         const int32_t rr = (int32_t)(id / C), rc = (int32_t)(id - (uint32_t)rr * C);
+        long long mr, mc;
+        if (heavy && Q > kQSafe32) {
+            mr = (long long)t.exact[2 * s];
+            mc = (long long)t.exact[2 * s + 1];
+        } else {
+            const int2 mm = t.m[s];
+            mr = mm.x;
+            mc = mm.y;
+        }
         StagedCluster o;
         o.id = (int32_t)id;
         o.charge = Q;
         o.npix = (int32_t)(qn & 0x1FFFFull);
-        o.x = centroid(rr, (long long)sa.sr[s], Q);
-        o.y = centroid(rc, (long long)sa.sc[s], Q);
+        o.x = centroid(rr, mr, Q);
+        o.y = centroid(rc, mc, Q);
         o.pad = 0;
         L.ws.staging[it.b + ord++] = o;
     }
@@ -757,174 +694,212 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// Decoupled look-back over tickets, run by one full warp: publish this
-// ticket's aggregate, then read the 32 preceding tickets at once; the
-// exclusive prefix is the sum of the values from the nearest inclusive prefix
-// onwards (or of the whole window, which then slides back by 32).  Every
-// predecessor ticket is held by a running block that publishes its aggregate
-// without waiting, so the wait ends; it is bounded regardless (kErrTimeout).
-__device__ unsigned long long chain_lookback(unsigned long long *chain, uint64_t g, unsigned long long agg,
-                                             uint32_t *launch_err)
+// Decoupled look-back over tickets, run by one full warp.  Each ticket's
+// aggregate is published as soon as its clusters are staged; this reads the
+// 32 preceding tickets at once: the exclusive prefix is the sum of the values
+// from the nearest inclusive prefix onwards (or of the whole window, which
+// then slides back by 32).  Non-blocking mode gives up when a needed
+// predecessor has not published yet; blocking mode waits, bounded by
+// kSpinLimit (then kErrTimeout).  On success the inclusive prefix is
+// published.  Predecessor aggregates never wait on anything, so every
+// blocking wait ends.
+__device__ bool chain_resolve(unsigned long long *chain, uint64_t g, unsigned long long agg, bool blocking,
+                              unsigned long long *excl_out, uint32_t *launch_err)
 {
     const unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62, kMask = kAgg - 1;
+    (void)kAgg;
     const uint32_t lane = threadIdx.x & 31;
-    if (g == 0) {
-        if (lane == 0) st_release(&chain[0], kInc | agg);
-        return 0;
-    }
-    if (lane == 0) st_release(&chain[g], kAgg | agg);
     unsigned long long excl = 0;
-    long long end = (long long)g - 1;
-    uint32_t spins = 0;
-    for (;;) {
-        const long long j = end - (31 - (long long)lane);
-        const unsigned long long v = j >= 0 ? ld_acquire(&chain[j]) : kInc;
-        const uint32_t flag = (uint32_t)(v >> 62);
-        const uint32_t inc = __ballot_sync(kFull, flag == 2);
-        const int top = inc ? 31 - __clz(inc) : -1;
-        const uint32_t waiting = __ballot_sync(kFull, flag == 0 && (int)lane > top);
-        if (waiting) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0) atomicOr(launch_err, kErrTimeout);
-                break;
+    if (g > 0) {
+        long long end = (long long)g - 1;
+        uint32_t spins = 0;
+        for (;;) {
+            const long long j = end - (31 - (long long)lane);
+            const unsigned long long v = j >= 0 ? ld_acquire(&chain[j]) : kInc;
+            const uint32_t flag = (uint32_t)(v >> 62);
+            const uint32_t inc = __ballot_sync(kFull, flag == 2);
+            const int top = inc ? 31 - __clz(inc) : -1;
+            const uint32_t waiting = __ballot_sync(kFull, flag == 0 && (int)lane > top);
+            if (waiting) {
+                if (!blocking) return false;
+                if (++spins > kSpinLimit) {
+                    if (lane == 0) atomicOr(launch_err, kErrTimeout);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
             }
-            __nanosleep(32);
-            continue;
+            excl += warp_sum_u64((int)lane >= top ? (v & kMask) : 0ull);
+            if (inc) break;
+            end -= 32;
         }
-        excl += warp_sum_u64((int)lane >= top ? (v & kMask) : 0ull);
-        if (inc) break;
-        end -= 32;
     }
     if (lane == 0) st_release(&chain[g], kInc | (excl + agg));
-    return excl;
+    *excl_out = excl;
+    return true;
 }
+
+struct Pending {
+    uint32_t g;
+    uint32_t K[kGroup];
+    uint32_t b[kGroup];
+};
 
 __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ BlockShared bs;
     __shared__ uint32_t s_n[kGroup], s_b[kGroup], s_K[kGroup], s_pref[kGroup + 1];
-    __shared__ uint32_t s_ticket;
+    __shared__ Pending ring[kRing];
+    __shared__ uint32_t s_ticket, s_head, s_tail, s_ok;
     __shared__ unsigned long long s_prefix;
 
     const uint32_t R = L.g.R, C = L.g.C, M = L.g.M;
     const uint32_t nwords = (R * C + 31) >> 5;
     const uint32_t tid = threadIdx.x;
-    SlotArrays sm;
+    Tile sm;
     sm.qn = reinterpret_cast<unsigned long long *>(dsm);
-    sm.sr = sm.qn + kSmemSlots;
-    sm.sc = sm.sr + kSmemSlots;
-    sm.parent = reinterpret_cast<uint32_t *>(sm.sc + kSmemSlots);
-    sm.slin = sm.parent + kSmemSlots;
-    uint32_t *abits = sm.slin + kSmemSlots;
+    sm.m = reinterpret_cast<int2 *>(sm.qn + kSmemSlots);
+    sm.parent = reinterpret_cast<uint32_t *>(sm.m + kSmemSlots);
+    sm.exact = L.ws.exact + (size_t)blockIdx.x * 2 * kSmemSlots;
+    uint32_t *abits = sm.parent + kSmemSlots;
     uint32_t *sbits = abits + nwords;
     uint32_t *spre = sbits + nwords;
 
     const uint64_t EM = (uint64_t)L.E * M;
     const uint64_t ngroups = (EM + kGroup - 1) / kGroup;
+    const unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62;
+    if (tid == 0) {
+        s_head = 0;
+        s_tail = 0;
+    }
+    bool tickets_left = true;
 
     for (;;) {
-        if (tid == 0) s_ticket = atomicAdd(&L.ws.ctl[0], 1u);
-        __syncthreads();
-        const uint64_t g = s_ticket;
-        if (g >= ngroups) break;
-        const uint64_t item0 = g * kGroup;
-        if (tid < (uint32_t)kGroup) {
-            const uint64_t item = item0 + tid;
-            const bool ok = item < EM;
-            s_n[tid] = ok ? L.ws.count[item] : 0u;
-            s_b[tid] = ok ? L.ws.boff[item] : 0u;
-            s_K[tid] = 0;
-        }
-        __syncthreads();
-
-        {   // warp tier: one warp per small item
-            const uint32_t wi = tid >> 5;
-            const uint32_t n = s_n[wi];
-            if (n > 0 && n <= (uint32_t)kWarpMax) {
-                const ItemCtx it = make_item(L, item0 + wi, s_b[wi], n);
-                const uint32_t K = warp_item(L, it);
-                if ((tid & 31) == 0) s_K[wi] = K;
-            }
-        }
-        __syncthreads();
-
-        for (int i = 0; i < kGroup; ++i) { // block tier: larger items one at a time
-            const uint32_t n = s_n[i];
-            if (n <= (uint32_t)kWarpMax) continue;
-            const ItemCtx it = make_item(L, item0 + i, s_b[i], n);
-            uint32_t K;
-            if (n <= (uint32_t)kSmemSlots) {
-                K = block_item_small(L, it, abits, sbits, spre, sm, bs);
+        if (tickets_left) {
+            if (tid == 0) s_ticket = atomicAdd(&L.ws.ctl[0], 1u);
+            __syncthreads();
+            const uint64_t g = s_ticket;
+            if (g >= ngroups) {
+                tickets_left = false;
             } else {
-                if (tid == 0) {
-                    bs.big_off = 0;
-                    if (L.ws.big_arena) {
-                        const uint32_t off = atomicAdd(&L.ws.ctl[2], n);
-                        bs.big_off = off;
-                        if ((uint64_t)off + n > L.ws.big_slots) atomicOr(&L.ws.ctl[1], kErrCapacity);
+                const uint64_t item0 = g * kGroup;
+                if (tid < (uint32_t)kGroup) {
+                    const uint64_t item = item0 + tid;
+                    const bool ok = item < EM;
+                    s_n[tid] = ok ? L.ws.count[item] : 0u;
+                    s_b[tid] = ok ? L.ws.boff[item] : 0u;
+                    s_K[tid] = 0;
+                }
+                __syncthreads();
+                {   // warp tier: one warp per small item
+                    const uint32_t wi = tid >> 5;
+                    const uint32_t n = s_n[wi];
+                    if (n > 0 && n <= (uint32_t)kWarpMax) {
+                        const ItemCtx it = make_item(L, item0 + wi, s_b[wi], n);
+                        const uint32_t K = warp_item(L, it);
+                        if ((tid & 31) == 0) s_K[wi] = K;
                     }
                 }
                 __syncthreads();
-                SlotArrays ga;
-                uint64_t cap;
-                unsigned char *base;
-                if (L.ws.big_arena) {
-                    cap = n;
-                    base = L.ws.big + (uint64_t)bs.big_off * kBigSlotBytes;
-                } else {
-                    cap = L.ws.big_slots;
-                    base = L.ws.big + (uint64_t)blockIdx.x * L.ws.big_slots * kBigSlotBytes;
+                for (int i = 0; i < kGroup; ++i) { // block tier: larger items one at a time
+                    const uint32_t n = s_n[i];
+                    if (n <= (uint32_t)kWarpMax) continue;
+                    const ItemCtx it = make_item(L, item0 + i, s_b[i], n);
+                    uint32_t K;
+                    if (n <= (uint32_t)kSmemSlots) {
+                        K = block_item<false>(L, it, abits, sbits, spre, sm, bs);
+                    } else {
+                        if (tid == 0) {
+                            bs.big_off = 0;
+                            if (L.ws.big_arena) bs.big_off = atomicAdd(&L.ws.ctl[2], n);
+                        }
+                        __syncthreads();
+                        const uint64_t cap = L.ws.big_arena ? (uint64_t)n : L.ws.big_slots;
+                        unsigned char *base =
+                            L.ws.big + (L.ws.big_arena ? (uint64_t)bs.big_off : (uint64_t)blockIdx.x * L.ws.big_slots) *
+                                           kBigSlotBytes;
+                        const bool fits = L.ws.big_arena ? (uint64_t)bs.big_off + n <= L.ws.big_slots
+                                                         : (uint64_t)min(n, R * C) <= L.ws.big_slots;
+                        Tile gt;
+                        gt.qn = reinterpret_cast<unsigned long long *>(base);
+                        gt.exact = gt.qn + cap;
+                        gt.m = reinterpret_cast<int2 *>(gt.exact + 2 * cap);
+                        gt.parent = reinterpret_cast<uint32_t *>(gt.m + cap);
+                        K = fits ? block_item<true>(L, it, abits, sbits, spre, gt, bs) : 0u;
+                        if (!fits && tid == 0) atomicOr(&L.ws.ctl[1], kErrCapacity);
+                    }
+                    if (tid == 0) s_K[i] = K;
+                    __syncthreads();
                 }
-                const bool fits = L.ws.big_arena ? (uint64_t)bs.big_off + n <= L.ws.big_slots
-                                                 : (uint64_t)min(n, R * C) <= L.ws.big_slots;
-                ga.qn = reinterpret_cast<unsigned long long *>(base);
-                ga.sr = ga.qn + cap;
-                ga.sc = ga.sr + cap;
-                ga.parent = reinterpret_cast<uint32_t *>(ga.sc + cap);
-                ga.slin = ga.parent + cap;
-                K = fits ? block_item<true>(L, it, abits, sbits, spre, ga, bs) : 0u;
-                if (!fits && tid == 0) atomicOr(&L.ws.ctl[1], kErrCapacity);
+                // park the ticket and publish its aggregate (no waiting here)
+                if (tid == 0) {
+                    Pending &pd = ring[s_tail % kRing];
+                    unsigned long long agg = 0;
+                    pd.g = (uint32_t)g;
+                    for (int i = 0; i < kGroup; ++i) {
+                        pd.K[i] = s_K[i];
+                        pd.b[i] = s_b[i];
+                        agg += s_K[i];
+                    }
+                    __threadfence();
+                    st_release(&L.ws.chain[g], (g == 0 ? kInc : kAgg) | agg);
+                    ++s_tail;
+                }
+                __syncthreads();
             }
-            if (tid == 0) s_K[i] = K;
-            __syncthreads();
         }
 
-        // ordered write of the ticket's clusters
-        if (tid < 32) {
-            uint32_t p = 0;
-            for (int i = 0; i < kGroup; ++i) {
-                if (tid == 0) s_pref[i] = p;
-                p += s_K[i];
+        // write out parked tickets whose prefix is known, oldest first
+        while (s_head != s_tail) {
+            const bool blocking = !tickets_left || (s_tail - s_head) >= (uint32_t)kRing;
+            const Pending &pd = ring[s_head % kRing];
+            if (tid < 32) {
+                unsigned long long agg = 0;
+                for (int i = 0; i < kGroup; ++i) agg += pd.K[i];
+                unsigned long long excl = 0;
+                const bool ok = chain_resolve(L.ws.chain, pd.g, agg, blocking, &excl, &L.ws.ctl[1]);
+                if (tid == 0) {
+                    s_ok = ok ? 1u : 0u;
+                    s_prefix = excl;
+                    uint32_t p = 0;
+                    for (int i = 0; i < kGroup; ++i) {
+                        s_pref[i] = p;
+                        p += pd.K[i];
+                    }
+                    s_pref[kGroup] = p;
+                }
             }
-            if (tid == 0) s_pref[kGroup] = p;
-            const unsigned long long pre = chain_lookback(L.ws.chain, g, p, &L.ws.ctl[1]);
-            if (tid == 0) s_prefix = pre;
-        }
-        __syncthreads();
-        const unsigned long long P = s_prefix;
-        const uint32_t tot = s_pref[kGroup];
-        for (uint32_t o = tid; o < tot; o += kCCThreads) {
-            int i = 0;
-            while (i + 1 < kGroup && s_pref[i + 1] <= o) ++i;
-            const StagedCluster s = L.ws.staging[s_b[i] + (o - s_pref[i])];
-            const unsigned long long d = P + o;
-            if (d < L.out.capacity) {
-                L.out.module[d] = (uint32_t)((item0 + i) % M);
-                L.out.id[d] = s.id;
-                L.out.charge[d] = s.charge;
-                L.out.npix[d] = s.npix;
-                L.out.x[d] = s.x;
-                L.out.y[d] = s.y;
+            __syncthreads();
+            if (!s_ok) break;
+            const unsigned long long P = s_prefix;
+            const uint32_t tot = s_pref[kGroup];
+            const uint64_t item0 = (uint64_t)pd.g * kGroup;
+            for (uint32_t o = tid; o < tot; o += kCCThreads) {
+                int i = 0;
+                while (i + 1 < kGroup && s_pref[i + 1] <= o) ++i;
+                const StagedCluster sc = L.ws.staging[pd.b[i] + (o - s_pref[i])];
+                const unsigned long long d = P + o;
+                if (d < L.out.capacity) {
+                    L.out.module[d] = (uint32_t)((item0 + i) % M);
+                    L.out.id[d] = sc.id;
+                    L.out.charge[d] = sc.charge;
+                    L.out.npix[d] = sc.npix;
+                    L.out.x[d] = sc.x;
+                    L.out.y[d] = sc.y;
+                }
             }
+            if (tid == 0 && P + tot > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
+            if (tid < (uint32_t)kGroup) {
+                const uint64_t item = item0 + tid;
+                if (item < EM && item % M == 0) L.out.cluster_offsets[item / M] = P + s_pref[tid];
+            }
+            if (tid == 0 && pd.g == ngroups - 1) L.out.cluster_offsets[L.E] = P + tot;
+            __syncthreads();
+            if (tid == 0) ++s_head;
+            __syncthreads();
         }
-        if (tid == 0 && P + tot > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
-        if (tid < (uint32_t)kGroup) {
-            const uint64_t item = item0 + tid;
-            if (item < EM && item % M == 0) L.out.cluster_offsets[item / M] = P + s_pref[tid];
-        }
-        if (tid == 0 && g == ngroups - 1) L.out.cluster_offsets[L.E] = P + tot;
-        __syncthreads();
+        if (!tickets_left && s_head == s_tail) break;
     }
 }
 
@@ -946,7 +921,7 @@ __global__ void finalize_kernel(const Launch L)
 size_t cc_smem_bytes(uint32_t R, uint32_t C)
 {
     const size_t nwords = ((size_t)R * C + 31) / 32;
-    return (size_t)kSmemSlots * (8 * 3 + 4 * 2) + nwords * 4 * 3;
+    return (size_t)kSmemSlots * (8 + 8 + 4) + nwords * 4 * 3;
 }
 
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
@@ -973,6 +948,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.staging = reinterpret_cast<StagedCluster *>(take(sizeof(StagedCluster) * N));
+    w.exact = reinterpret_cast<unsigned long long *>(take(16ull * kSmemSlots * (cc_grid > 0 ? cc_grid : 1)));
     const uint64_t slab_slots = std::min<uint64_t>((uint64_t)R * C, N);
     const uint64_t slab_total = slab_slots * (uint64_t)(cc_grid > 0 ? cc_grid : 1);
     w.big_arena = N <= slab_total ? 1 : 0;
