@@ -322,7 +322,6 @@ constexpr uint32_t kMark = 0x80000000u;
 // |dcol| < 512): they cannot overflow while Q <= INT32_MAX / 512.  Items with
 // a heavier cluster recompute the moments in 64 bits.
 constexpr int32_t kQSafe32 = 0x7FFFFFFF / 512;
-constexpr int kPer = kSmemSlots / kCCThreads; // digis per thread in the shared-memory tier
 constexpr int kRing = 16;                    // tickets a block may hold before their prefix is known
 
 // Per-item arrays of the block tier: shared memory, or global scratch for
@@ -463,20 +462,14 @@ __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
     return __popc(kl);
 }
 
-// Apply f(k, word) to every digi of the item owned by this thread: from the
-// register copy (shared-memory tier) or from the bucket (global tier).
-template <bool kBig, class F>
-__device__ __forceinline__ void for_digis(const uint32_t (&wreg)[kPer], const uint32_t *bw, uint32_t n, F &&f)
+// Apply f(k, word) to every digi of the item owned by this thread.  The
+// loop is kept rolled so that the block tier stays small in the instruction
+// cache; the item's bucket (read-only here) is re-read through L1.
+template <class F>
+__device__ __forceinline__ void for_digis(const uint32_t *bw, uint32_t n, F &&f)
 {
-    if constexpr (!kBig) {
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const uint32_t k = threadIdx.x + j * kCCThreads;
-            if (k < n) f(k, wreg[j]);
-        }
-    } else {
-        for (uint32_t k = threadIdx.x; k < n; k += kCCThreads) f(k, bw[k]);
-    }
+#pragma unroll 1
+    for (uint32_t k = threadIdx.x; k < n; k += kCCThreads) f(k, __ldg(bw + k));
 }
 
 // One item clustered by the whole block (see the file comment).  kBig: the
@@ -495,14 +488,6 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     auto lin_of = [C](uint32_t w) { return (w & 0xFFu) * C + ((w >> 8) & 0x1FFu); };
     auto charge = [gain, ped](uint32_t w) { return (int32_t)((w >> 17) & 0xFFu) * gain - ped; };
 
-    uint32_t wreg[kPer];
-    if constexpr (!kBig) {
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const uint32_t k = tid + j * kCCThreads;
-            wreg[j] = k < n ? bw[k] : 0u;
-        }
-    }
     for (uint32_t i = tid; i < nwords; i += kCCThreads) {
         abits[i] = 0;
         sbits[i] = 0;
@@ -514,7 +499,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
 
     // occupancy and survivor bitmaps; validation and duplicate detection
-    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, adc = (w >> 17) & 0xFFu;
         if (r >= R || c >= C || adc == 0 || (w >> 25) != 0) {
             atomicOr(&bs.flag, kErrBadDigi);
@@ -545,7 +530,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     }
     __syncthreads();
 
-    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t lin = lin_of(w);
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
@@ -556,7 +541,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
 
     // union with the surviving backward neighbours (the left one is the previous slot)
-    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
@@ -571,7 +556,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
 
     // mark every root with its linear index (the root is the smallest slot = smallest index)
-    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t lin = lin_of(w);
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
@@ -580,7 +565,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
 
     // charge, size and 32-bit moments about the root pixel; compress to the root
-    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
@@ -601,7 +586,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
 
     // heavy clusters: recompute their moments exactly in 64 bits
-    for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t lin = lin_of(w);
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
@@ -610,7 +595,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
     const bool heavy = bs.heavy != 0;
     if (heavy) {
-        for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        for_digis(bw, n, [&](uint32_t, uint32_t w) {
             const uint32_t lin = lin_of(w);
             if (!has_bit(sbits, lin)) return;
             const uint32_t s = rank_of(sbits, spre, lin);
@@ -620,7 +605,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
             }
         });
         __syncthreads();
-        for_digis<kBig>(wreg, bw, n, [&](uint32_t, uint32_t w) {
+        for_digis(bw, n, [&](uint32_t, uint32_t w) {
             const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
             if (!has_bit(sbits, lin)) return;
             const uint32_t s = rank_of(sbits, spre, lin);
@@ -636,7 +621,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     }
 
     if (it.label_e) {
-        for_digis<kBig>(wreg, bw, n, [&](uint32_t k, uint32_t w) {
+        for_digis(bw, n, [&](uint32_t k, uint32_t w) {
             const uint32_t lin = lin_of(w);
             int32_t lab = -1;
             if (has_bit(sbits, lin)) {

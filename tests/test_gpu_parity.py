@@ -124,9 +124,9 @@ def _module_with(n, rng, r0=10, c0=10, span=None):
     return synth.pack(rr, cc, adc)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 64, 2047, 2048, 2049, 5000, 20000])
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 64, 2048, 4095, 4096, 4097, 9000, 20000])
 def test_tier_boundaries(torch_cuda, n):
-    """Module sizes around the warp (32) and shared-memory (2048) capacities."""
+    """Module sizes around the warp (32) and shared-memory (4096) capacities."""
     rng = np.random.default_rng(n)
     gain = np.array([70, 75, 80], np.int32)
     ped = np.array([100, 0, 200], np.int32)
@@ -255,3 +255,26 @@ def test_device_path_occupancy_sampled(torch_cuda):
         lab = got.label[s:t]
         assert int(got.charge[a:b].astype(np.int64).sum()) == int(q[s:t][lab >= 0].sum())
         assert int(got.npix[a:b].sum()) == int((lab >= 0).sum())
+
+
+@pytest.mark.parametrize("rows,cols", [(40, 100), (50, 120)])
+def test_heavy_cluster_exact_moments(torch_cuda, rows, cols):
+    """One dense cluster whose moments overflow 32 bits (Q ~ 1.3e8): the 64-bit
+    fallback, in the shared-memory tier (4000 digis) and the global tier (6000)."""
+    rr, cc = np.meshgrid(np.arange(rows) + 60, np.arange(cols) + 200, indexing="ij")
+    rr, cc = rr.ravel(), cc.ravel()
+    rng = np.random.default_rng(rows)
+    adc = rng.integers(200, 256, rr.size)
+    words = synth.pack(rr, cc, adc)
+    gain = np.array([126, 70], np.int32)
+    ped = np.array([0, 100], np.int32)
+    extra = synth.pack([3, 150], [3, 400], [90, 90])
+    w = np.concatenate([words, extra])
+    m = np.concatenate([np.zeros(rr.size, np.uint16), np.array([1, 1], np.uint16)])
+    perm = rng.permutation(len(w))
+    w, m = w[perm], m[perm]
+    offs = np.array([0, len(w)], np.uint64)
+    ref = oracle.reconstruct_batch(w, m, offs, 2, gain, ped)
+    assert ref.charge[0] > 0x7FFFFFFF // 512
+    got = run_batch(ctx_for(2, gain, ped), w, m, offs)
+    assert_batch_matches(got, ref, offs)
