@@ -50,7 +50,7 @@ struct Outputs {
 // the first kernel (one memset): control words, per-event error bits,
 // per-item counts and the chained-scan state.
 struct Workspace {
-    uint32_t *ctl;        // [16]: 0 group ticket, 1 launch error bits, 2 arena bump
+    uint32_t *ctl;        // [16]: 0 group ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier
     uint32_t *event_err;  // [E]
     uint32_t *count;      // [E*M]
     unsigned long long *chain; // [n_groups]

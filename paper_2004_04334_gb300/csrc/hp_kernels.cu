@@ -672,56 +672,80 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     return K;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+// Ordered output across tickets.  Each ticket publishes its aggregate (the
+// number of clusters it staged) in chain[g] as soon as it is staged, without
+// waiting.  The prefix then spreads by a cooperative frontier: ctl[3] = F
+// means tickets below F carry their inclusive prefix.  Any warp may push F
+// forward: it reads the 32 tickets from F on, takes the run of consecutive
+// published aggregates, scans it on top of chain[F-1], publishes those
+// inclusive prefixes and raises F.  Racing warps compute identical values.
+__device__ void advance_frontier(unsigned long long *chain, uint32_t *frontier, uint64_t ngroups)
 {
+    const unsigned long long kInc = 2ull << 62, kMask = (1ull << 62) - 1;
+    const uint32_t lane = threadIdx.x & 31;
+    for (int rounds = 0; rounds < 64; ++rounds) {
+        uint32_t F = 0;
+        if (lane == 0) F = *(volatile uint32_t *)frontier;
+        F = __shfl_sync(kFull, F, 0);
+        if (F >= ngroups) return;
+        unsigned long long prev = 0;
+        if (F > 0) {
+            const unsigned long long pv = ld_acquire(&chain[F - 1]);
+            if ((pv >> 62) != 2) return; // the inclusive below F is not visible yet
+            prev = pv & kMask;
+        }
+        const uint64_t j = (uint64_t)F + lane;
+        const unsigned long long v = j < ngroups ? ld_acquire(&chain[j]) : 0ull;
+        const uint32_t avail = __ballot_sync(kFull, (v >> 62) != 0);
+        const uint32_t u = (~avail) ? (uint32_t)(__ffs(~avail) - 1) : 32u; // leading run of published tickets
+        if (u == 0) return;
+        unsigned long long x = lane < u ? (v & kMask) : 0ull;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane < u && (v >> 62) == 1) st_release(&chain[j], kInc | (prev + x));
+        __syncwarp();
+        __threadfence();
+        if (lane == 0) atomicMax(frontier, F + u);
+        if (u < 32) return;
+    }
 }
 
-// Decoupled look-back over tickets, run by one full warp.  Each ticket's
-// aggregate is published as soon as its clusters are staged; this reads the
-// 32 preceding tickets at once: the exclusive prefix is the sum of the values
-// from the nearest inclusive prefix onwards (or of the whole window, which
-// then slides back by 32).  Non-blocking mode gives up when a needed
-// predecessor has not published yet; blocking mode waits, bounded by
-// kSpinLimit (then kErrTimeout).  On success the inclusive prefix is
-// published.  Predecessor aggregates never wait on anything, so every
-// blocking wait ends.
-__device__ bool chain_resolve(unsigned long long *chain, uint64_t g, unsigned long long agg, bool blocking,
-                              unsigned long long *excl_out, uint32_t *launch_err)
+// Resolve ticket g (one full warp): its inclusive prefix once the frontier
+// has passed it.  Non-blocking mode returns false if it has not; blocking
+// mode keeps pushing the frontier, bounded by kSpinLimit (then kErrTimeout).
+// Every aggregate is published without waiting, so every blocking wait ends.
+__device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uint64_t ngroups, uint64_t g,
+                              unsigned long long agg, bool blocking, unsigned long long *excl_out,
+                              uint32_t *launch_err)
 {
-    const unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62, kMask = kAgg - 1;
-    (void)kAgg;
+    const unsigned long long kMask = (1ull << 62) - 1;
     const uint32_t lane = threadIdx.x & 31;
-    unsigned long long excl = 0;
-    if (g > 0) {
-        long long end = (long long)g - 1;
-        uint32_t spins = 0;
-        for (;;) {
-            const long long j = end - (31 - (long long)lane);
-            const unsigned long long v = j >= 0 ? ld_acquire(&chain[j]) : kInc;
-            const uint32_t flag = (uint32_t)(v >> 62);
-            const uint32_t inc = __ballot_sync(kFull, flag == 2);
-            const int top = inc ? 31 - __clz(inc) : -1;
-            const uint32_t waiting = __ballot_sync(kFull, flag == 0 && (int)lane > top);
-            if (waiting) {
-                if (!blocking) return false;
-                if (++spins > kSpinLimit) {
-                    if (lane == 0) atomicOr(launch_err, kErrTimeout);
-                    break;
-                }
-                __nanosleep(32);
-                continue;
-            }
-            excl += warp_sum_u64((int)lane >= top ? (v & kMask) : 0ull);
-            if (inc) break;
-            end -= 32;
+    for (uint32_t spins = 0;; ++spins) {
+        unsigned long long v = 0;
+        if (lane == 0) v = ld_acquire(&chain[g]);
+        v = __shfl_sync(kFull, v, 0);
+        if ((v >> 62) == 2) {
+            *excl_out = (v & kMask) - agg;
+            return true;
         }
+        advance_frontier(chain, frontier, ngroups);
+        if (lane == 0) v = ld_acquire(&chain[g]);
+        v = __shfl_sync(kFull, v, 0);
+        if ((v >> 62) == 2) {
+            *excl_out = (v & kMask) - agg;
+            return true;
+        }
+        if (!blocking) return false;
+        if (spins > kSpinLimit) {
+            if (lane == 0) atomicOr(launch_err, kErrTimeout);
+            *excl_out = 0;
+            return true;
+        }
+        __nanosleep(64);
     }
-    if (lane == 0) st_release(&chain[g], kInc | (excl + agg));
-    *excl_out = excl;
-    return true;
 }
 
 struct Pending {
@@ -843,7 +867,8 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
                 unsigned long long agg = 0;
                 for (int i = 0; i < kGroup; ++i) agg += pd.K[i];
                 unsigned long long excl = 0;
-                const bool ok = chain_resolve(L.ws.chain, pd.g, agg, blocking, &excl, &L.ws.ctl[1]);
+                const bool ok =
+                    chain_resolve(L.ws.chain, &L.ws.ctl[3], ngroups, pd.g, agg, blocking, &excl, &L.ws.ctl[1]);
                 if (tid == 0) {
                     s_ok = ok ? 1u : 0u;
                     s_prefix = excl;
