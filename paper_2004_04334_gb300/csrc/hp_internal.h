@@ -17,7 +17,7 @@ constexpr uint32_t kErrTimeout = 8u;
 constexpr int kChunk = 4096;         // digis per histogram / scatter block
 constexpr int kHistThreads = 512;
 constexpr int kHistCap = 4096;       // (event, module) bins a block can histogram in shared memory
-constexpr int kCCThreads = 256;      // threads of a clustering block
+constexpr int kCCThreads = 512;      // threads of a clustering block (two blocks per SM)
 constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue ticket, one per warp
 constexpr int kWarpMax = 32;         // items with at most this many digis are clustered by one warp
 constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory
@@ -53,7 +53,7 @@ struct Workspace {
     uint32_t *ctl;        // [16]: 0 group ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier
     uint32_t *event_err;  // [E]
     uint32_t *count;      // [E*M]
-    unsigned long long *chain; // [n_groups]
+    unsigned long long *chain; // [2 * n_groups]: ticket aggregates, then inclusive prefixes
     size_t zero_bytes;
     uint32_t *boff;       // [E*M] bucket start of each item
     uint32_t *cursor;     // [E*M] scatter cursor

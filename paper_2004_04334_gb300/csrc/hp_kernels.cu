@@ -351,22 +351,34 @@ __device__ __forceinline__ uint32_t uf_find(const uint32_t *parent, uint32_t x)
     return x;
 }
 
-// Lock-free union of the trees of a and b: the larger root is linked under
-// the smaller with atomicMin; a lost race re-runs with the new parent.
-__device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t b)
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+// Lock-free union of the trees of a and b, for all 32 lanes of a warp in
+// lockstep (lanes with b == kNoSlot idle; the whole warp must call it): the
+// larger root is linked under the smaller with atomicMin, and a lost race
+// re-runs with the new parent.
+__device__ __forceinline__ void warp_union(uint32_t *parent, uint32_t a, uint32_t b)
 {
-    for (;;) {
-        a = uf_find(parent, a);
-        b = uf_find(parent, b);
-        if (a == b) return;
-        if (a < b) {
-            const uint32_t t = a;
-            a = b;
-            b = t;
+    bool done = b == kNoSlot;
+    while (__any_sync(kFull, !done)) {
+        if (!done) {
+            a = uf_find(parent, a);
+            b = uf_find(parent, b);
+            if (a == b) {
+                done = true;
+            } else {
+                if (a < b) {
+                    const uint32_t t = a;
+                    a = b;
+                    b = t;
+                }
+                const uint32_t old = atomicMin(&parent[a], b);
+                if (old == a)
+                    done = true;
+                else
+                    a = old;
+            }
         }
-        const uint32_t old = atomicMin(&parent[a], b);
-        if (old == a) return;
-        a = old;
     }
 }
 
@@ -540,19 +552,38 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     });
     __syncthreads();
 
-    // union with the surviving backward neighbours (the left one is the previous slot)
-    for_digis(bw, n, [&](uint32_t, uint32_t w) {
-        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
-        if (!has_bit(sbits, lin)) return;
-        const uint32_t s = rank_of(sbits, spre, lin);
-        if (c > 0 && has_bit(sbits, lin - 1)) uf_union(t.parent, s, s - 1);
-        if (r > 0) {
-            const uint32_t up = lin - C;
-            if (c > 0 && has_bit(sbits, up - 1)) uf_union(t.parent, s, rank_of(sbits, spre, up - 1));
-            if (has_bit(sbits, up)) uf_union(t.parent, s, rank_of(sbits, spre, up));
-            if (c + 1 < C && has_bit(sbits, up + 1)) uf_union(t.parent, s, rank_of(sbits, spre, up + 1));
+    // Union with the surviving backward neighbours.  A decision tree keeps at
+    // most two unions per pixel: when the pixel above survives it alone
+    // suffices (the left and upper-left neighbours reach it through their own
+    // unions, row by row); otherwise the left one (the previous slot), the
+    // upper-left one only when there is no left one, and the upper-right one.
+    // The lanes of a warp walk the item in step and union in lockstep.
+    {
+        const uint32_t lane = tid & 31;
+        for (uint32_t k0 = tid - lane; k0 < n; k0 += kCCThreads) {
+            const uint32_t k = k0 + lane;
+            uint32_t s = 0, nb0 = kNoSlot, nb1 = kNoSlot;
+            if (k < n) {
+                const uint32_t w = __ldg(bw + k);
+                const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
+                if (has_bit(sbits, lin)) {
+                    s = rank_of(sbits, spre, lin);
+                    const uint32_t up = lin - C;
+                    if (r > 0 && has_bit(sbits, up)) {
+                        nb0 = rank_of(sbits, spre, up);
+                    } else {
+                        if (c > 0 && has_bit(sbits, lin - 1))
+                            nb0 = s - 1;
+                        else if (r > 0 && c > 0 && has_bit(sbits, up - 1))
+                            nb0 = rank_of(sbits, spre, up - 1);
+                        if (r > 0 && c + 1 < C && has_bit(sbits, up + 1)) nb1 = rank_of(sbits, spre, up + 1);
+                    }
+                }
+            }
+            warp_union(t.parent, s, nb0);
+            warp_union(t.parent, s, nb1);
         }
-    });
+    }
     __syncthreads();
 
     // mark every root with its linear index (the root is the smallest slot = smallest index)
@@ -672,17 +703,20 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     return K;
 }
 
-// Ordered output across tickets.  Each ticket publishes its aggregate (the
-// number of clusters it staged) in chain[g] as soon as it is staged, without
-// waiting.  The prefix then spreads by a cooperative frontier: ctl[3] = F
-// means tickets below F carry their inclusive prefix.  Any warp may push F
-// forward: it reads the 32 tickets from F on, takes the run of consecutive
-// published aggregates, scans it on top of chain[F-1], publishes those
-// inclusive prefixes and raises F.  Racing warps compute identical values.
+// Ordered output across tickets.  chain[g] holds ticket g's aggregate (the
+// number of clusters it staged, flag bit 62), published by its owner as soon
+// as it is staged, without waiting; chain[ngroups + g] receives its inclusive
+// prefix (flag bit 63).  The prefix spreads by a cooperative frontier:
+// ctl[3] = F means tickets below F carry their inclusive prefix.  Any warp may
+// push F forward: it reads the aggregates of the 32 tickets from F on, scans
+// the run of consecutive published ones on top of the inclusive prefix of
+// F - 1, publishes those prefixes and raises F.  Racing warps compute and
+// write identical values.
 __device__ void advance_frontier(unsigned long long *chain, uint32_t *frontier, uint64_t ngroups)
 {
-    const unsigned long long kInc = 2ull << 62, kMask = (1ull << 62) - 1;
+    const unsigned long long kFlagInc = 1ull << 63, kMask = (1ull << 62) - 1;
     const uint32_t lane = threadIdx.x & 31;
+    unsigned long long *inc = chain + ngroups;
     for (int rounds = 0; rounds < 64; ++rounds) {
         uint32_t F = 0;
         if (lane == 0) F = *(volatile uint32_t *)frontier;
@@ -690,22 +724,22 @@ __device__ void advance_frontier(unsigned long long *chain, uint32_t *frontier, 
         if (F >= ngroups) return;
         unsigned long long prev = 0;
         if (F > 0) {
-            const unsigned long long pv = ld_acquire(&chain[F - 1]);
-            if ((pv >> 62) != 2) return; // the inclusive below F is not visible yet
+            const unsigned long long pv = ld_acquire(&inc[F - 1]);
+            if (!(pv & kFlagInc)) return; // the prefix below F is not visible yet
             prev = pv & kMask;
         }
         const uint64_t j = (uint64_t)F + lane;
-        const unsigned long long v = j < ngroups ? ld_acquire(&chain[j]) : 0ull;
-        const uint32_t avail = __ballot_sync(kFull, (v >> 62) != 0);
+        const unsigned long long a = j < ngroups ? ld_acquire(&chain[j]) : 0ull;
+        const uint32_t avail = __ballot_sync(kFull, (a >> 62) != 0);
         const uint32_t u = (~avail) ? (uint32_t)(__ffs(~avail) - 1) : 32u; // leading run of published tickets
         if (u == 0) return;
-        unsigned long long x = lane < u ? (v & kMask) : 0ull;
+        unsigned long long x = lane < u ? (a & kMask) : 0ull;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(kFull, x, o);
             if ((int)lane >= o) x += y;
         }
-        if (lane < u && (v >> 62) == 1) st_release(&chain[j], kInc | (prev + x));
+        if (lane < u) st_release(&inc[j], kFlagInc | (prev + x));
         __syncwarp();
         __threadfence();
         if (lane == 0) atomicMax(frontier, F + u);
@@ -713,7 +747,7 @@ __device__ void advance_frontier(unsigned long long *chain, uint32_t *frontier, 
     }
 }
 
-// Resolve ticket g (one full warp): its inclusive prefix once the frontier
+// Resolve ticket g (one full warp): its exclusive prefix once the frontier
 // has passed it.  Non-blocking mode returns false if it has not; blocking
 // mode keeps pushing the frontier, bounded by kSpinLimit (then kErrTimeout).
 // Every aggregate is published without waiting, so every blocking wait ends.
@@ -721,20 +755,19 @@ __device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uin
                               unsigned long long agg, bool blocking, unsigned long long *excl_out,
                               uint32_t *launch_err)
 {
-    const unsigned long long kMask = (1ull << 62) - 1;
+    const unsigned long long kFlagInc = 1ull << 63, kMask = (1ull << 62) - 1;
     const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long *inc = chain + ngroups;
     for (uint32_t spins = 0;; ++spins) {
         unsigned long long v = 0;
-        if (lane == 0) v = ld_acquire(&chain[g]);
+        if (lane == 0) v = ld_acquire(&inc[g]);
         v = __shfl_sync(kFull, v, 0);
-        if ((v >> 62) == 2) {
-            *excl_out = (v & kMask) - agg;
-            return true;
+        if (!(v & kFlagInc)) {
+            advance_frontier(chain, frontier, ngroups);
+            if (lane == 0) v = ld_acquire(&inc[g]);
+            v = __shfl_sync(kFull, v, 0);
         }
-        advance_frontier(chain, frontier, ngroups);
-        if (lane == 0) v = ld_acquire(&chain[g]);
-        v = __shfl_sync(kFull, v, 0);
-        if ((v >> 62) == 2) {
+        if (v & kFlagInc) {
             *excl_out = (v & kMask) - agg;
             return true;
         }
@@ -777,7 +810,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
 
     const uint64_t EM = (uint64_t)L.E * M;
     const uint64_t ngroups = (EM + kGroup - 1) / kGroup;
-    const unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62;
+    const unsigned long long kAgg = 1ull << 62;
     if (tid == 0) {
         s_head = 0;
         s_tail = 0;
@@ -852,7 +885,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
                         agg += s_K[i];
                     }
                     __threadfence();
-                    st_release(&L.ws.chain[g], (g == 0 ? kInc : kAgg) | agg);
+                    st_release(&L.ws.chain[g], kAgg | agg);
                     ++s_tail;
                 }
                 __syncthreads();
@@ -950,7 +983,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     w.ctl = reinterpret_cast<uint32_t *>(take(64));
     w.event_err = reinterpret_cast<uint32_t *>(take(4ull * E));
     w.count = reinterpret_cast<uint32_t *>(take(4ull * EM));
-    w.chain = reinterpret_cast<unsigned long long *>(take(8ull * ngroups));
+    w.chain = reinterpret_cast<unsigned long long *>(take(16ull * ngroups)); // aggregates, then inclusive prefixes
     off = (off + 255) & ~(size_t)255;
     w.zero_bytes = off;
     w.boff = reinterpret_cast<uint32_t *>(take(4ull * EM));
