@@ -364,15 +364,17 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
         if len(inflight) >= 2:
             ev = inflight.pop(0)
             ev.wait(120)
-            r = ev.fetch()
+            r = ev.fetch(copy=False)
+            nc, st = r.n_clusters, r.status
             ev.release()
     for ev in inflight:
         ev.wait(120)
-        r = ev.fetch()
+        r = ev.fetch(copy=False)
+        nc, st = r.n_clusters, r.status
         ev.release()
     barrier()
     t_e2e = time.perf_counter() - t0
-    assert r.status == hp.HP_OK and r.n_clusters == n_clusters
+    assert st == hp.HP_OK and nc == n_clusters
     if world > 1:
         t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

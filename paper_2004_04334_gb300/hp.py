@@ -143,11 +143,12 @@ class Result:
                       None, self.tag)
 
 
-def _arr(ptr, n, dtype):
+def _arr(ptr, n, dtype, copy=True):
     if n == 0 or not ptr:
         return np.empty(0, dtype)
     buf = (ctypes.c_char * (n * np.dtype(dtype).itemsize)).from_address(ptr)
-    return np.frombuffer(buf, dtype=dtype, count=n).copy()
+    a = np.frombuffer(buf, dtype=dtype, count=n)
+    return a.copy() if copy else a
 
 
 # Python-side completion dispatch: one C callback for all events.
@@ -218,16 +219,19 @@ class Event:
     def stream(self) -> int:
         return int(self._ctx._lib.hp_event_stream(self._h) or 0)
 
-    def fetch(self) -> Result:
+    def fetch(self, copy: bool = True) -> Result:
+        """The event's results.  copy=False returns numpy views of the
+        library's pinned buffers, valid only until release()."""
         v = ClustersView()
         st = self._ctx._lib.hp_fetch_clusters(self._h, ctypes.byref(v))
         if st == HP_ENOTREADY:
             raise HPError(st, "hp_fetch_clusters")
         E, N, C = v.n_events, v.n_digis, v.n_clusters
-        return Result(st, E, _arr(v.cluster_offsets, E + 1, np.uint64), _arr(v.event_status, E, np.int32),
-                      _arr(v.module, C, np.uint32), _arr(v.id, C, np.int32), _arr(v.charge, C, np.int32),
-                      _arr(v.npix, C, np.int32), _arr(v.x, C, np.float32), _arr(v.y, C, np.float32),
-                      _arr(v.label, N, np.int32) if v.label else None, int(v.tag))
+        a = lambda p, n, t: _arr(p, n, t, copy)  # noqa: E731
+        return Result(st, E, a(v.cluster_offsets, E + 1, np.uint64), a(v.event_status, E, np.int32),
+                      a(v.module, C, np.uint32), a(v.id, C, np.int32), a(v.charge, C, np.int32),
+                      a(v.npix, C, np.int32), a(v.x, C, np.float32), a(v.y, C, np.float32),
+                      a(v.label, N, np.int32) if v.label else None, int(v.tag))
 
     def release(self):
         if not self._released:
