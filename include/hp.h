@@ -234,6 +234,30 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
                                 const uint32_t *d_words, const uint16_t *d_module_ids,
                                 const hp_device_clusters *out, void *stream);
 
+/*
+ * Allocation-free variant of hp_reconstruct_device, for callers that cannot
+ * allocate device memory: code that runs where cudaMalloc/cudaFree are not
+ * allowed or would stall the device (they synchronise), or under a
+ * framework whose own allocator owns the device memory.  (The paper has no
+ * counterpart; it is an addition of this library.)
+ *
+ * Same arguments, work and outputs as hp_reconstruct_device, but the scratch
+ * is one fixed 24 MiB device array inside the library, so the call makes no
+ * cudaMalloc, cudaFree or other allocating call.  That array exists on every
+ * GPU where the library is used, for the life of the process.
+ * Limits: n_digis <= 131072 and n_events * n_modules <= 16384 per call, else
+ * HP_ECAPACITY (nothing is launched).  The first call on a device looks the
+ * array up on that device (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array and each call
+ * overwrites what the previous one left in it: calls whose work overlaps on
+ * the GPU (different streams, or another thread) race and corrupt each
+ * other; serialise them, e.g. on one stream.
+ * Errors: HP_EINVAL, HP_ECAPACITY, HP_ECUDA.
+ */
+hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                                        const uint32_t *d_words, const uint16_t *d_module_ids,
+                                        const hp_device_clusters *out, void *stream);
+
 hp_status hp_get_stats(hp_ctx *ctx, hp_stats *out);
 
 /*

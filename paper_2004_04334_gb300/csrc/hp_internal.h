@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+struct hp_ctx;
+
 namespace hp {
 
 // Error bits accumulated on the device (per event, and per launch).
@@ -95,5 +97,10 @@ extern const char *const kKernelNames[kNumKernels];
 // Queue the whole reconstruction of one launch on `stream` (memset + kernels).
 cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count,
                                cudaEvent_t *marks = nullptr);
+
+// Launch parameters of a context (implemented by the runtime): geometry with
+// device calibration pointers, device ordinal, clustering grid size, and
+// whether the context has failed.
+bool context_launch_params(hp_ctx *ctx, Geometry *g, int *device, int *cc_grid);
 
 } // namespace hp

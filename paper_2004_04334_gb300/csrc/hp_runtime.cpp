@@ -540,6 +540,15 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
 
 } // namespace
 
+bool hp::context_launch_params(hp_ctx *ctx, hp::Geometry *g, int *device, int *cc_grid)
+{
+    if (!ctx || ctx->failed.load()) return false;
+    *g = geometry(ctx);
+    *device = ctx->device;
+    *cc_grid = ctx->cc_grid;
+    return true;
+}
+
 extern "C" {
 
 const char *hp_status_string(hp_status st)

@@ -25,7 +25,8 @@ HP_INPUT_NOCOPY = 0x2
 # Every function that include/hp.h declares.
 EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "hp_enqueue_batch", "hp_on_complete",
            "hp_event_query", "hp_fetch_clusters", "hp_release_event", "hp_event_device", "hp_event_stream",
-           "hp_event_cuda_event", "hp_event_latency_ns", "hp_reconstruct_device", "hp_get_stats",
+           "hp_event_cuda_event", "hp_event_latency_ns", "hp_reconstruct_device", "hp_reconstruct_device_noalloc",
+           "hp_get_stats",
            "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations")
 
 
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
             "hp_event_cuda_event": (V, [V]),
             "hp_event_latency_ns": (U64, [V]),
             "hp_reconstruct_device": (I, [V, U32, U64, V, V, V, P(DeviceClusters), V]),
+            "hp_reconstruct_device_noalloc": (I, [V, U32, U64, V, V, V, P(DeviceClusters), V]),
             "hp_get_stats": (I, [V, P(Stats)]),
             "hp_profile_enable": (I, [V, U32]),
             "hp_profile_read": (I, [V, U32, P(ctypes.c_char_p), P(ctypes.c_double), P(U64), P(U32)]),
