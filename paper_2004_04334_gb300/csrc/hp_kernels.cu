@@ -64,19 +64,6 @@ __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long 
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Largest e in [lo, hi] with off[e] <= k (requires off[lo] <= k).
-__device__ __forceinline__ uint32_t find_event(const uint64_t *off, uint32_t lo, uint32_t hi, uint64_t k)
-{
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= k)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 // Exclusive scan of one value per thread over a block of T threads.
 template <int T>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t *total)
@@ -166,13 +153,28 @@ __device__ __forceinline__ void load_words(const Launch &L, uint64_t k0, uint64_
     }
 }
 
-// Event of each of the thread's digis (events are contiguous, so walk forward
-// from a binary search for the first one).
-__device__ __forceinline__ void digi_events(const Launch &L, uint32_t ef, uint32_t el, uint64_t k0,
-                                            uint32_t e_of[kPerThread])
+// Event of each of the thread's digis: a binary search over the block's
+// event offsets (in shared memory when they fit), then a forward walk.
+constexpr uint32_t kChunkEvents = 512; // event offsets a block keeps in shared memory
+
+__device__ __forceinline__ void digi_events(const Launch &L, const uint64_t *s_off, uint32_t ef, uint32_t el,
+                                            uint64_t k0, uint32_t e_of[kPerThread])
 {
-    uint32_t e = ef == el ? ef : find_event(L.offsets, ef, el, k0);
-    uint64_t next = e < el ? L.offsets[e + 1] : ~0ull;
+    uint32_t e = ef;
+    if (ef != el) {
+        const bool in_sh = el - ef + 1 < kChunkEvents;
+        uint32_t lo = ef, hi = el;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            const uint64_t o = in_sh ? s_off[mid - ef] : L.offsets[mid];
+            if (o <= k0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        e = lo;
+    }
+    uint64_t next = e < el ? (el - ef + 1 < kChunkEvents ? s_off[e + 1 - ef] : L.offsets[e + 1]) : ~0ull;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         while (k0 + j >= next) {
@@ -181,6 +183,28 @@ __device__ __forceinline__ void digi_events(const Launch &L, uint32_t ef, uint32
         }
         e_of[j] = e;
     }
+}
+
+// Largest e in [lo, hi] with off[e] <= k (requires off[lo] <= k), by one
+// full warp: 32 probes per round shrink the interval 32-fold.
+__device__ __forceinline__ uint32_t find_event_warp(const uint64_t *off, uint32_t lo, uint32_t hi, uint64_t k)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    while (lo < hi) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t p = min(hi, lo + (lane + 1) * step);
+        const uint32_t le = __ballot_sync(kFull, off[p] <= k);
+        if (le == 0) {
+            hi = lo + step - 1;
+        } else {
+            const uint32_t t = 31 - __clz(le);
+            const uint32_t pt = min(hi, lo + (t + 1) * step);
+            if (t < 31) hi = min(hi, lo + (t + 2) * step) - 1;
+            lo = pt;
+            if (hi < lo) hi = lo;
+        }
+    }
+    return lo;
 }
 
 // bins[key] += 1 for every active lane with one atomic per distinct key of
@@ -204,18 +228,24 @@ struct ChunkInfo {
     bool use_sh;
 };
 
-__device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint32_t *s_ev)
+__device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint32_t *s_ev, uint64_t *s_off)
 {
     ChunkInfo ci;
     ci.c0 = (uint64_t)blockIdx.x * kChunk;
     ci.c1 = min(L.N, ci.c0 + (uint64_t)kChunk);
-    if (threadIdx.x == 0) {
-        s_ev[0] = find_event(L.offsets, 0, L.E - 1, ci.c0);
-        s_ev[1] = find_event(L.offsets, s_ev[0], L.E - 1, ci.c1 - 1);
+    if (threadIdx.x < 32) {
+        const uint32_t ef = find_event_warp(L.offsets, 0, L.E - 1, ci.c0);
+        const uint32_t el = find_event_warp(L.offsets, ef, L.E - 1, ci.c1 - 1);
+        if (threadIdx.x == 0) {
+            s_ev[0] = ef;
+            s_ev[1] = el;
+        }
     }
     __syncthreads();
     ci.ef = s_ev[0];
     ci.el = s_ev[1];
+    if (ci.el - ci.ef + 1 < kChunkEvents)
+        for (uint32_t i = threadIdx.x; i <= ci.el - ci.ef + 1; i += kHistThreads) s_off[i] = L.offsets[ci.ef + i];
     const uint64_t nk = (uint64_t)(ci.el - ci.ef + 1) * L.g.M;
     ci.use_sh = nk <= (uint64_t)kHistCap;
     ci.nkeys = ci.use_sh ? (uint32_t)nk : 0u;
@@ -227,14 +257,15 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
     __shared__ uint32_t s_ev[2];
-    const ChunkInfo ci = chunk_info(L, s_ev);
+    __shared__ uint64_t s_off[kChunkEvents + 1];
+    const ChunkInfo ci = chunk_info(L, s_ev, s_off);
     const uint32_t M = L.g.M;
     for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) sh[i] = 0;
-    __syncthreads();
     const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
     uint32_t m[kPerThread], e_of[kPerThread];
     load_modules(L, k0, ci.c1, m);
-    digi_events(L, ci.ef, ci.el, k0, e_of);
+    __syncthreads();
+    digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         const bool present = k0 + j < ci.c1;
@@ -279,15 +310,16 @@ __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
     uint32_t *cnt = sh;
     uint32_t *bas = sh + kHistCap;
     __shared__ uint32_t s_ev[2];
-    const ChunkInfo ci = chunk_info(L, s_ev);
+    __shared__ uint64_t s_off[kChunkEvents + 1];
+    const ChunkInfo ci = chunk_info(L, s_ev, s_off);
     const uint32_t M = L.g.M;
     for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) cnt[i] = 0;
-    __syncthreads();
     const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
     uint32_t m[kPerThread], e_of[kPerThread], w[kPerThread], rank[kPerThread];
     load_modules(L, k0, ci.c1, m);
     load_words(L, k0, ci.c1, w);
-    digi_events(L, ci.ef, ci.el, k0, e_of);
+    __syncthreads();
+    digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         const bool ok = k0 + j < ci.c1 && m[j] < M;
