@@ -516,6 +516,20 @@ __device__ __forceinline__ void for_digis(const uint32_t *bw, uint32_t n, F &&f)
     for (uint32_t k = threadIdx.x; k < n; k += kCCThreads) f(k, __ldg(bw + k));
 }
 
+// Centroid coordinate sum / Q from an exact, non-negative moment: integer
+// quotient plus the remainder fraction, so the float result is within a
+// few ulps whatever the magnitude.
+__device__ __forceinline__ float centroid_abs(long long sum, int32_t Q)
+{
+    if (sum < 0x80000000LL) {
+        const uint32_t su = (uint32_t)sum, qu = (uint32_t)Q;
+        const uint32_t qt = su / qu;
+        return (float)qt + (float)(su - qt * qu) / (float)Q;
+    }
+    const long long qt = sum / Q;
+    return (float)qt + (float)(sum - qt * Q) / (float)Q;
+}
+
 // One item clustered by the whole block (see the file comment).  kBig: the
 // tile lives in global scratch instead of shared memory.  Returns the number
 // of kept clusters (uniform over the block).
@@ -525,7 +539,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
 {
     const uint32_t R = L.g.R, C = L.g.C, nwords = (R * C + 31) >> 5;
     const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
-    const uint32_t tid = threadIdx.x, n = it.n;
+    const uint32_t tid = threadIdx.x, n = it.n, lane = tid & 31, warp = tid >> 5;
     const uint32_t *bw = L.ws.bucket_w + it.b;
     const uint32_t *bi = L.ws.bucket_i + it.b;
     const int32_t gain = it.gain, ped = it.ped;
@@ -572,16 +586,11 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         spre[i] = run;
         run += __popc(sbits[i]);
     }
-    __syncthreads();
-
-    for_digis(bw, n, [&](uint32_t, uint32_t w) {
-        const uint32_t lin = lin_of(w);
-        if (!has_bit(sbits, lin)) return;
-        const uint32_t s = rank_of(sbits, spre, lin);
+    for (uint32_t s = tid; s < S; s += kCCThreads) {
         t.parent[s] = s;
         t.qn[s] = 0;
         t.m[s] = make_int2(0, 0);
-    });
+    }
     __syncthreads();
 
     // Union with the surviving backward neighbours.  A decision tree keeps at
@@ -590,83 +599,60 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     // unions, row by row); otherwise the left one (the previous slot), the
     // upper-left one only when there is no left one, and the upper-right one.
     // The lanes of a warp walk the item in step and union in lockstep.
-    {
-        const uint32_t lane = tid & 31;
-        for (uint32_t k0 = tid - lane; k0 < n; k0 += kCCThreads) {
-            const uint32_t k = k0 + lane;
-            uint32_t s = 0, nb0 = kNoSlot, nb1 = kNoSlot;
-            if (k < n) {
-                const uint32_t w = __ldg(bw + k);
-                const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
-                if (has_bit(sbits, lin)) {
-                    s = rank_of(sbits, spre, lin);
-                    const uint32_t up = lin - C;
-                    if (r > 0 && has_bit(sbits, up)) {
-                        nb0 = rank_of(sbits, spre, up);
-                    } else {
-                        if (c > 0 && has_bit(sbits, lin - 1))
-                            nb0 = s - 1;
-                        else if (r > 0 && c > 0 && has_bit(sbits, up - 1))
-                            nb0 = rank_of(sbits, spre, up - 1);
-                        if (r > 0 && c + 1 < C && has_bit(sbits, up + 1)) nb1 = rank_of(sbits, spre, up + 1);
-                    }
+    for (uint32_t k0 = tid - lane; k0 < n; k0 += kCCThreads) {
+        const uint32_t k = k0 + lane;
+        uint32_t s = 0, nb0 = kNoSlot, nb1 = kNoSlot;
+        if (k < n) {
+            const uint32_t w = __ldg(bw + k);
+            const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
+            if (has_bit(sbits, lin)) {
+                s = rank_of(sbits, spre, lin);
+                const uint32_t up = lin - C;
+                if (r > 0 && has_bit(sbits, up)) {
+                    nb0 = rank_of(sbits, spre, up);
+                } else {
+                    if (c > 0 && has_bit(sbits, lin - 1))
+                        nb0 = s - 1;
+                    else if (r > 0 && c > 0 && has_bit(sbits, up - 1))
+                        nb0 = rank_of(sbits, spre, up - 1);
+                    if (r > 0 && c + 1 < C && has_bit(sbits, up + 1)) nb1 = rank_of(sbits, spre, up + 1);
                 }
             }
-            warp_union(t.parent, s, nb0);
-            warp_union(t.parent, s, nb1);
         }
+        warp_union(t.parent, s, nb0);
+        warp_union(t.parent, s, nb1);
     }
     __syncthreads();
 
-    // mark every root with its linear index (the root is the smallest slot = smallest index)
-    for_digis(bw, n, [&](uint32_t, uint32_t w) {
-        const uint32_t lin = lin_of(w);
-        if (!has_bit(sbits, lin)) return;
-        const uint32_t s = rank_of(sbits, spre, lin);
-        if (t.parent[s] == s) t.parent[s] = kMark | lin;
-    });
-    __syncthreads();
-
-    // charge, size and 32-bit moments about the root pixel; compress to the root
+    // Charge, size and absolute moments per root.  Each pixel walks to its
+    // root (the smallest slot); a root's own pixel marks it with kMark | its
+    // linear index (the cluster id), the others compress to it.  Moments
+    // accumulate in 32 bits; a cluster heavier than kQSafe32 (possible
+    // overflow) sends the item through the exact 64-bit pass below.
     for_digis(bw, n, [&](uint32_t, uint32_t w) {
         const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
         const volatile uint32_t *vp = t.parent;
         uint32_t x = s, p = vp[s];
-        while (!(p & kMark)) {
+        while (p != x && !(p & kMark)) {
             x = p;
             p = vp[x];
         }
-        if (x != s) t.parent[s] = x;
-        const uint32_t rl = p & ~kMark;
-        const int32_t rr = (int32_t)(rl / C), rc = (int32_t)(rl - (uint32_t)rr * C);
+        t.parent[s] = x == s ? (kMark | lin) : x;
         const int32_t q = charge(w);
-        atomicAdd(&t.qn[x], ((unsigned long long)q << 17) | 1ull);
-        atomicAdd(&t.m[x].x, q * ((int32_t)r - rr));
-        atomicAdd(&t.m[x].y, q * ((int32_t)c - rc));
-    });
-    __syncthreads();
-
-    // heavy clusters: recompute their moments exactly in 64 bits
-    for_digis(bw, n, [&](uint32_t, uint32_t w) {
-        const uint32_t lin = lin_of(w);
-        if (!has_bit(sbits, lin)) return;
-        const uint32_t s = rank_of(sbits, spre, lin);
-        if ((t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) > kQSafe32) bs.heavy = 1;
+        const unsigned long long old = atomicAdd(&t.qn[x], ((unsigned long long)q << 17) | 1ull);
+        if ((int32_t)(old >> 17) + q > kQSafe32) bs.heavy = 1;
+        atomicAdd(&t.m[x].x, q * (int32_t)r);
+        atomicAdd(&t.m[x].y, q * (int32_t)c);
     });
     __syncthreads();
     const bool heavy = bs.heavy != 0;
     if (heavy) {
-        for_digis(bw, n, [&](uint32_t, uint32_t w) {
-            const uint32_t lin = lin_of(w);
-            if (!has_bit(sbits, lin)) return;
-            const uint32_t s = rank_of(sbits, spre, lin);
-            if (t.parent[s] & kMark) {
-                t.exact[2 * s] = 0;
-                t.exact[2 * s + 1] = 0;
-            }
-        });
+        for (uint32_t s = tid; s < S; s += kCCThreads) {
+            t.exact[2 * s] = 0;
+            t.exact[2 * s + 1] = 0;
+        }
         __syncthreads();
         for_digis(bw, n, [&](uint32_t, uint32_t w) {
             const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
@@ -674,11 +660,9 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
             const uint32_t s = rank_of(sbits, spre, lin);
             const uint32_t p = t.parent[s];
             const uint32_t x = (p & kMark) ? s : p;
-            const uint32_t rl = t.parent[x] & ~kMark;
-            const long long rr = rl / C, rc = rl - (rl / C) * C;
             const long long q = charge(w);
-            atomicAdd(&t.exact[2 * x], (unsigned long long)(q * ((long long)r - rr)));
-            atomicAdd(&t.exact[2 * x + 1], (unsigned long long)(q * ((long long)c - rc)));
+            atomicAdd(&t.exact[2 * x], (unsigned long long)(q * (long long)r));
+            atomicAdd(&t.exact[2 * x + 1], (unsigned long long)(q * (long long)c));
         });
         __syncthreads();
     }
@@ -694,28 +678,43 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
                 const uint32_t px = (p & kMark) ? p : t.parent[x];
                 lab = (int32_t)(t.qn[x] >> 17) >= cthr ? (int32_t)(px & ~kMark) : -2;
             }
-            it.label_e[bi[k]] = lab;
+            it.label_e[__ldg(bi + k)] = lab;
         });
     }
 
-    // kept roots in slot order (= id order) -> ordinals -> staging
-    const uint32_t sper = (S + kCCThreads - 1) / kCCThreads;
-    const uint32_t s0 = min(S, tid * sper), s1 = min(S, s0 + sper);
-    uint32_t cnt = 0;
-    for (uint32_t s = s0; s < s1; ++s)
-        if ((t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) >= cthr) ++cnt;
+    // Kept roots in slot order (= id order): one ballot per 32 consecutive
+    // slots (kept into abits, free since the bitmaps were built), an
+    // exclusive scan of their popcounts (into spre, free once the labels are
+    // written), then each kept root writes its record at its ordinal.
+    const uint32_t chunks = (S + 31) >> 5;
+    constexpr uint32_t kWarps = kCCThreads / 32;
+    for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+        const uint32_t s = (ch << 5) + lane;
+        const bool kept = s < S && (t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) >= cthr;
+        const uint32_t bal = __ballot_sync(kFull, kept);
+        if (lane == 0) abits[ch] = bal;
+    }
+    __syncthreads();
+    const uint32_t cper = (chunks + kCCThreads - 1) / kCCThreads;
+    const uint32_t c0 = min(chunks, tid * cper), c1 = min(chunks, c0 + cper);
+    uint32_t cl = 0;
+    for (uint32_t ch = c0; ch < c1; ++ch) cl += __popc(abits[ch]);
     uint32_t K;
-    uint32_t ord = block_exclusive_scan<kCCThreads>(cnt, bs.scan_tmp, &K);
-    for (uint32_t s = s0; s < s1; ++s) {
-        const uint32_t p = t.parent[s];
-        if (!(p & kMark)) continue;
+    uint32_t crun = block_exclusive_scan<kCCThreads>(cl, bs.scan_tmp, &K);
+    for (uint32_t ch = c0; ch < c1; ++ch) {
+        spre[ch] = crun;
+        crun += __popc(abits[ch]);
+    }
+    __syncthreads();
+    for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+        const uint32_t s = (ch << 5) + lane;
+        const uint32_t bal = abits[ch];
+        if (!((bal >> lane) & 1u)) continue;
+        const uint32_t ord = spre[ch] + __popc(bal & ((1u << lane) - 1u));
         const unsigned long long qn = t.qn[s];
         const int32_t Q = (int32_t)(qn >> 17);
-        if (Q < cthr) continue;
-        const uint32_t id = p & ~kMark;
-        const int32_t rr = (int32_t)(id / C), rc = (int32_t)(id - (uint32_t)rr * C);
         long long mr, mc;
-        if (heavy && Q > kQSafe32) {
+        if (heavy) {
             mr = (long long)t.exact[2 * s];
             mc = (long long)t.exact[2 * s + 1];
         } else {
@@ -724,13 +723,13 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
             mc = mm.y;
         }
         StagedCluster o;
-        o.id = (int32_t)id;
+        o.id = (int32_t)(t.parent[s] & ~kMark);
         o.charge = Q;
         o.npix = (int32_t)(qn & 0x1FFFFull);
-        o.x = centroid(rr, mr, Q);
-        o.y = centroid(rc, mc, Q);
+        o.x = centroid_abs(mr, Q);
+        o.y = centroid_abs(mc, Q);
         o.pad = 0;
-        L.ws.staging[it.b + ord++] = o;
+        L.ws.staging[it.b + ord] = o;
     }
     return K;
 }
