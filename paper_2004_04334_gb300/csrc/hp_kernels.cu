@@ -207,21 +207,6 @@ __device__ __forceinline__ uint32_t find_event_warp(const uint64_t *off, uint32_
     return lo;
 }
 
-// bins[key] += 1 for every active lane with one atomic per distinct key of
-// the warp; returns the old bin value plus the lane's rank among its peers.
-// Must be called by all 32 lanes.
-__device__ __forceinline__ uint32_t warp_bin_add(uint32_t *bins, uint32_t key, bool active)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t k = active ? key : 0xFFFFFFFFu - lane;
-    const uint32_t peers = __match_any_sync(kFull, k);
-    const uint32_t leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (active && lane == leader) base = atomicAdd(&bins[key], (uint32_t)__popc(peers));
-    base = __shfl_sync(kFull, base, leader);
-    return base + __popc(peers & ((1u << lane) - 1u));
-}
-
 struct ChunkInfo {
     uint64_t c0, c1, keybase;
     uint32_t ef, el, nkeys;
@@ -253,33 +238,47 @@ __device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint32_t *s_ev,
     return ci;
 }
 
+// Shared-memory histogram of a block: with few (event, module) keys every
+// warp counts into its own sub-histogram (atomics collide only inside a
+// warp), else one shared histogram.
+constexpr uint32_t kHistWarps = kHistThreads / 32;
+constexpr uint32_t kSubKeys = kHistCap / kHistWarps; // keys per warp sub-histogram
+
 __global__ void __launch_bounds__(kHistThreads) hist_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
     const ChunkInfo ci = chunk_info(L, s_ev, s_off);
-    const uint32_t M = L.g.M;
-    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) sh[i] = 0;
+    const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
+    const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
+    const uint32_t nbins = sub ? ci.nkeys * kHistWarps : ci.nkeys;
+    for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) sh[i] = 0;
     const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
     uint32_t m[kPerThread], e_of[kPerThread];
     load_modules(L, k0, ci.c1, m);
     __syncthreads();
     digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
+    uint32_t *bins = sub ? sh + warp * ci.nkeys : sh;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         const bool present = k0 + j < ci.c1;
         const bool ok = present && m[j] < M;
         if (present && !ok) atomicOr(&L.ws.event_err[e_of[j]], kErrBadDigi);
-        const uint64_t key = (uint64_t)e_of[j] * M + (ok ? m[j] : 0u);
+        if (!ok) continue;
+        const uint64_t key = (uint64_t)e_of[j] * M + m[j];
         if (ci.use_sh)
-            warp_bin_add(sh, (uint32_t)(key - ci.keybase), ok);
-        else if (ok)
+            atomicAdd(&bins[key - ci.keybase], 1u);
+        else
             atomicAdd(&L.ws.count[key], 1u);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
-        const uint32_t v = sh[i];
+        uint32_t v = 0;
+        if (sub)
+            for (uint32_t w = 0; w < kHistWarps; ++w) v += sh[w * ci.nkeys + i];
+        else
+            v = sh[i];
         if (v) atomicAdd(&L.ws.count[ci.keybase + i], v);
     }
 }
@@ -307,40 +306,57 @@ __global__ void __launch_bounds__(256) scan_kernel(const Launch L)
 __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
-    uint32_t *cnt = sh;
-    uint32_t *bas = sh + kHistCap;
+    uint32_t *cnt = sh;             // counts: per warp sub-histograms, or one histogram
+    uint32_t *bas = sh + kHistCap;  // single-histogram mode: base of each key
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
     const ChunkInfo ci = chunk_info(L, s_ev, s_off);
-    const uint32_t M = L.g.M;
-    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) cnt[i] = 0;
+    const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
+    const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
+    const uint32_t nbins = sub ? ci.nkeys * kHistWarps : ci.nkeys;
+    for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) cnt[i] = 0;
     const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
     uint32_t m[kPerThread], e_of[kPerThread], w[kPerThread], rank[kPerThread];
     load_modules(L, k0, ci.c1, m);
     load_words(L, k0, ci.c1, w);
     __syncthreads();
     digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
+    uint32_t *bins = sub ? cnt + warp * ci.nkeys : cnt;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         const bool ok = k0 + j < ci.c1 && m[j] < M;
-        const uint64_t key = (uint64_t)e_of[j] * M + (ok ? m[j] : 0u);
-        if (ci.use_sh)
-            rank[j] = warp_bin_add(cnt, (uint32_t)(key - ci.keybase), ok);
-        else
-            rank[j] = ok ? atomicAdd(&L.ws.cursor[key], 1u) : 0u;
-        if (!ok) m[j] = 0xFFFFFFFFu;
+        if (!ok) {
+            m[j] = 0xFFFFFFFFu;
+            continue;
+        }
+        const uint64_t key = (uint64_t)e_of[j] * M + m[j];
+        rank[j] = ci.use_sh ? atomicAdd(&bins[key - ci.keybase], 1u) : atomicAdd(&L.ws.cursor[key], 1u);
     }
     __syncthreads();
+    // reserve each key's range in its bucket; sub-histogram mode turns the
+    // per-warp counts into per-warp bases (an exclusive scan over the warps)
     for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
-        const uint32_t v = cnt[i];
-        if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
+        if (sub) {
+            uint32_t tot = 0;
+            for (uint32_t wi = 0; wi < kHistWarps; ++wi) tot += cnt[wi * ci.nkeys + i];
+            uint32_t base = tot ? atomicAdd(&L.ws.cursor[ci.keybase + i], tot) : 0u;
+            for (uint32_t wi = 0; wi < kHistWarps; ++wi) {
+                const uint32_t c = cnt[wi * ci.nkeys + i];
+                cnt[wi * ci.nkeys + i] = base;
+                base += c;
+            }
+        } else {
+            const uint32_t v = cnt[i];
+            if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
+        }
     }
     __syncthreads();
+    const uint32_t *base_of = sub ? cnt + warp * ci.nkeys : bas;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         if (m[j] == 0xFFFFFFFFu) continue;
         const uint64_t key = (uint64_t)e_of[j] * M + m[j];
-        const uint32_t p = ci.use_sh ? bas[key - ci.keybase] + rank[j] : rank[j];
+        const uint32_t p = ci.use_sh ? base_of[key - ci.keybase] + rank[j] : rank[j];
         L.ws.bucket_w[p] = w[j];
         L.ws.bucket_i[p] = (uint32_t)(k0 + j - L.offsets[e_of[j]]);
     }
