@@ -440,6 +440,24 @@ __device__ __forceinline__ bool has_bit(const uint32_t *bits, uint32_t lin)
     return (bits[lin >> 5] >> (lin & 31)) & 1u;
 }
 
+// Number of surviving pixels immediately to the left of pixel lin in its row
+// (the pixel's offset in its horizontal run), read from the survivor bitmap
+// 32 bits at a time.
+__device__ __forceinline__ uint32_t run_offset(const uint32_t *sbits, uint32_t lin, uint32_t row0)
+{
+    uint32_t off = 0, pos = lin;
+    while (pos > row0) {
+        const uint32_t bt = (pos - 1) & 31;
+        const uint32_t x = ~sbits[(pos - 1) >> 5] << (31 - bt); // bit pos-1 moved to the top
+        const uint32_t ones = x ? (uint32_t)__clz(x) : bt + 1;  // set bits from pos-1 downwards
+        const uint32_t take = min(ones, pos - row0);
+        off += take;
+        pos -= take;
+        if (take < bt + 1) break;
+    }
+    return off;
+}
+
 // One item of at most 32 digis, clustered by one warp in registers: lane i
 // holds digi i; adjacency is a 32-bit mask per lane; the cluster id (the
 // smallest linear index) spreads over the adjacency by min-propagation.
@@ -602,36 +620,43 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         spre[i] = run;
         run += __popc(sbits[i]);
     }
-    for (uint32_t s = tid; s < S; s += kCCThreads) {
-        t.parent[s] = s;
+    __syncthreads();
+    // every surviving pixel starts in its horizontal run: parent = the run's
+    // first pixel, whose slot is the pixel's slot minus its run offset
+    for_digis(bw, n, [&](uint32_t, uint32_t w) {
+        const uint32_t r = w & 0xFFu, lin = lin_of(w);
+        if (!has_bit(sbits, lin)) return;
+        const uint32_t s = rank_of(sbits, spre, lin);
+        t.parent[s] = s - run_offset(sbits, lin, r * C);
         t.qn[s] = 0;
         t.m[s] = make_int2(0, 0);
-    }
+    });
     __syncthreads();
 
-    // Union with the surviving backward neighbours.  A decision tree keeps at
-    // most two unions per pixel: when the pixel above survives it alone
-    // suffices (the left and upper-left neighbours reach it through their own
-    // unions, row by row); otherwise the left one (the previous slot), the
-    // upper-left one only when there is no left one, and the upper-right one.
-    // The lanes of a warp walk the item in step and union in lockstep.
+    // Join runs of adjacent rows.  For a pixel p whose upper neighbour U
+    // survives, one union per maximal stretch of such pixels (at p = the run
+    // head, or where the upper-left pixel does not survive) joins p's run to
+    // U's run; a run head whose U is empty checks its upper-left pixel, a run
+    // tail whose U is empty its upper-right one.  Every 8-adjacency between
+    // two runs passes through one of these.  The lanes of a warp walk the
+    // item in step and union in lockstep.
     for (uint32_t k0 = tid - lane; k0 < n; k0 += kCCThreads) {
         const uint32_t k = k0 + lane;
         uint32_t s = 0, nb0 = kNoSlot, nb1 = kNoSlot;
         if (k < n) {
             const uint32_t w = __ldg(bw + k);
             const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
-            if (has_bit(sbits, lin)) {
+            if (r > 0 && has_bit(sbits, lin)) {
                 s = rank_of(sbits, spre, lin);
                 const uint32_t up = lin - C;
-                if (r > 0 && has_bit(sbits, up)) {
-                    nb0 = rank_of(sbits, spre, up);
+                const bool head = c == 0 || !has_bit(sbits, lin - 1);
+                const bool tail = c + 1 == C || !has_bit(sbits, lin + 1);
+                const bool ul = c > 0 && has_bit(sbits, up - 1);
+                if (has_bit(sbits, up)) {
+                    if (head || !ul) nb0 = rank_of(sbits, spre, up);
                 } else {
-                    if (c > 0 && has_bit(sbits, lin - 1))
-                        nb0 = s - 1;
-                    else if (r > 0 && c > 0 && has_bit(sbits, up - 1))
-                        nb0 = rank_of(sbits, spre, up - 1);
-                    if (r > 0 && c + 1 < C && has_bit(sbits, up + 1)) nb1 = rank_of(sbits, spre, up + 1);
+                    if (head && ul) nb0 = rank_of(sbits, spre, up - 1);
+                    if (tail && c + 1 < C && has_bit(sbits, up + 1)) nb1 = rank_of(sbits, spre, up + 1);
                 }
             }
         }
@@ -939,8 +964,10 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
             }
         }
 
-        // write out parked tickets whose prefix is known, oldest first
-        while (s_head != s_tail) {
+        // write out parked tickets whose prefix is known, oldest first (once
+        // half the ring is parked, or at the end)
+        const bool resolve_now = !tickets_left || s_tail - s_head >= (uint32_t)kRing / 2;
+        while (resolve_now && s_head != s_tail) {
             const bool blocking = !tickets_left || (s_tail - s_head) >= (uint32_t)kRing;
             const Pending &pd = ring[s_head % kRing];
             if (tid < 32) {
