@@ -57,6 +57,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--device-only", action="store_true",
                    help="only the device-resident timed loop (for profiler captures)")
+    p.add_argument("--serving-rates", default="5000,20000",
+                   help="Poisson arrival rates (events/s) of the serving measurement")
+    p.add_argument("--serving-events", type=int, default=2000, help="requests per serving rate")
+    p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
     return p.parse_args()
 
 
@@ -307,10 +311,12 @@ def run_ours(a):
     path_bytes = algorithmic_bytes(N, E, M, n_clusters)
     shares = {k: round(v[1] / max(1e-12, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
 
-    e2e = per_event = None
+    e2e = per_event = serving = None
     if not a.device_only:
         e2e, per_event = _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world)
     ctx.close()
+    if not a.device_only and rank == 0:
+        serving = run_serving(local, [float(x) for x in a.serving_rates.split(",") if x], a.serving_events)
 
     if rank == 0:
         line = {
@@ -331,6 +337,7 @@ def run_ours(a):
             "e2e": e2e,
             "per_event": per_event,
             "batched_vs_per_event": value / per_event["value"] if per_event else None,
+            "serving": serving,
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -421,10 +428,92 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
     return e2e, per_event
 
 
+def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=16 << 30):
+    """Serving workload: Poisson arrivals at each rate, event sizes lognormal
+    (median 80k digis, sigma 0.8, capped at 500k), 4 submitter threads, a
+    16 GB device budget, continuous batching; requests cycle over a pool of
+    pre-generated events.  Returns per-rate sustained events/s and p50/p99
+    submit-to-callback latency (measured by the library)."""
+    from paper_2004_04334_gb300 import hp
+
+    w = synth.workload("serving", n_events=pool_events)
+    out = []
+    with hp.Context(w.n_modules, w.gain, w.pedestal, device=local, want_labels=True, n_streams=4) as ctx:
+        ctx.serve_start(budget_bytes=budget, want_labels=True)
+        events = [w.event(e) for e in range(w.n_events)]
+        # warm the pools
+        for ev in [ctx.submit(*events[e]) for e in range(16)]:
+            ev.wait(60)
+            ev.release()
+        for k, rate in enumerate(rates):
+            gaps = synth.exponential(synth.child_seed(synth.BASE_SEED + 5, 1000 + k), n_requests, rate)
+            arrival = np.cumsum(gaps)
+            lat = np.zeros(n_requests)
+            t_done = np.zeros(n_requests)
+            ndigis = np.zeros(n_requests)
+            pending = threading.Semaphore(0)
+            status = []
+
+            def cb_for(i):
+                def cb(ev, st):
+                    lat[i] = ev.latency_ns * 1e-9
+                    t_done[i] = time.perf_counter()
+                    if st != hp.HP_OK:
+                        status.append(st)
+                    ev.release()
+                    pending.release()
+                return cb
+
+            t0 = time.perf_counter() + 0.01
+
+            def submitter(tid):
+                for i in range(tid, n_requests, submitters):
+                    while True:
+                        dt = t0 + arrival[i] - time.perf_counter()
+                        if dt <= 0:
+                            break
+                        if dt > 2e-4:
+                            time.sleep(dt - 1e-4)
+                    e = i % len(events)
+                    ndigis[i] = len(events[e][0])
+                    while True:
+                        st, ev = ctx.try_submit(*events[e], tag=i)
+                        if st == hp.HP_OK:
+                            break
+                        time.sleep(1e-4)
+                    ev.on_complete(cb_for(i))
+
+            ts = [threading.Thread(target=submitter, args=(t,)) for t in range(submitters)]
+            for t in ts:
+                t.start()
+            for t in ts:
+                t.join()
+            for _ in range(n_requests):
+                pending.acquire()
+            span = t_done.max() - t0
+            out.append({"rate_offered": rate, "requests": n_requests,
+                        "sustained_events_per_s": n_requests / span,
+                        "mdigis_per_s": ndigis.sum() / span / 1e6,
+                        "latency_ms_p50": float(np.percentile(lat, 50) * 1e3),
+                        "latency_ms_p99": float(np.percentile(lat, 99) * 1e3),
+                        "errors": len(status)})
+        stats = ctx.stats()
+        ctx.serve_stop()
+    return {"workload": f"serving: lognormal sizes (median 80k, sigma 0.8, cap 500k), pool of {pool_events} "
+                        f"events, {submitters} submitter threads, {budget >> 30} GB budget",
+            "batches": stats["serve_batches"], "rates": out}
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serving_only:
+        _, _, local = _dist()
+        from paper_2004_04334_gb300 import build
+        build.build()
+        print(json.dumps(run_serving(local, [float(x) for x in a.serving_rates.split(",") if x],
+                                     a.serving_events)), flush=True)
     else:
         run_ours(a)
 

@@ -142,7 +142,19 @@ typedef struct hp_stats {
     uint64_t inflight;          /* current */
     uint64_t h2d_bytes, d2h_bytes; /* bytes moved by cudaMemcpyAsync */
     uint64_t kernel_launches;   /* kernels launched by the library */
+    uint64_t serve_batches;     /* batches launched by the serving loop */
+    uint64_t serve_requests;    /* requests accepted by hp_submit */
 } hp_stats;
+
+/* Serving loop configuration (hp_serve_start). */
+typedef struct hp_serve_config {
+    size_t device_budget_bytes;    /* device bytes in-flight batches may hold; 0 = no limit */
+    uint32_t max_batch_events;     /* requests per batch; 0 = 256 */
+    uint64_t max_batch_digis;      /* digis per batch; 0 = 32 Mi */
+    uint32_t max_inflight_batches; /* batches on the device at once; 0 = 4 */
+    uint32_t max_pending;          /* queued requests before hp_submit says HP_EAGAIN; 0 = 65536 */
+    uint32_t flags;                /* HP_WANT_LABELS */
+} hp_serve_config;
 
 const char *hp_status_string(hp_status st);
 
@@ -257,6 +269,28 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
 hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
                                         const uint32_t *d_words, const uint16_t *d_module_ids,
                                         const hp_device_clusters *out, void *stream);
+
+/*
+ * Serving (continuous batching).  hp_serve_start starts an admitter thread.
+ * hp_submit is a non-blocking acquire() of one event (Sec. 2): it copies the
+ * inputs into pooled pinned staging and queues the request; it returns
+ * HP_EAGAIN only when max_pending requests already wait.  The admitter
+ * launches everything queued as one batch whenever fewer than
+ * max_inflight_batches batches run and the batch fits the device budget
+ * (Sec. 4.1: only asynchronous calls, pooled memory; batches overlap on the
+ * context's streams, so copies of one batch overlap compute of another).
+ * Each request is an hp_event with its own completion (cb, if given, is its
+ * hp_on_complete callback), status, latency and one-event view
+ * (hp_fetch_clusters); release each with hp_release_event.  hp_serve_stop
+ * launches what is still queued and waits for every batch (blocking;
+ * hp_destroy does it too).
+ * Errors: HP_EINVAL (not serving / already serving / bad arguments),
+ * HP_EAGAIN, HP_ENOMEM, HP_ECUDA.
+ */
+hp_status hp_serve_start(hp_ctx *ctx, const hp_serve_config *cfg);
+hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_ids, uint64_t n_digis, uint64_t tag,
+                    hp_callback cb, void *user, hp_event **out);
+hp_status hp_serve_stop(hp_ctx *ctx);
 
 hp_status hp_get_stats(hp_ctx *ctx, hp_stats *out);
 

@@ -98,6 +98,19 @@ extern const char *const kKernelNames[kNumKernels];
 cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count,
                                cudaEvent_t *marks = nullptr);
 
+// One request of a serving batch: its inputs in (mapped) pinned host memory
+// and where they go in the batch's device arrays.
+struct GatherEntry {
+    const uint32_t *words;
+    const uint16_t *modules;
+    uint64_t n;
+    uint64_t off;
+};
+// Copy every request's inputs into the batch's device arrays (reads the host
+// buffers over the C2C link; `table` must be device-accessible).
+cudaError_t launch_gather(const GatherEntry *table, uint32_t n_requests, uint64_t max_n, uint32_t *words,
+                          uint16_t *modules, cudaStream_t stream);
+
 // Launch parameters of a context (implemented by the runtime): geometry with
 // device calibration pointers, device ordinal, clustering grid size, and
 // whether the context has failed.

@@ -34,6 +34,7 @@
 // moments relative to the root pixel accumulate in 64-bit integers; the
 // ordinal of a kept cluster is the rank of its root among kept roots in slot
 // order, so the per-module output is already sorted by id.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -1033,7 +1034,26 @@ __global__ void finalize_kernel(const Launch L)
     L.out.event_status[e] = st;
 }
 
+// Serving batches: block (x, e) copies a slice of request e's digis.
+__global__ void __launch_bounds__(256) gather_kernel(const GatherEntry *table, uint32_t *words, uint16_t *modules)
+{
+    const GatherEntry g = table[blockIdx.y];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        words[g.off + i] = g.words[i];
+        modules[g.off + i] = g.modules[i];
+    }
+}
+
 } // namespace
+
+cudaError_t launch_gather(const GatherEntry *table, uint32_t n_requests, uint64_t max_n, uint32_t *words,
+                          uint16_t *modules, cudaStream_t stream)
+{
+    if (n_requests == 0 || max_n == 0) return cudaSuccess;
+    const uint64_t bx = std::min<uint64_t>(32, (max_n + 4095) / 4096);
+    gather_kernel<<<dim3((unsigned)bx, n_requests), 256, 0, stream>>>(table, words, modules);
+    return cudaGetLastError();
+}
 
 size_t cc_smem_bytes(uint32_t R, uint32_t C)
 {

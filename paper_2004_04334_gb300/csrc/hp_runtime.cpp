@@ -14,11 +14,14 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
 #include <set>
+#include <thread>
 #include <vector>
 
 #include "hp.h"
@@ -160,6 +163,9 @@ class Pool {
 
 constexpr uint32_t kDone = 1u, kCbSet = 2u, kCbDone = 4u, kReleaseReq = 8u;
 
+struct Serve;
+struct Batch;
+
 } // namespace
 
 struct hp_ctx {
@@ -189,6 +195,10 @@ struct hp_ctx {
     uint32_t prof_left = 0;
     std::vector<ProfRec> prof_used;
     std::vector<cudaEvent_t> prof_pool;
+    // serving loop (hp_serve_start / hp_submit / hp_serve_stop)
+    std::mutex serve_mu;
+    Serve *serve = nullptr;
+    std::atomic<uint64_t> serve_batches{0}, serve_requests{0};
 };
 
 struct hp_event {
@@ -211,6 +221,13 @@ struct hp_event {
     hp_callback cb = nullptr;
     void *user = nullptr;
     uint64_t t_enq = 0, t_done = 0;
+    // serving requests: the batch that carries the request and its index in it
+    bool request = false;
+    int32_t status_local = 0;
+    Batch *batch = nullptr;
+    uint32_t index = 0;
+    Block staging;               // the request's inputs (pinned), until its batch completes
+    uint64_t coff_local[2] = {0, 0};
 };
 
 namespace {
@@ -223,12 +240,17 @@ hp_status fail(hp_ctx *ctx)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+void release_batch_ref(Batch *b);
+
 // Free the host side of a completed, released event (no CUDA call).
 void destroy_event(hp_event *ev)
 {
     hp_ctx *ctx = ev->ctx;
-    ctx->hpool.free(ev->host);
-    {
+    if (ev->request) {
+        ctx->hpool.free(ev->staging);
+        if (ev->batch) release_batch_ref(ev->batch);
+    } else {
+        ctx->hpool.free(ev->host);
         std::lock_guard<std::mutex> g(ctx->cev_mu);
         ctx->cev_free.push_back(ev->done);
     }
@@ -237,6 +259,20 @@ void destroy_event(hp_event *ev)
         ctx->live.erase(ev);
     }
     delete ev;
+}
+
+// Completion of one event on the host-function thread: the exactly-once
+// hand-off to the callback (Sec. 2 holder) and a deferred release.
+void complete_event(hp_event *ev)
+{
+    const uint32_t prev = ev->state.fetch_or(kDone, std::memory_order_acq_rel);
+    if (prev & kCbSet) {
+        ev->cb(ev->user, ev, ev->status);
+        const uint32_t p2 = ev->state.fetch_or(kCbDone, std::memory_order_acq_rel);
+        if (p2 & kReleaseReq) destroy_event(ev);
+    } else if (prev & kReleaseReq) {
+        destroy_event(ev);
+    }
 }
 
 // Runs on the CUDA host-function thread once the event's stream work is done.
@@ -257,14 +293,7 @@ void CUDART_CB trampoline(void *p)
     ctx->dev_in_use.fetch_sub(ev->dev_charge);
     ctx->inflight.fetch_sub(1);
     ctx->completed.fetch_add(1);
-    const uint32_t prev = ev->state.fetch_or(kDone, std::memory_order_acq_rel);
-    if (prev & kCbSet) {
-        ev->cb(ev->user, ev, st);
-        const uint32_t p2 = ev->state.fetch_or(kCbDone, std::memory_order_acq_rel);
-        if (p2 & kReleaseReq) destroy_event(ev);
-    } else if (prev & kReleaseReq) {
-        destroy_event(ev);
-    }
+    complete_event(ev);
 }
 
 cudaEvent_t take_cuda_event(hp_ctx *ctx)
@@ -538,6 +567,314 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     return HP_OK;
 }
 
+
+// ------------------------------------------------------------------ serving
+
+// A batch of serving requests that runs as one device pass.
+struct Batch {
+    hp_ctx *ctx = nullptr;
+    Serve *sv = nullptr;
+    Block dev, host;
+    size_t dev_charge = 0;
+    uint32_t E = 0;
+    uint64_t N = 0;
+    bool labels = false;
+    std::vector<hp_event *> reqs;
+    std::atomic<uint32_t> refs{0}; // one per request, plus one while in flight
+    uint64_t *h_offs = nullptr, *h_coff = nullptr;
+    int32_t *h_status = nullptr, *h_id = nullptr, *h_charge = nullptr, *h_npix = nullptr, *h_label = nullptr;
+    uint32_t *h_module = nullptr;
+    float *h_x = nullptr, *h_y = nullptr;
+};
+
+// The continuous-batching admission loop of a context: requests queue here
+// and an admitter thread launches everything pending as one batch whenever a
+// batch slot is free and the batch fits the device budget.
+struct Serve {
+    hp_serve_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<hp_event *> pending;
+    uint32_t inflight_batches = 0;
+    bool stop = false;
+    std::thread admitter;
+};
+
+void release_batch_ref(Batch *b)
+{
+    if (b->refs.fetch_sub(1) == 1) {
+        b->ctx->hpool.free(b->host);
+        delete b;
+    }
+}
+
+// Complete requests that never reached the device (allocation or CUDA error).
+void fail_requests(hp_ctx *ctx, std::vector<hp_event *> &reqs, hp_status st)
+{
+    const uint64_t now = now_ns();
+    for (hp_event *r : reqs) {
+        r->status = st;
+        r->status_local = st;
+        r->coff_local[0] = r->coff_local[1] = 0;
+        r->h_coff = r->coff_local;
+        r->h_status = &r->status_local;
+        r->t_done = now;
+        ctx->completed.fetch_add(1);
+        complete_event(r);
+    }
+}
+
+// Host function after a batch: per-request status and result views, buffers
+// back to the pools, a free batch slot for the admitter, then every request's
+// completion hand-off.  No CUDA call.
+void CUDART_CB batch_done(void *p)
+{
+    Batch *b = static_cast<Batch *>(p);
+    hp_ctx *ctx = b->ctx;
+    const uint64_t now = now_ns();
+    for (uint32_t e = 0; e < b->E; ++e) {
+        hp_event *r = b->reqs[e];
+        const uint64_t c0 = b->h_coff[e], c1 = b->h_coff[e + 1];
+        r->status = (hp_status)b->h_status[e];
+        r->coff_local[0] = 0;
+        r->coff_local[1] = c1 >= c0 ? c1 - c0 : 0;
+        r->h_coff = r->coff_local;
+        r->h_status = b->h_status + e;
+        r->h_module = b->h_module + c0;
+        r->h_id = b->h_id + c0;
+        r->h_charge = b->h_charge + c0;
+        r->h_npix = b->h_npix + c0;
+        r->h_x = b->h_x + c0;
+        r->h_y = b->h_y + c0;
+        r->h_label = b->labels ? b->h_label + b->h_offs[e] : nullptr;
+        r->t_done = now;
+        ctx->hpool.free(r->staging);
+        r->staging = Block();
+    }
+    ctx->dpool.free(b->dev);
+    b->dev = Block();
+    ctx->dev_in_use.fetch_sub(b->dev_charge);
+    ctx->completed.fetch_add(b->E);
+    {
+        std::lock_guard<std::mutex> g(b->sv->mu);
+        b->sv->inflight_batches--;
+        b->sv->cv.notify_all();
+    }
+    for (uint32_t e = 0; e < b->E; ++e) complete_event(b->reqs[e]);
+    release_batch_ref(b);
+}
+
+struct BatchLayout {
+    size_t d_words, d_mods, d_offs, d_label, d_ws, dev_bytes;
+    size_t h_offs, h_coff, h_status, h_arr[6], h_label, h_table, host_bytes;
+    int grid;
+};
+
+BatchLayout batch_layout(const hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
+{
+    BatchLayout l;
+    l.grid = cc_grid_for(ctx, E);
+    const size_t ws = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.grid,
+                                          nullptr);
+    size_t d = 0;
+    l.d_words = d;
+    d = align_up(d + 4 * N, 256);
+    l.d_mods = d;
+    d = align_up(d + 2 * N, 256);
+    l.d_offs = d;
+    d = align_up(d + 8 * (size_t)(E + 1), 256);
+    l.d_label = d;
+    if (labels) d = align_up(d + 4 * N, 256);
+    l.d_ws = d;
+    l.dev_bytes = d + ws;
+    size_t h = 0;
+    l.h_offs = h;
+    h = align_up(h + 8 * (size_t)(E + 1), 256);
+    l.h_coff = h;
+    h = align_up(h + 8 * (size_t)(E + 1), 256);
+    l.h_status = h;
+    h = align_up(h + 4 * (size_t)E, 256);
+    for (int i = 0; i < 6; ++i) {
+        l.h_arr[i] = h;
+        h = align_up(h + 4 * N, 256);
+    }
+    l.h_label = h;
+    if (labels) h = align_up(h + 4 * N, 256);
+    l.h_table = h;
+    h = align_up(h + sizeof(hp::GatherEntry) * E, 256);
+    l.host_bytes = h;
+    return l;
+}
+
+void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
+{
+    const uint32_t E = (uint32_t)take.size();
+    uint64_t N = 0, max_n = 0;
+    for (hp_event *r : take) {
+        N += r->N;
+        max_n = std::max<uint64_t>(max_n, r->N);
+    }
+    const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
+    const BatchLayout l = batch_layout(ctx, E, N, labels);
+    Batch *b = new (std::nothrow) Batch();
+    auto give_up = [&](hp_status st) {
+        {
+            std::lock_guard<std::mutex> g(sv->mu);
+            sv->inflight_batches--;
+            sv->cv.notify_all();
+        }
+        fail_requests(ctx, take, st);
+    };
+    if (!b) return give_up(HP_ENOMEM);
+    b->ctx = ctx;
+    b->sv = sv;
+    b->E = E;
+    b->N = N;
+    b->labels = labels;
+    b->reqs = take;
+    if (ctx->dpool.alloc(l.dev_bytes, &b->dev) != HP_OK) {
+        delete b;
+        return give_up(HP_ENOMEM);
+    }
+    if (ctx->hpool.alloc(l.host_bytes, &b->host) != HP_OK) {
+        ctx->dpool.free(b->dev);
+        delete b;
+        return give_up(HP_ENOMEM);
+    }
+    b->dev_charge = round_bin(l.dev_bytes);
+    ctx->dev_in_use.fetch_add(b->dev_charge);
+    b->refs.store(E + 1);
+    for (hp_event *r : take) r->batch = b;
+    unsigned char *hb = static_cast<unsigned char *>(b->host.ptr);
+    unsigned char *hd = static_cast<unsigned char *>(b->host.dptr);
+    unsigned char *db = static_cast<unsigned char *>(b->dev.ptr);
+    b->h_offs = reinterpret_cast<uint64_t *>(hb + l.h_offs);
+    b->h_coff = reinterpret_cast<uint64_t *>(hb + l.h_coff);
+    b->h_status = reinterpret_cast<int32_t *>(hb + l.h_status);
+    b->h_module = reinterpret_cast<uint32_t *>(hb + l.h_arr[0]);
+    b->h_id = reinterpret_cast<int32_t *>(hb + l.h_arr[1]);
+    b->h_charge = reinterpret_cast<int32_t *>(hb + l.h_arr[2]);
+    b->h_npix = reinterpret_cast<int32_t *>(hb + l.h_arr[3]);
+    b->h_x = reinterpret_cast<float *>(hb + l.h_arr[4]);
+    b->h_y = reinterpret_cast<float *>(hb + l.h_arr[5]);
+    b->h_label = labels ? reinterpret_cast<int32_t *>(hb + l.h_label) : nullptr;
+    hp::GatherEntry *table = reinterpret_cast<hp::GatherEntry *>(hb + l.h_table);
+    b->h_offs[0] = 0;
+    for (uint32_t e = 0; e < E; ++e) {
+        hp_event *r = take[e];
+        b->h_offs[e + 1] = b->h_offs[e] + r->N;
+        const unsigned char *sd = static_cast<const unsigned char *>(r->staging.dptr);
+        table[e].words = reinterpret_cast<const uint32_t *>(sd);
+        table[e].modules = reinterpret_cast<const uint16_t *>(sd + align_up(4 * r->N, 256));
+        table[e].n = r->N;
+        table[e].off = b->h_offs[e];
+    }
+
+    hp::Launch L;
+    L.g = geometry(ctx);
+    L.E = E;
+    L.N = N;
+    L.offsets = reinterpret_cast<const uint64_t *>(db + l.d_offs);
+    L.words = reinterpret_cast<const uint32_t *>(db + l.d_words);
+    L.modules = reinterpret_cast<const uint16_t *>(db + l.d_mods);
+    L.out.capacity = N;
+    L.out.module = reinterpret_cast<uint32_t *>(hd + l.h_arr[0]);
+    L.out.id = reinterpret_cast<int32_t *>(hd + l.h_arr[1]);
+    L.out.charge = reinterpret_cast<int32_t *>(hd + l.h_arr[2]);
+    L.out.npix = reinterpret_cast<int32_t *>(hd + l.h_arr[3]);
+    L.out.x = reinterpret_cast<float *>(hd + l.h_arr[4]);
+    L.out.y = reinterpret_cast<float *>(hd + l.h_arr[5]);
+    L.out.cluster_offsets = reinterpret_cast<uint64_t *>(hd + l.h_coff);
+    L.out.event_status = reinterpret_cast<int32_t *>(hd + l.h_status);
+    L.out.label = labels ? reinterpret_cast<int32_t *>(db + l.d_label) : nullptr;
+    hp::carve_workspace(db + l.d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.grid, &L.ws);
+    L.cc_grid = l.grid;
+
+    const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
+    cudaStream_t s = ctx->streams[si];
+    uint64_t nk = 0;
+    cudaError_t err = cudaMemcpyAsync(db + l.d_offs, b->h_offs, 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+        err = hp::launch_gather(reinterpret_cast<const hp::GatherEntry *>(hd + l.h_table), E, max_n,
+                                reinterpret_cast<uint32_t *>(db + l.d_words),
+                                reinterpret_cast<uint16_t *>(db + l.d_mods), s);
+    nk += (N > 0);
+    if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
+    if (err == cudaSuccess && labels && N)
+        err = cudaMemcpyAsync(b->h_label, db + l.d_label, 4 * N, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaLaunchHostFunc(s, batch_done, b);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        fail(ctx);
+        for (hp_event *r : take) r->batch = nullptr; // the batch's memory is not reclaimed: the context is failed
+        return give_up(HP_ECUDA);
+    }
+    ctx->h2d.fetch_add(6 * N + 8 * (uint64_t)(E + 1));
+    if (labels) ctx->d2h.fetch_add(4 * N);
+    ctx->kernels.fetch_add(nk);
+    ctx->serve_batches.fetch_add(1);
+}
+
+void admitter_main(hp_ctx *ctx, Serve *sv)
+{
+    cudaSetDevice(ctx->device);
+    const uint32_t max_events = sv->cfg.max_batch_events ? sv->cfg.max_batch_events : 256;
+    const uint64_t max_digis = sv->cfg.max_batch_digis ? sv->cfg.max_batch_digis : (32ull << 20);
+    const uint32_t max_batches = sv->cfg.max_inflight_batches ? sv->cfg.max_inflight_batches : 4;
+    const size_t budget = sv->cfg.device_budget_bytes;
+    const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
+    for (;;) {
+        std::vector<hp_event *> take;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait(lk, [&] {
+                return (sv->stop && sv->pending.empty()) ||
+                       (!sv->pending.empty() && sv->inflight_batches < max_batches);
+            });
+            if (sv->pending.empty()) break; // stopping, and everything queued was launched
+            uint64_t nd = 0;
+            while (!sv->pending.empty() && take.size() < max_events) {
+                hp_event *r = sv->pending.front();
+                if (!take.empty() && nd + r->N > max_digis) break;
+                nd += r->N;
+                take.push_back(r);
+                sv->pending.pop_front();
+            }
+            if (budget) {
+                const size_t need = round_bin(batch_layout(ctx, (uint32_t)take.size(), nd, labels).dev_bytes);
+                sv->cv.wait(lk, [&] {
+                    return sv->inflight_batches == 0 || ctx->dev_in_use.load() + need <= budget;
+                });
+            }
+            sv->inflight_batches++;
+        }
+        launch_batch(ctx, sv, take);
+    }
+}
+
+hp_status serve_stop(hp_ctx *ctx)
+{
+    Serve *sv = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->serve_mu);
+        sv = ctx->serve;
+        ctx->serve = nullptr;
+    }
+    if (!sv) return HP_EINVAL;
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    sv->admitter.join();
+    {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        sv->cv.wait(lk, [&] { return sv->inflight_batches == 0; });
+    }
+    delete sv;
+    return HP_OK;
+}
+
 } // namespace
 
 bool hp::context_launch_params(hp_ctx *ctx, hp::Geometry *g, int *device, int *cc_grid)
@@ -611,6 +948,7 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
 hp_status hp_destroy(hp_ctx *ctx)
 {
     if (!ctx) return HP_EINVAL;
+    serve_stop(ctx); // drains a running serving loop (no-op otherwise)
     cudaSetDevice(ctx->device);
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
     {
@@ -785,6 +1123,92 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
     return HP_OK;
 }
 
+hp_status hp_serve_start(hp_ctx *ctx, const hp_serve_config *cfg)
+{
+    if (!ctx || !cfg) return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    std::lock_guard<std::mutex> g(ctx->serve_mu);
+    if (ctx->serve) return HP_EINVAL;
+    Serve *sv = new (std::nothrow) Serve();
+    if (!sv) return HP_ENOMEM;
+    sv->cfg = *cfg;
+    try {
+        sv->admitter = std::thread(admitter_main, ctx, sv);
+    } catch (...) {
+        delete sv;
+        return HP_ENOMEM;
+    }
+    ctx->serve = sv;
+    return HP_OK;
+}
+
+hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_ids, uint64_t n_digis, uint64_t tag,
+                    hp_callback cb, void *user, hp_event **out)
+{
+    if (!ctx || !out) return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    if (n_digis >= 0xFFFFFFFFull) return HP_EINVAL;
+    if (n_digis > 0 && (!words || !module_ids)) return HP_EINVAL;
+    Serve *sv = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->serve_mu);
+        sv = ctx->serve;
+    }
+    if (!sv) return HP_EINVAL;
+    const uint32_t max_pending = sv->cfg.max_pending ? sv->cfg.max_pending : 65536;
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        if (sv->stop) return HP_EINVAL;
+        if (sv->pending.size() >= max_pending) return HP_EAGAIN;
+    }
+    hp_event *ev = new (std::nothrow) hp_event();
+    if (!ev) return HP_ENOMEM;
+    ev->ctx = ctx;
+    ev->request = true;
+    ev->E = 1;
+    ev->N = n_digis;
+    ev->tag = tag;
+    ev->flags = sv->cfg.flags | ctx->cfg.flags;
+    const size_t wbytes = align_up(4 * n_digis, 256);
+    if (ctx->hpool.alloc(wbytes + 2 * n_digis + 256, &ev->staging) != HP_OK) {
+        delete ev;
+        return HP_ENOMEM;
+    }
+    unsigned char *st = static_cast<unsigned char *>(ev->staging.ptr);
+    if (n_digis) {
+        std::memcpy(st, words, 4 * n_digis);
+        std::memcpy(st + wbytes, module_ids, 2 * n_digis);
+    }
+    if (cb) {
+        ev->cb = cb;
+        ev->user = user;
+        ev->state.store(kCbSet);
+    }
+    ev->coff_local[0] = ev->coff_local[1] = 0;
+    ev->h_coff = ev->coff_local;
+    ev->h_status = &ev->status_local;
+    {
+        std::lock_guard<std::mutex> g(ctx->live_mu);
+        ctx->live.insert(ev);
+    }
+    ev->t_enq = now_ns();
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        sv->pending.push_back(ev);
+    }
+    sv->cv.notify_one();
+    ctx->serve_requests.fetch_add(1);
+    ctx->enqueued.fetch_add(1);
+    *out = ev;
+    return HP_OK;
+}
+
+hp_status hp_serve_stop(hp_ctx *ctx)
+{
+    if (!ctx) return HP_EINVAL;
+    return serve_stop(ctx);
+}
+
 hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)
 {
     if (!ctx || !o) return HP_EINVAL;
@@ -799,6 +1223,8 @@ hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)
     o->h2d_bytes = ctx->h2d.load();
     o->d2h_bytes = ctx->d2h.load();
     o->kernel_launches = ctx->kernels.load();
+    o->serve_batches = ctx->serve_batches.load();
+    o->serve_requests = ctx->serve_requests.load();
     return ctx->failed.load() ? HP_ECUDA : HP_OK;
 }
 

@@ -27,7 +27,8 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_event_query", "hp_fetch_clusters", "hp_release_event", "hp_event_device", "hp_event_stream",
            "hp_event_cuda_event", "hp_event_latency_ns", "hp_reconstruct_device", "hp_reconstruct_device_noalloc",
            "hp_get_stats",
-           "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations")
+           "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations", "hp_serve_start", "hp_submit",
+           "hp_serve_stop")
 
 
 class HPError(RuntimeError):
@@ -61,7 +62,14 @@ class DeviceClusters(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "device_mallocs", "host_mallocs", "pool_hits", "device_bytes_in_use", "device_bytes_cached",
-        "events_enqueued", "events_completed", "inflight", "h2d_bytes", "d2h_bytes", "kernel_launches")]
+        "events_enqueued", "events_completed", "inflight", "h2d_bytes", "d2h_bytes", "kernel_launches",
+        "serve_batches", "serve_requests")]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_size_t), ("max_batch_events", ctypes.c_uint32),
+                ("max_batch_digis", ctypes.c_uint64), ("max_inflight_batches", ctypes.c_uint32),
+                ("max_pending", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 CALLBACK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int)
@@ -100,6 +108,9 @@ def load(path: str = LIB_PATH):
             "hp_profile_enable": (I, [V, U32]),
             "hp_profile_read": (I, [V, U32, P(ctypes.c_char_p), P(ctypes.c_double), P(U64), P(U32)]),
             "hp_debug_fail_allocations": (I, [V, U32]),
+            "hp_serve_start": (I, [V, P(ServeConfig)]),
+            "hp_submit": (I, [V, V, V, U64, U64, V, V, P(V)]),
+            "hp_serve_stop": (I, [V]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -311,6 +322,33 @@ class Context:
         _check(self._lib.hp_reconstruct_device(self._h, n_events, n_digis, d_offsets, d_words, d_modules,
                                                ctypes.byref(out.struct), ctypes.c_void_p(stream)),
                "hp_reconstruct_device")
+
+    def serve_start(self, budget_bytes=0, max_batch_events=0, max_batch_digis=0, max_inflight_batches=0,
+                    max_pending=0, want_labels=False):
+        """Start the continuous-batching serving loop (see hp_serve_start)."""
+        cfg = ServeConfig(budget_bytes, max_batch_events, max_batch_digis, max_inflight_batches, max_pending,
+                          HP_WANT_LABELS if want_labels else 0)
+        _check(self._lib.hp_serve_start(self._h, ctypes.byref(cfg)), "hp_serve_start")
+
+    def try_submit(self, words, modules, tag=0):
+        """Queue one event for serving: (status, Event-or-None)."""
+        words = np.ascontiguousarray(words, np.uint32)
+        modules = np.ascontiguousarray(modules, np.uint16)
+        h = ctypes.c_void_p()
+        st = self._lib.hp_submit(self._h, words.ctypes.data, modules.ctypes.data, len(words), tag, None, None,
+                                 ctypes.byref(h))
+        if st != HP_OK:
+            return st, None
+        return st, Event(self, h.value, 1, len(words))
+
+    def submit(self, words, modules, tag=0) -> "Event":
+        st, ev = self.try_submit(words, modules, tag)
+        _check(st, "hp_submit")
+        return ev
+
+    def serve_stop(self):
+        """Launch what is queued and wait for every batch."""
+        _check(self._lib.hp_serve_stop(self._h), "hp_serve_stop")
 
     def debug_fail_allocations(self, count: int):
         _check(self._lib.hp_debug_fail_allocations(self._h, count), "hp_debug_fail_allocations")

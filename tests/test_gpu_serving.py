@@ -1,0 +1,134 @@
+"""GPU tests of the serving loop (continuous batching): requests submitted
+from several threads while others run are admitted as batch slots and
+device budget free up, and every result equals the result of the same event
+processed alone (and the oracle)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2004_04334_gb300 import hp, synth
+from tests.gpu_util import assert_batch_matches
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pool():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    # serving-recipe events (lognormal sizes), a few of them small for speed
+    w = synth.workload("serving", n_events=24)
+    return w
+
+
+def _alone(ctx, w, e):
+    words, mods = w.event(e)
+    ev = ctx.enqueue_event(words, mods)
+    assert ev.wait(60) == hp.HP_OK
+    r = ev.fetch()
+    ev.release()
+    return r
+
+
+def test_mix_equals_alone(pool):
+    w = pool
+    with hp.Context(w.n_modules, w.gain, w.pedestal, want_labels=True, n_streams=4) as ctx:
+        alone = [_alone(ctx, w, e) for e in range(w.n_events)]
+        ctx.serve_start(budget_bytes=16 << 30, want_labels=True)
+        order = [e for _ in range(3) for e in np.random.default_rng(2).permutation(w.n_events)]
+        results = [None] * len(order)
+        errors = []
+
+        def submitter(tid):
+            try:
+                evs = []
+                for i in range(tid, len(order), 4):
+                    words, mods = w.event(order[i])
+                    evs.append((i, ctx.submit(words, mods, tag=i)))
+                for i, ev in evs:
+                    assert ev.wait(120) == hp.HP_OK
+                    results[i] = ev.fetch()
+                    assert ev.latency_ns > 0
+                    ev.release()
+            except Exception as exc:  # noqa: BLE001
+                errors.append(exc)
+
+        ts = [threading.Thread(target=submitter, args=(t,)) for t in range(4)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        assert not errors, errors[0]
+        stats = ctx.stats()
+        ctx.serve_stop()
+    assert stats["serve_requests"] == len(order)
+    assert stats["serve_batches"] < len(order)  # requests were batched together
+    for i, e in enumerate(order):
+        r, a = results[i], alone[e]
+        for f in ("module", "id", "charge", "npix", "x", "y", "label"):
+            assert np.array_equal(getattr(r, f), getattr(a, f)), (i, f)
+    # and the alone results are the oracle's
+    for e in (0, 5, 11):
+        words, mods = w.event(e)
+        ref = oracle.reconstruct_event(words, mods, w.n_modules, w.gain, w.pedestal)
+        assert_batch_matches(alone[e], ref, np.array([0, len(words)], np.uint64))
+
+
+def test_budget_admits_one_batch_at_a_time(pool):
+    w = pool
+    with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
+        ctx.serve_start(budget_bytes=1 << 20, max_batch_events=2)
+        evs = [ctx.submit(*w.event(e)) for e in range(8)]
+        for ev in evs:
+            assert ev.wait(120) == hp.HP_OK
+        s = ctx.stats()
+        assert s["serve_batches"] >= 4
+        for e, ev in enumerate(evs):
+            r = ev.fetch()
+            a = _alone(ctx, w, e)
+            assert np.array_equal(r.id, a.id) and np.array_equal(r.charge, a.charge)
+            ev.release()
+        ctx.serve_stop()
+
+
+def test_backpressure_and_draining_stop(pool):
+    w = pool
+    done = []
+    with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
+        ctx.serve_start(max_pending=4, max_inflight_batches=1, max_batch_events=1)
+        statuses, evs = [], []
+        for e in range(40):
+            st, ev = ctx.try_submit(*w.event(e % w.n_events))
+            statuses.append(st)
+            if ev is not None:
+                ev.on_complete(lambda ev, st: done.append(st))
+                evs.append(ev)
+        assert hp.HP_EAGAIN in statuses
+        ctx.serve_stop()  # launches what is queued and waits
+        assert len(done) == len(evs) and all(st == hp.HP_OK for st in done)
+        for ev in evs:
+            ev.release()
+
+
+def test_bad_request_does_not_disturb_its_batch(pool):
+    w = pool
+    with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
+        a0 = _alone(ctx, w, 0)
+        ctx.serve_start(max_inflight_batches=1)
+        words, mods = w.event(1)
+        bad = words.copy()
+        bad[7] |= 1 << 27
+        time.sleep(0.01)
+        evs = [ctx.submit(*w.event(0)), ctx.submit(bad, mods), ctx.submit(*w.event(0))]
+        sts = [ev.wait(60) for ev in evs]
+        assert sts == [hp.HP_OK, hp.HP_EBADDIGI, hp.HP_OK]
+        for ev in (evs[0], evs[2]):
+            r = ev.fetch()
+            assert np.array_equal(r.id, a0.id) and np.array_equal(r.x, a0.x)
+        for ev in evs:
+            ev.release()
+        ctx.serve_stop()
