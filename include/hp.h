@@ -292,6 +292,24 @@ hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_i
                     hp_callback cb, void *user, hp_event **out);
 hp_status hp_serve_stop(hp_ctx *ctx);
 
+/*
+ * Load driver for the serving loop (Sec. 2: several threads acquire
+ * concurrently, none blocks on the device): n_threads native submitter
+ * threads replay a schedule of n_requests arrivals.  Request i arrives
+ * arrival_ns[i] after the start (non-decreasing per thread is not required)
+ * and submits pool event event_index[i] (pool_words/pool_modules/pool_n, n_pool
+ * events, host memory).  Each completion callback records the request's
+ * submit-to-completion latency in latency_ns[i] and its status in status[i],
+ * then releases it.  The call returns when every request has completed;
+ * *span_ns is the time from the start to the last completion.  Requires a
+ * running serving loop (hp_serve_start).  Returns the first hp_submit error
+ * other than HP_EAGAIN (which is retried), else HP_OK.
+ */
+hp_status hp_serve_replay(hp_ctx *ctx, uint32_t n_threads, uint64_t n_requests, const uint64_t *arrival_ns,
+                          const uint32_t *event_index, uint32_t n_pool, const uint32_t *const *pool_words,
+                          const uint16_t *const *pool_modules, const uint64_t *pool_n, uint64_t *latency_ns,
+                          int32_t *status, uint64_t *span_ns);
+
 hp_status hp_get_stats(hp_ctx *ctx, hp_stats *out);
 
 /*

@@ -68,8 +68,8 @@ class Pool {
                 --fail_next_;
                 return HP_ENOMEM;
             }
-            auto it = free_.find(b);
-            if (it != free_.end()) {
+            auto it = free_.lower_bound(b); // best fit among cached blocks of up to twice the size
+            if (it != free_.end() && it->first <= 2 * b) {
                 *out = it->second;
                 free_.erase(it);
                 ++hits_;
@@ -1207,6 +1207,80 @@ hp_status hp_serve_stop(hp_ctx *ctx)
 {
     if (!ctx) return HP_EINVAL;
     return serve_stop(ctx);
+}
+
+hp_status hp_serve_replay(hp_ctx *ctx, uint32_t n_threads, uint64_t n_requests, const uint64_t *arrival_ns,
+                          const uint32_t *event_index, uint32_t n_pool, const uint32_t *const *pool_words,
+                          const uint16_t *const *pool_modules, const uint64_t *pool_n, uint64_t *latency_ns,
+                          int32_t *status, uint64_t *span_ns)
+{
+    if (!ctx || !arrival_ns || !event_index || !pool_words || !pool_modules || !pool_n || !latency_ns || !status ||
+        !span_ns || n_threads < 1 || n_pool < 1)
+        return HP_EINVAL;
+    for (uint64_t i = 0; i < n_requests; ++i)
+        if (event_index[i] >= n_pool) return HP_EINVAL;
+    struct Shared {
+        std::mutex mu;
+        std::condition_variable cv;
+        uint64_t remaining;
+        uint64_t last_done = 0;
+        uint64_t *latency;
+        int32_t *status;
+        hp_status submit_error = HP_OK;
+    } sh;
+    sh.remaining = n_requests;
+    sh.latency = latency_ns;
+    sh.status = status;
+    struct Slot {
+        Shared *sh;
+        uint64_t i;
+    };
+    std::vector<Slot> slots(n_requests);
+    auto cb = [](void *user, hp_event *ev, hp_status st) {
+        Slot *sl = static_cast<Slot *>(user);
+        sl->sh->latency[sl->i] = hp_event_latency_ns(ev);
+        sl->sh->status[sl->i] = st;
+        hp_release_event(ev);
+        const uint64_t t = now_ns();
+        std::lock_guard<std::mutex> g(sl->sh->mu);
+        if (t > sl->sh->last_done) sl->sh->last_done = t;
+        if (--sl->sh->remaining == 0) sl->sh->cv.notify_all();
+    };
+    const uint64_t t0 = now_ns() + 1000000; // start 1 ms from now
+    auto worker = [&](uint32_t tid) {
+        for (uint64_t i = tid; i < n_requests; i += n_threads) {
+            const uint64_t due = t0 + arrival_ns[i];
+            uint64_t now = now_ns();
+            if (due > now + 100000) std::this_thread::sleep_for(std::chrono::nanoseconds(due - now - 50000));
+            while (now_ns() < due) {
+            }
+            slots[i] = Slot{&sh, i};
+            const uint32_t e = event_index[i];
+            hp_event *ev = nullptr;
+            for (;;) {
+                const hp_status st = hp_submit(ctx, pool_words[e], pool_modules[e], pool_n[e], i, +cb, &slots[i], &ev);
+                if (st == HP_OK) break;
+                if (st != HP_EAGAIN) {
+                    std::lock_guard<std::mutex> g(sh.mu);
+                    sh.submit_error = st;
+                    status[i] = st;
+                    latency_ns[i] = 0;
+                    if (--sh.remaining == 0) sh.cv.notify_all();
+                    break;
+                }
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+        }
+    };
+    std::vector<std::thread> ts;
+    for (uint32_t t = 0; t < n_threads; ++t) ts.emplace_back(worker, t);
+    for (auto &t : ts) t.join();
+    {
+        std::unique_lock<std::mutex> lk(sh.mu);
+        sh.cv.wait(lk, [&] { return sh.remaining == 0; });
+    }
+    *span_ns = sh.last_done > t0 ? sh.last_done - t0 : 0;
+    return sh.submit_error;
 }
 
 hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)

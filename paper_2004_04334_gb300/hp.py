@@ -28,7 +28,7 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_event_cuda_event", "hp_event_latency_ns", "hp_reconstruct_device", "hp_reconstruct_device_noalloc",
            "hp_get_stats",
            "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations", "hp_serve_start", "hp_submit",
-           "hp_serve_stop")
+           "hp_serve_stop", "hp_serve_replay")
 
 
 class HPError(RuntimeError):
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
             "hp_serve_start": (I, [V, P(ServeConfig)]),
             "hp_submit": (I, [V, V, V, U64, U64, V, V, P(V)]),
             "hp_serve_stop": (I, [V]),
+            "hp_serve_replay": (I, [V, U32, U64, V, V, U32, V, V, V, V, V, P(U64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -345,6 +346,27 @@ class Context:
         st, ev = self.try_submit(words, modules, tag)
         _check(st, "hp_submit")
         return ev
+
+    def serve_replay(self, pool, arrival_s, event_index, n_threads=4):
+        """Replay an arrival schedule with native submitter threads (see
+        hp_serve_replay).  pool: list of (words, modules).  Returns
+        (latency seconds[n], status[n], span seconds)."""
+        ws = [np.ascontiguousarray(w, np.uint32) for w, _ in pool]
+        ms = [np.ascontiguousarray(m, np.uint16) for _, m in pool]
+        P = len(pool)
+        pw = (ctypes.c_void_p * P)(*[w.ctypes.data for w in ws])
+        pm = (ctypes.c_void_p * P)(*[m.ctypes.data for m in ms])
+        pn = np.array([len(w) for w in ws], np.uint64)
+        arr = np.ascontiguousarray(np.round(np.asarray(arrival_s) * 1e9), np.uint64)
+        idx = np.ascontiguousarray(event_index, np.uint32)
+        n = len(arr)
+        lat = np.zeros(n, np.uint64)
+        st = np.zeros(n, np.int32)
+        span = ctypes.c_uint64()
+        _check(self._lib.hp_serve_replay(self._h, n_threads, n, arr.ctypes.data, idx.ctypes.data, P, pw, pm,
+                                         pn.ctypes.data, lat.ctypes.data, st.ctypes.data, ctypes.byref(span)),
+               "hp_serve_replay")
+        return lat * 1e-9, st, span.value * 1e-9
 
     def serve_stop(self):
         """Launch what is queued and wait for every batch."""

@@ -132,3 +132,19 @@ def test_bad_request_does_not_disturb_its_batch(pool):
         for ev in evs:
             ev.release()
         ctx.serve_stop()
+
+
+def test_native_replay_driver(pool):
+    """hp_serve_replay: 4 native submitter threads on a Poisson schedule."""
+    w = pool
+    events = [w.event(e) for e in range(w.n_events)]
+    with hp.Context(w.n_modules, w.gain, w.pedestal, want_labels=True) as ctx:
+        ctx.serve_start(budget_bytes=16 << 30, want_labels=True)
+        rng = np.random.default_rng(4)
+        arrival = np.cumsum(rng.exponential(1 / 5000.0, 200))
+        lat, st, span = ctx.serve_replay(events, arrival, np.arange(200) % len(events), 4)
+        s = ctx.stats()
+        ctx.serve_stop()
+    assert np.all(st == 0) and np.all(lat > 0)
+    assert span >= arrival[-1] - arrival[0]
+    assert s["serve_requests"] == 200 and s["serve_batches"] <= 200
