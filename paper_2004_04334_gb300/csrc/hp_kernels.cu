@@ -389,13 +389,19 @@ struct BlockShared {
     uint32_t scan_tmp[kCCThreads / 32 + 1];
 };
 
-__device__ __forceinline__ uint32_t uf_find(const uint32_t *parent, uint32_t x)
+// Find with path halving (each visited node is re-pointed to its
+// grandparent).  Parent entries only ever point to a smaller slot of the same
+// tree, so a plain store that races with a link elsewhere leaves a valid
+// ancestor behind; a link that loses such a race is retried by its union.
+__device__ __forceinline__ uint32_t uf_find_halving(uint32_t *parent, uint32_t x)
 {
-    const volatile uint32_t *p = parent;
+    volatile uint32_t *p = parent;
     uint32_t y = p[x];
     while (y != x) {
+        const uint32_t z = p[y];
+        if (z != y) p[x] = z;
         x = y;
-        y = p[x];
+        y = z;
     }
     return x;
 }
@@ -411,8 +417,8 @@ __device__ __forceinline__ void warp_union(uint32_t *parent, uint32_t a, uint32_
     bool done = b == kNoSlot;
     while (__any_sync(kFull, !done)) {
         if (!done) {
-            a = uf_find(parent, a);
-            b = uf_find(parent, b);
+            a = uf_find_halving(parent, a);
+            b = uf_find_halving(parent, b);
             if (a == b) {
                 done = true;
             } else {
