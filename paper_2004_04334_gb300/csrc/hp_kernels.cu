@@ -754,11 +754,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         crun += __popc(abits[ch]);
     }
     __syncthreads();
-    for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
-        const uint32_t s = (ch << 5) + lane;
-        const uint32_t bal = abits[ch];
-        if (!((bal >> lane) & 1u)) continue;
-        const uint32_t ord = spre[ch] + __popc(bal & ((1u << lane) - 1u));
+    auto stage = [&](uint32_t s, uint32_t ord) {
         const unsigned long long qn = t.qn[s];
         const int32_t Q = (int32_t)(qn >> 17);
         long long mr, mc;
@@ -778,6 +774,22 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         o.y = centroid_abs(mc, Q);
         o.pad = 0;
         L.ws.staging[it.b + ord] = o;
+    };
+    if (S <= 2 * nwords) {
+        // compact the kept roots (their slots, by ordinal, into the survivor
+        // bitmap's space, free now) so that every lane stages a cluster
+        uint16_t *kslot = reinterpret_cast<uint16_t *>(sbits);
+        for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+            const uint32_t bal = abits[ch];
+            if ((bal >> lane) & 1u) kslot[spre[ch] + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((ch << 5) + lane);
+        }
+        __syncthreads();
+        for (uint32_t o = tid; o < K; o += kCCThreads) stage(kslot[o], o);
+    } else {
+        for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+            const uint32_t bal = abits[ch];
+            if ((bal >> lane) & 1u) stage((ch << 5) + lane, spre[ch] + __popc(bal & ((1u << lane) - 1u)));
+        }
     }
     return K;
 }
