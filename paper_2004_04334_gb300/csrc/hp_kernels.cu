@@ -304,13 +304,23 @@ __global__ void __launch_bounds__(256) scan_kernel(const Launch L)
     }
 }
 
+// Shared memory of the scatter kernel (bytes).
+constexpr size_t kScatterSmem = kHistCap * 4 + kChunk * (4 + 4 + 2) + (2 * kSubKeys + 1) * 4;
+static_assert(kChunk * (4 + 4 + 2) >= kHistCap * 4, "the staging area also holds the single-histogram bases");
+
 __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
 {
-    extern __shared__ uint32_t sh[];
+    extern __shared__ __align__(16) uint32_t sh[];
     uint32_t *cnt = sh;             // counts: per warp sub-histograms, or one histogram
     uint32_t *bas = sh + kHistCap;  // single-histogram mode: base of each key
+    uint32_t *stage_w = sh + kHistCap;                                      // sub mode: block-local sorted words
+    uint32_t *stage_i = stage_w + kChunk;                                   // and in-event indices
+    uint16_t *stage_k = reinterpret_cast<uint16_t *>(stage_i + kChunk);     // and local keys
+    uint32_t *lk = reinterpret_cast<uint32_t *>(stage_k + kChunk);          // block-local start of each key
+    uint32_t *gb = lk + kSubKeys + 1;                                       // bucket position of each key's range
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
+    __shared__ uint32_t s_scan[kHistThreads / 32 + 1];
     const ChunkInfo ci = chunk_info(L, s_ev, s_off);
     const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
     const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
@@ -334,30 +344,54 @@ __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
         rank[j] = ci.use_sh ? atomicAdd(&bins[key - ci.keybase], 1u) : atomicAdd(&L.ws.cursor[key], 1u);
     }
     __syncthreads();
-    // reserve each key's range in its bucket; sub-histogram mode turns the
-    // per-warp counts into per-warp bases (an exclusive scan over the warps)
-    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
-        if (sub) {
-            uint32_t tot = 0;
-            for (uint32_t wi = 0; wi < kHistWarps; ++wi) tot += cnt[wi * ci.nkeys + i];
-            uint32_t base = tot ? atomicAdd(&L.ws.cursor[ci.keybase + i], tot) : 0u;
+    if (sub) {
+        // Few keys: sort the block's digis by key in shared memory, then write
+        // each key's run to its bucket with consecutive threads.  Per key:
+        // per-warp counts become offsets within the key, the key's block
+        // start comes from a scan over keys, and one atomic reserves its range.
+        uint32_t tot = 0;
+        if (threadIdx.x < ci.nkeys) {
             for (uint32_t wi = 0; wi < kHistWarps; ++wi) {
-                const uint32_t c = cnt[wi * ci.nkeys + i];
-                cnt[wi * ci.nkeys + i] = base;
-                base += c;
+                const uint32_t c = cnt[wi * ci.nkeys + threadIdx.x];
+                cnt[wi * ci.nkeys + threadIdx.x] = tot;
+                tot += c;
             }
-        } else {
-            const uint32_t v = cnt[i];
-            if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
         }
+        uint32_t total;
+        const uint32_t start = block_exclusive_scan<kHistThreads>(tot, s_scan, &total);
+        if (threadIdx.x < ci.nkeys) {
+            lk[threadIdx.x] = start;
+            gb[threadIdx.x] = tot ? atomicAdd(&L.ws.cursor[ci.keybase + threadIdx.x], tot) : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) {
+            if (m[j] == 0xFFFFFFFFu) continue;
+            const uint32_t key = (uint32_t)((uint64_t)e_of[j] * M + m[j] - ci.keybase);
+            const uint32_t p = lk[key] + cnt[warp * ci.nkeys + key] + rank[j];
+            stage_w[p] = w[j];
+            stage_i[p] = (uint32_t)(k0 + j - L.offsets[e_of[j]]);
+            stage_k[p] = (uint16_t)key;
+        }
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < total; p += kHistThreads) {
+            const uint32_t key = stage_k[p];
+            const uint32_t g = gb[key] + (p - lk[key]);
+            L.ws.bucket_w[g] = stage_w[p];
+            L.ws.bucket_i[g] = stage_i[p];
+        }
+        return;
+    }
+    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
+        const uint32_t v = cnt[i];
+        if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
     }
     __syncthreads();
-    const uint32_t *base_of = sub ? cnt + warp * ci.nkeys : bas;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         if (m[j] == 0xFFFFFFFFu) continue;
         const uint64_t key = (uint64_t)e_of[j] * M + m[j];
-        const uint32_t p = ci.use_sh ? base_of[key - ci.keybase] + rank[j] : rank[j];
+        const uint32_t p = ci.use_sh ? bas[key - ci.keybase] + rank[j] : rank[j];
         L.ws.bucket_w[p] = w[j];
         L.ws.bucket_i[p] = (uint32_t)(k0 + j - L.offsets[e_of[j]]);
     }
@@ -1121,6 +1155,8 @@ cudaError_t init_kernels(int device, uint32_t R, uint32_t C, int *cc_blocks_per_
     const size_t smem = cc_smem_bytes(R, C);
     err = cudaFuncSetAttribute(cc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    if (err != cudaSuccess) return err;
     int nb = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cc_kernel, kCCThreads, smem);
     if (err != cudaSuccess) return err;
@@ -1150,7 +1186,7 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     ++nk;
     mark(2);
     if (L.N > 0) {
-        scatter_kernel<<<(unsigned)nchunks, kHistThreads, 2 * kHistCap * sizeof(uint32_t), stream>>>(L);
+        scatter_kernel<<<(unsigned)nchunks, kHistThreads, kScatterSmem, stream>>>(L);
         ++nk;
     }
     mark(3);
