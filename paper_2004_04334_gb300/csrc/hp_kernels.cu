@@ -701,8 +701,18 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
                 }
             }
         }
-        warp_union(t.parent, s, nb0);
-        warp_union(t.parent, s, nb1);
+        // gather the warp's union pairs onto consecutive lanes, then union them
+        const uint32_t m0 = __ballot_sync(kFull, nb0 != kNoSlot);
+        const uint32_t m1 = __ballot_sync(kFull, nb1 != kNoSlot);
+        const uint32_t n0 = __popc(m0), total = n0 + __popc(m1);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t p = base + lane;
+            const bool from0 = p < n0;
+            const uint32_t src = p < total ? __fns(from0 ? m0 : m1, 0, (int)(from0 ? p : p - n0) + 1) : 0u;
+            const uint32_t a = __shfl_sync(kFull, s, src);
+            const uint32_t b0 = __shfl_sync(kFull, nb0, src), b1 = __shfl_sync(kFull, nb1, src);
+            warp_union(t.parent, a, p < total ? (from0 ? b0 : b1) : kNoSlot);
+        }
     }
     __syncthreads();
 
