@@ -44,6 +44,14 @@ from paper_2004_04334_gb300 import synth  # noqa: E402
 
 METRIC = "events/s & Mdigis/s at 1 GB300 (batched vs per-event, % HBM peak); p50/p99 latency"
 WORKLOAD = "batched"
+WORKLOAD_TEXT = {
+    "batched": "uneven events, digi counts uniform in 10k-200k",
+    "occupancy": "Poisson(80) clusters of 1-40 px per module, 10% 1x30 streaks, 2% hot modules at 20% occupancy",
+    "full": "one full-size event (~60k digis)",
+    "full_literal": "one event with 1% noise occupancy (~1.5M digis)",
+    "tiny": "one 64-module event (~1.2k digis)",
+    "serving": "lognormal sizes (median 80k, sigma 0.8, cap 500k)",
+}
 
 
 def _args():
@@ -323,7 +331,7 @@ def run_ours(a):
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000 * t_dev / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
-            "config": {"workload": f"{a.workload}: {E} events of uneven size (10k-200k digis), {M} modules "
+            "config": {"workload": f"{a.workload}: {WORKLOAD_TEXT.get(a.workload, '')}; {E} events, {M} modules "
                                    f"of 160x416, {N} digis, labels on",
                        "events_per_step": E, "digis_per_step": N, "clusters_per_step": n_clusters,
                        "l2": "inputs (6 B/digi) and working set larger than the 129 MB L2; no flush",
