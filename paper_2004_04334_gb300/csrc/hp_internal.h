@@ -21,7 +21,7 @@ constexpr int kHistThreads = 512;
 constexpr int kHistCap = 4096;       // (event, module) bins a block can histogram in shared memory
 constexpr int kCCThreads = 512;      // threads of a clustering block (two blocks per SM)
 constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue ticket, one per warp
-constexpr int kWarpMax = 32;         // items with at most this many digis are clustered by one warp
+constexpr int kWarpMax = 64;         // items with at most this many digis are clustered by one warp
 constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory
 
 // A cluster parked between the clustering phase and the ordered write.

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "hp_internal.h"
 
@@ -499,86 +500,147 @@ __device__ __forceinline__ uint32_t run_offset(const uint32_t *sbits, uint32_t l
     return off;
 }
 
-// One item of at most 32 digis, clustered by one warp in registers: lane i
-// holds digi i; adjacency is a 32-bit mask per lane; the cluster id (the
-// smallest linear index) spreads over the adjacency by min-propagation.
-// Returns the number of kept clusters (all lanes).
+// One item of at most 32 * K digis, clustered by one warp in registers:
+// digi j is held by lane j % 32 in register slot j / 32.  Adjacency is a bit
+// mask over the item's digis per held digi; the cluster id (the smallest
+// linear index) spreads over the adjacency by min-propagation; cluster sums
+// run over the digis sharing an id.  Returns the number of kept clusters
+// (all lanes).
+template <int K>
 __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
 {
+    using Mask = typename std::conditional<K == 1, uint32_t, unsigned long long>::type;
     const uint32_t lane = threadIdx.x & 31;
     const int R = (int)L.g.R, C = (int)L.g.C;
     const uint32_t n = it.n;
-    const bool have = lane < n;
-    uint32_t w = 0, idx = 0;
-    if (have) {
-        w = L.ws.bucket_w[it.b + lane];
-        idx = L.ws.bucket_i[it.b + lane];
+    int r[K], c[K], q[K], lin[K], lab[K];
+    uint32_t idx[K];
+    bool have[K], surv[K];
+    Mask adj[K];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t j = lane + 32 * k;
+        have[k] = j < n;
+        const uint32_t w = have[k] ? L.ws.bucket_w[it.b + j] : 0u;
+        idx[k] = have[k] ? L.ws.bucket_i[it.b + j] : 0u;
+        r[k] = (int)(w & 0xFFu);
+        c[k] = (int)((w >> 8) & 0x1FFu);
+        const int adc = (int)((w >> 17) & 0xFFu);
+        if (have[k] && (r[k] >= R || c[k] >= C || adc == 0 || (w >> 25) != 0)) bad = true;
+        lin[k] = have[k] ? r[k] * C + c[k] : -1 - (int)j;
+        q[k] = adc * it.gain - it.ped;
+        surv[k] = have[k] && q[k] >= L.g.pixel_thr;
+        adj[k] = 0;
     }
-    const int r = (int)(w & 0xFFu), c = (int)((w >> 8) & 0x1FFu), adc = (int)((w >> 17) & 0xFFu);
-    const bool valid = r < R && c < C && adc > 0 && (w >> 25) == 0;
-    if (__any_sync(kFull, have && !valid)) {
+    if (__any_sync(kFull, bad)) {
         if (lane == 0) atomicOr(it.err_e, kErrBadDigi);
         return 0;
     }
-    const int lin = have ? r * C + c : -1 - (int)lane;
-    const uint32_t same = __match_any_sync(kFull, lin);
-    if (__any_sync(kFull, have && __popc(same) > 1)) {
+    Mask smask = (Mask)__ballot_sync(kFull, surv[0]);
+    if constexpr (K == 2) smask |= (Mask)__ballot_sync(kFull, surv[1]) << 32;
+    bool dup = false;
+    for (uint32_t j = 0; j < n; ++j) {
+        const uint32_t sl = j & 31, sk = j >> 5;
+        const int lj = __shfl_sync(kFull, (K == 2 && sk) ? lin[K - 1] : lin[0], sl);
+        const int rj = __shfl_sync(kFull, (K == 2 && sk) ? r[K - 1] : r[0], sl);
+        const int cj = __shfl_sync(kFull, (K == 2 && sk) ? c[K - 1] : c[0], sl);
+        const bool sj = (smask >> j) & 1u;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint32_t me = lane + 32 * k;
+            if (me == j) continue;
+            if (have[k] && lj == lin[k]) dup = true;
+            if (surv[k] && sj && abs(rj - r[k]) <= 1 && abs(cj - c[k]) <= 1) adj[k] |= (Mask)1 << j;
+        }
+    }
+    if (__any_sync(kFull, dup)) {
         if (lane == 0) atomicOr(it.err_e, kErrDup);
         return 0;
     }
-    const int q = adc * it.gain - it.ped;
-    const bool surv = have && q >= L.g.pixel_thr;
-    const uint32_t smask = __ballot_sync(kFull, surv);
-    uint32_t adj = 0;
-    for (uint32_t j = 0; j < n; ++j) {
-        const int rj = __shfl_sync(kFull, r, j), cj = __shfl_sync(kFull, c, j);
-        if (((smask >> j) & 1u) && j != lane && abs(rj - r) <= 1 && abs(cj - c) <= 1) adj |= 1u << j;
-    }
-    if (!surv) adj = 0;
-    int lab = surv ? lin : INT_MAX;
+#pragma unroll
+    for (int k = 0; k < K; ++k) lab[k] = surv[k] ? lin[k] : INT_MAX;
     for (uint32_t round = 0; round < n; ++round) {
-        int nl = lab;
+        int nl[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) nl[k] = lab[k];
         for (uint32_t j = 0; j < n; ++j) {
-            const int lj = __shfl_sync(kFull, lab, j);
-            if ((adj >> j) & 1u) nl = min(nl, lj);
+            const int lj = __shfl_sync(kFull, (K == 2 && (j >> 5)) ? lab[K - 1] : lab[0], j & 31);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if ((adj[k] >> j) & 1u) nl[k] = min(nl[k], lj);
         }
-        const bool changed = nl != lab;
-        lab = nl;
+        bool changed = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            changed |= nl[k] != lab[k];
+            lab[k] = nl[k];
+        }
         if (!__any_sync(kFull, changed)) break;
     }
-    const uint32_t grp = __match_any_sync(kFull, surv ? lab : -1 - (int)lane);
-    const int rr = surv ? lab / C : 0;
-    const int rc = surv ? lab - rr * C : 0;
-    int Q = 0, np = 0, Sr = 0, Sc = 0; // |sums| < 32 * 32263 * 31 < 2^31
+    // sums over the digis of each held digi's cluster, about the cluster's id pixel
+    // (|sums| < 64 * 32263 * 63 < 2^31)
+    int Q[K], np[K], Sr[K], Sc[K], rr[K], rc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        Q[k] = np[k] = Sr[k] = Sc[k] = 0;
+        rr[k] = surv[k] ? lab[k] / C : 0;
+        rc[k] = surv[k] ? lab[k] - rr[k] * C : 0;
+    }
     for (uint32_t j = 0; j < n; ++j) {
-        const int qj = __shfl_sync(kFull, q, j), rj = __shfl_sync(kFull, r, j), cj = __shfl_sync(kFull, c, j);
-        if ((grp >> j) & 1u) {
-            Q += qj;
-            ++np;
-            Sr += qj * (rj - rr);
-            Sc += qj * (cj - rc);
+        const uint32_t sl = j & 31;
+        const bool hi = K == 2 && (j >> 5);
+        const int labj = __shfl_sync(kFull, hi ? lab[K - 1] : lab[0], sl);
+        const int qj = __shfl_sync(kFull, hi ? q[K - 1] : q[0], sl);
+        const int rj = __shfl_sync(kFull, hi ? r[K - 1] : r[0], sl);
+        const int cj = __shfl_sync(kFull, hi ? c[K - 1] : c[0], sl);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (surv[k] && labj == lab[k]) {
+                Q[k] += qj;
+                ++np[k];
+                Sr[k] += qj * (rj - rr[k]);
+                Sc[k] += qj * (cj - rc[k]);
+            }
         }
     }
-    const bool leader = surv && lin == lab;
-    const bool kept = surv && Q >= L.g.cluster_thr;
-    const uint32_t kl = __ballot_sync(kFull, leader && kept);
-    uint32_t ord = 0;
+    bool kept[K], lead[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        lead[k] = surv[k] && lin[k] == lab[k];
+        kept[k] = surv[k] && Q[k] >= L.g.cluster_thr;
+    }
+    Mask kl = (Mask)__ballot_sync(kFull, lead[0] && kept[0]);
+    if constexpr (K == 2) kl |= (Mask)__ballot_sync(kFull, lead[K - 1] && kept[K - 1]) << 32;
+    uint32_t ord[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) ord[k] = 0;
     for (uint32_t j = 0; j < n; ++j) {
-        const int lj = __shfl_sync(kFull, lin, j);
-        if (((kl >> j) & 1u) && lj < lin) ++ord;
+        const int lj = __shfl_sync(kFull, (K == 2 && (j >> 5)) ? lin[K - 1] : lin[0], j & 31);
+        if ((kl >> j) & 1u) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (lj < lin[k]) ++ord[k];
+        }
     }
-    if (leader && kept) {
-        StagedCluster s;
-        s.id = lab;
-        s.charge = Q;
-        s.npix = np;
-        s.x = centroid(rr, Sr, Q);
-        s.y = centroid(rc, Sc, Q);
-        s.pad = 0;
-        L.ws.staging[it.b + ord] = s;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (lead[k] && kept[k]) {
+            StagedCluster st;
+            st.id = lab[k];
+            st.charge = Q[k];
+            st.npix = np[k];
+            st.x = centroid(rr[k], Sr[k], Q[k]);
+            st.y = centroid(rc[k], Sc[k], Q[k]);
+            st.pad = 0;
+            L.ws.staging[it.b + ord[k]] = st;
+        }
+        if (it.label_e && have[k]) it.label_e[idx[k]] = !surv[k] ? -1 : (kept[k] ? lab[k] : -2);
     }
-    if (it.label_e && have) it.label_e[idx] = !surv ? -1 : (kept ? lab : -2);
-    return __popc(kl);
+    if constexpr (K == 1)
+        return __popc(kl);
+    else
+        return __popcll(kl);
 }
 
 // Apply f(k, word) to every digi of the item owned by this thread.  The
@@ -974,7 +1036,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
                     const uint32_t n = s_n[wi];
                     if (n > 0 && n <= (uint32_t)kWarpMax) {
                         const ItemCtx it = make_item(L, item0 + wi, s_b[wi], n);
-                        const uint32_t K = warp_item(L, it);
+                        const uint32_t K = n <= 32 ? warp_item<1>(L, it) : warp_item<2>(L, it);
                         if ((tid & 31) == 0) s_K[wi] = K;
                     }
                 }

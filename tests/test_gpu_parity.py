@@ -124,9 +124,9 @@ def _module_with(n, rng, r0=10, c0=10, span=None):
     return synth.pack(rr, cc, adc)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 64, 2048, 4095, 4096, 4097, 9000, 20000])
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 63, 64, 65, 2048, 4095, 4096, 4097, 9000, 20000])
 def test_tier_boundaries(torch_cuda, n):
-    """Module sizes around the warp (32) and shared-memory (4096) capacities."""
+    """Module sizes around the warp tiers (32, 64 digis) and the shared-memory tier (4096)."""
     rng = np.random.default_rng(n)
     gain = np.array([70, 75, 80], np.int32)
     ped = np.array([100, 0, 200], np.int32)
