@@ -24,6 +24,16 @@ constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue 
 constexpr int kWarpMax = 64;         // items with at most this many digis are clustered by one warp
 constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory
 
+// Items per work-queue ticket of a launch of EM items on `grid` clustering
+// blocks: kGroup, halved (down to 4) while there would be fewer than two
+// tickets per block, so that large items of small launches spread over blocks.
+__host__ __device__ inline uint32_t ticket_items(uint64_t EM, unsigned grid)
+{
+    uint32_t g = kGroup;
+    while (g > 4 && (EM + g - 1) / g < 2ull * grid) g >>= 1;
+    return g;
+}
+
 // A cluster parked between the clustering phase and the ordered write.
 struct StagedCluster {
     int32_t id, charge, npix;

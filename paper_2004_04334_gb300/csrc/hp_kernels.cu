@@ -1006,7 +1006,8 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
     uint32_t *spre = sbits + nwords;
 
     const uint64_t EM = (uint64_t)L.E * M;
-    const uint64_t ngroups = (EM + kGroup - 1) / kGroup;
+    const uint32_t G = ticket_items(EM, gridDim.x);
+    const uint64_t ngroups = (EM + G - 1) / G;
     const unsigned long long kAgg = 1ull << 62;
     if (tid == 0) {
         s_head = 0;
@@ -1022,10 +1023,10 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
             if (g >= ngroups) {
                 tickets_left = false;
             } else {
-                const uint64_t item0 = g * kGroup;
+                const uint64_t item0 = g * G;
                 if (tid < (uint32_t)kGroup) {
                     const uint64_t item = item0 + tid;
-                    const bool ok = item < EM;
+                    const bool ok = tid < G && item < EM;
                     s_n[tid] = ok ? L.ws.count[item] : 0u;
                     s_b[tid] = ok ? L.ws.boff[item] : 0u;
                     s_K[tid] = 0;
@@ -1116,7 +1117,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
             if (!s_ok) break;
             const unsigned long long P = s_prefix;
             const uint32_t tot = s_pref[kGroup];
-            const uint64_t item0 = (uint64_t)pd.g * kGroup;
+            const uint64_t item0 = (uint64_t)pd.g * G;
             for (uint32_t o = tid; o < tot; o += kCCThreads) {
                 int i = 0;
                 while (i + 1 < kGroup && s_pref[i + 1] <= o) ++i;
@@ -1132,7 +1133,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
                 }
             }
             if (tid == 0 && P + tot > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
-            if (tid < (uint32_t)kGroup) {
+            if (tid < G) {
                 const uint64_t item = item0 + tid;
                 if (item < EM && item % M == 0) L.out.cluster_offsets[item / M] = P + s_pref[tid];
             }
@@ -1196,7 +1197,8 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
         return base ? static_cast<unsigned char *>(base) + o : nullptr;
     };
     const uint64_t EM = (uint64_t)E * M;
-    const uint64_t ngroups = (EM + kGroup - 1) / kGroup;
+    const uint32_t G = ticket_items(EM, (unsigned)(cc_grid > 0 ? cc_grid : 1));
+    const uint64_t ngroups = (EM + G - 1) / G;
     Workspace w{};
     w.ctl = reinterpret_cast<uint32_t *>(take(64));
     w.event_err = reinterpret_cast<uint32_t *>(take(4ull * E));

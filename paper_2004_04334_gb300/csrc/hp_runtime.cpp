@@ -344,7 +344,8 @@ hp::Geometry geometry(const hp_ctx *ctx)
 
 int cc_grid_for(const hp_ctx *ctx, uint32_t E)
 {
-    const uint64_t groups = ((uint64_t)E * ctx->cfg.n_modules + hp::kGroup - 1) / hp::kGroup;
+    // enough blocks for tickets of the smallest size (see ticket_items)
+    const uint64_t groups = ((uint64_t)E * ctx->cfg.n_modules + 3) / 4;
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(groups, (uint64_t)ctx->cc_grid));
 }
 
