@@ -32,6 +32,10 @@
  * pixel_thr >= 1, gain >= 0 and 255 * gain - pedestal <= INT32_MAX /
  * (rows * cols) (every charge sum then fits int32), else ORACLE_EINVAL.
  *
+ * A second function, oracle_hits, takes the kept clusters one step further
+ * along Fig. 1 (clusters -> hits): module placement turns each centroid into
+ * a global position; its definition is written above the function.
+ *
  * Step 3 is a textbook sequential union-find (path halving, link the root
  * of one tree under the other); the component id of step 4 is then the
  * smallest linear index found among the members, independent of how the
@@ -272,4 +276,28 @@ int oracle_batch(const oracle_geometry *g, uint32_t n_events, const uint64_t *of
     cluster_offsets[n_events] = total;
     out->n_clusters = total;
     return first;
+}
+
+/*
+ * Hits: the clusters -> hits step of the paper's Fig. 1 (the GPU branch
+ * produces hits from raw data directly).  A cluster of module m with
+ * centroid (x, y) in pixel units (pixel (r, c) centred at (r, c)) has local
+ * coordinates u = (x - (rows - 1) / 2) * pitch_row and
+ * v = (y - (cols - 1) / 2) * pitch_col about the module centre, and global
+ * position origin[m] + R[m] (u, v, 0), R[m] row-major.  Computed in double.
+ */
+void oracle_hits(uint32_t rows, uint32_t cols, double pitch_row, double pitch_col, const float *origin,
+                 const float *rot, uint64_t n, const uint32_t *module, const double *x, const double *y,
+                 double *gx, double *gy, double *gz)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint32_t m = module[i];
+        const double u = (x[i] - 0.5 * (double)(rows - 1)) * pitch_row;
+        const double v = (y[i] - 0.5 * (double)(cols - 1)) * pitch_col;
+        const float *o = origin + 3 * (size_t)m;
+        const float *R = rot + 9 * (size_t)m;
+        gx[i] = (double)o[0] + (double)R[0] * u + (double)R[1] * v;
+        gy[i] = (double)o[1] + (double)R[3] * u + (double)R[4] * v;
+        gz[i] = (double)o[2] + (double)R[6] * u + (double)R[7] * v;
+    }
 }

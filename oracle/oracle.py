@@ -67,6 +67,11 @@ def _load():
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Out),
                                          ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_batch.restype = ctypes.c_int
+            lib.oracle_hits.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]
+            lib.oracle_hits.restype = None
             _lib = lib
     return _lib
 
@@ -140,3 +145,18 @@ def reconstruct_workload(w, events=None, **kw) -> Clusters:
     if events is not None:
         w = w.subset(events)
     return reconstruct_batch(w.words, w.modules, w.offsets, w.n_modules, w.gain, w.pedestal, **kw)
+
+
+def hits(module, x, y, origin, rot, pitch_row, pitch_col, rows=ROWS, cols=COLS):
+    """Global hit positions (double[n] x 3) of clusters (module, centroid x, y)."""
+    lib = _load()
+    module = np.ascontiguousarray(module, np.uint32)
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    origin = np.ascontiguousarray(origin, np.float32)
+    rot = np.ascontiguousarray(rot, np.float32)
+    n = len(module)
+    gx, gy, gz = (np.empty(n, np.float64) for _ in range(3))
+    lib.oracle_hits(rows, cols, pitch_row, pitch_col, origin.ctypes.data, rot.ctypes.data, n, module.ctypes.data,
+                    x.ctypes.data, y.ctypes.data, gx.ctypes.data, gy.ctypes.data, gz.ctypes.data)
+    return gx, gy, gz

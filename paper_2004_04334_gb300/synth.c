@@ -303,3 +303,35 @@ uint64_t synth_child_seed(uint64_t base, uint64_t index)
     splitmix64(&x);
     return splitmix64(&x);
 }
+
+/*
+ * Synthetic barrel geometry for hits: module m sits on one of four layers
+ * (radii 2.9, 6.8, 10.9, 16.0 cm), at azimuth phi and position z, facing
+ * outwards.  Local coordinate u runs along the module's rows (global z),
+ * v along its columns (the tangential direction).  origin[3m..] is the
+ * module centre, rot[9m..] the row-major matrix R with global = origin +
+ * R (u, v, 0).  Holds no reconstruction arithmetic.
+ */
+void synth_barrel_geometry(uint32_t n_modules, uint32_t rows, uint32_t cols, double pitch_row, double pitch_col,
+                           float *origin, float *rot)
+{
+    static const double radius[4] = {2.9, 6.8, 10.9, 16.0};
+    const double length = rows * pitch_row; /* along z */
+    const uint32_t nz = 8;
+    const uint32_t per_layer = (n_modules + 3) / 4;
+    for (uint32_t m = 0; m < n_modules; ++m) {
+        const uint32_t layer = m / per_layer, k = m % per_layer;
+        const uint32_t nphi = (per_layer + nz - 1) / nz;
+        const double phi = 6.283185307179586 * (double)(k % nphi) / (double)nphi;
+        const double z = ((double)(k / nphi) - 0.5 * (double)(nz - 1)) * length;
+        const double cp = cos(phi), sp = sin(phi);
+        origin[3 * m + 0] = (float)(radius[layer] * cp);
+        origin[3 * m + 1] = (float)(radius[layer] * sp);
+        origin[3 * m + 2] = (float)z;
+        float *R = rot + 9 * m;
+        R[0] = 0.0f, R[1] = (float)-sp, R[2] = (float)cp;
+        R[3] = 0.0f, R[4] = (float)cp, R[5] = (float)sp;
+        R[6] = 1.0f, R[7] = 0.0f, R[8] = 0.0f;
+        (void)cols;
+    }
+}

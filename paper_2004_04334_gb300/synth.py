@@ -89,6 +89,9 @@ def _load():
             lib.synth_exponential.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                               ctypes.c_void_p]
             lib.synth_exponential.restype = None
+            lib.synth_barrel_geometry.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+            lib.synth_barrel_geometry.restype = None
             lib.synth_child_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.synth_child_seed.restype = ctypes.c_uint64
             _lib = lib
@@ -266,6 +269,19 @@ def workload(name: str, n_events: int | None = None, seed: int | None = None) ->
         cfgs = [scaled_tiny(t) for t in sizes]
         return _assemble(name, cfgs, [child_seed(base, e) for e in range(E)], TINY.n_modules, calib_seed)
     raise KeyError(name)
+
+
+PITCH_ROW, PITCH_COL = 0.01, 0.015  # cm: 100 um x 150 um pixels
+
+
+def barrel_geometry(n_modules: int, pitch_row: float = PITCH_ROW, pitch_col: float = PITCH_COL):
+    """Synthetic module placement: (origin float32[M, 3], rotation float32[M, 3, 3])
+    with global = origin + R @ (u, v, 0) for local (u, v) in cm."""
+    lib = _load()
+    origin = np.empty((n_modules, 3), np.float32)
+    rot = np.empty((n_modules, 3, 3), np.float32)
+    lib.synth_barrel_geometry(n_modules, ROWS, COLS, pitch_row, pitch_col, origin.ctypes.data, rot.ctypes.data)
+    return origin, rot
 
 
 def pack(row, col, adc) -> np.ndarray:
