@@ -319,6 +319,8 @@ def run_ours(a):
     path_bytes = algorithmic_bytes(N, E, M, n_clusters)
     shares = {k: round(v[1] / max(1e-12, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
 
+    chain = _chain(a, ctx, w, out, n_clusters, dev, stream, step, barrier, world)
+
     e2e = per_event = serving = None
     if not a.device_only:
         e2e, per_event = _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world)
@@ -343,6 +345,7 @@ def run_ours(a):
                          "traffic": _traffic(name, N), "algorithmic_bytes_per_launch": kb,
                          "mean_launch_ms": per_launch_s * 1000, "kernel_shares": shares},
             "e2e": e2e,
+            "chain": chain,
             "per_event": per_event,
             "batched_vs_per_event": value / per_event["value"] if per_event else None,
             "serving": serving,
@@ -353,6 +356,54 @@ def run_ours(a):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _chain(a, ctx, w, out, n_clusters, dev, stream, step, barrier, world):
+    """raw -> clusters -> hits, device-resident on one stream: the chain's
+    events/s and the hits kernel's own launch time (CUDA events around it)."""
+    import torch
+
+    E, M = w.n_events, w.n_modules
+    origin, rot = synth.barrel_geometry(M)
+    ctx.set_geometry(origin, rot, synth.PITCH_ROW, synth.PITCH_COL)
+    cap = out.struct.capacity
+    hxyz = [torch.empty(cap, dtype=torch.float32, device=dev) for _ in range(3)]
+
+    def hits():
+        ctx.hits_device(E, cap, out.cluster_offsets.data_ptr(), out.module.data_ptr(), out.x.data_ptr(),
+                        out.y.data_ptr(), hxyz[0].data_ptr(), hxyz[1].data_ptr(), hxyz[2].data_ptr(),
+                        stream.cuda_stream)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+        hits()
+    barrier()
+    marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for m0, m1 in marks:
+        step()
+        m0.record(stream)
+        hits()
+        m1.record(stream)
+    c1.record(stream)
+    barrier()
+    t = c0.elapsed_time(c1) / 1000.0
+    hits_s = sum(m0.elapsed_time(m1) for m0, m1 in marks) / 1000.0 / a.steps
+    if world > 1:
+        v = torch.tensor([t], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(v, op=torch.distributed.ReduceOp.MAX)
+        t = float(v.item())
+    kb = 24 * n_clusters + 48 * M + 8 * (E + 1)
+    peak, peak_kind = _peaks()
+    return {"value": world * E * a.steps / t, "unit": "events/s", "ms_per_step": 1000 * t / a.steps,
+            "what": "hp_reconstruct_device + hp_hits_device per step on one stream",
+            "hits_kernel": {"mean_launch_ms": hits_s * 1000, "hits_per_launch": n_clusters,
+                            "algorithmic_bytes_per_launch": kb, "achieved": kb / hits_s / 1e9, "unit": "GB/s",
+                            "peak": peak, "frac": kb / hits_s / 1e9 / peak, "peak_kind": peak_kind,
+                            "note": "its inputs were just written by the clustering kernel and may be "
+                                    "partly L2-resident"}}
 
 
 def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):

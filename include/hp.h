@@ -13,7 +13,10 @@
  *   hp_fetch_clusters                     produce() (Sec. 2): collect the
  *        result once the stream has signalled completion;
  *   hp_event_* accessors                  the Product<T> wrapper of Sec. 4.2:
- *        device id, stream and CUDA event of the work that made the result.
+ *        device id, stream and CUDA event of the work that made the result;
+ *   hp_enqueue_hits                       a second module consuming that
+ *        product under the ScopedContext stream rules of Sec. 4.2 (the
+ *        clusters -> hits step of Fig. 1).
  *
  * The device work is the raw -> clusters step of the paper's Fig. 1: decode
  * digi words, bucket them by module, calibrate q = adc * gain[m] - pedestal[m]
@@ -144,6 +147,8 @@ typedef struct hp_stats {
     uint64_t kernel_launches;   /* kernels launched by the library */
     uint64_t serve_batches;     /* batches launched by the serving loop */
     uint64_t serve_requests;    /* requests accepted by hp_submit */
+    uint64_t consumer_stream_reuses; /* hp_enqueue_hits calls that took the product's own stream */
+    uint64_t consumer_stream_waits;  /* hp_enqueue_hits calls that queued cudaStreamWaitEvent */
 } hp_stats;
 
 /* Serving loop configuration (hp_serve_start). */
@@ -269,6 +274,77 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
 hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
                                         const uint32_t *d_words, const uint16_t *d_module_ids,
                                         const hp_device_clusters *out, void *stream);
+
+/*
+ * Hits: the clusters -> hits step of the paper's Fig. 1, the stage after the
+ * clusters, run as a second module of a GPU chain (Sec. 4.2).
+ *
+ * Placement of module m: origin[3m .. 3m+2] (cm) and the row-major rotation
+ * rot[9m .. 9m+8].  A cluster with centroid (x, y) in pixel units (pixel
+ * (r, c) has its centre at (r, c)) lies at local
+ *   u = (x - (rows - 1) / 2) * pitch_row,  v = (y - (cols - 1) / 2) * pitch_col
+ * about the module centre, and its hit at origin + rot * (u, v, 0).  The
+ * kernel computes in FP32.
+ *
+ * hp_set_geometry copies the placement (host arrays of n_modules entries) to
+ * the device; it blocks (set-up call).  Calling it again installs a new
+ * placement for later hp_enqueue_hits calls; work already queued keeps the
+ * one it was queued with.  Errors: HP_EINVAL (NULL arrays, pitches not
+ * finite and > 0), HP_ENOMEM, HP_ECUDA.
+ */
+hp_status hp_set_geometry(hp_ctx *ctx, const float *origin, const float *rot, float pitch_row, float pitch_col);
+
+/*
+ * Host view of a completed hits event (library-owned pinned memory, valid
+ * until hp_release_event).  Hit i is cluster i of the consumed event: same
+ * order, same per-event offsets and status.
+ */
+typedef struct hp_hits {
+    uint32_t n_events;
+    uint64_t n_hits;
+    uint64_t tag;
+    const uint64_t *hit_offsets;   /* [n_events + 1] */
+    const int32_t *event_status;   /* [n_events] */
+    const uint32_t *module;        /* [n_hits] */
+    const float *x, *y, *z;        /* [n_hits] global position (cm) */
+} hp_hits;
+
+/*
+ * A consumer of a clusters event (the Product<T> of an hp_enqueue_event or
+ * hp_enqueue_batch call), following the ScopedContext rules of Sec. 4.2:
+ * the work runs on the product's device; the first consumer of a product
+ * queues its kernel on the product's own stream (stream order is the
+ * synchronisation); every later consumer takes another stream of the
+ * context and, if the product's CUDA event has not completed yet, queues
+ * cudaStreamWaitEvent on it.  The call never waits for the device.  The
+ * result is a new event (*out) with its own completion, callback
+ * (hp_on_complete), query, stream and CUDA event, read with hp_fetch_hits
+ * and released with hp_release_event.  The consumer holds the product: a
+ * product released while consumers are queued is freed only once they have
+ * run.  The product must not have been released before this call, and must
+ * be a clusters event of hp_enqueue_event/hp_enqueue_batch (not a serving
+ * request, not a hits event).  flags is reserved (0).
+ * Errors: HP_EINVAL (no geometry set, wrong kind of event), HP_ENOMEM,
+ * HP_ECUDA.
+ */
+hp_status hp_enqueue_hits(hp_event *clusters, uint32_t flags, hp_event **out);
+
+/* produce() of a hits event: as hp_fetch_clusters (HP_ENOTREADY before
+ * completion, else the status of the consumed product). */
+hp_status hp_fetch_hits(hp_event *ev, hp_hits *view);
+
+/*
+ * Device-resident hits: reads the clusters that hp_reconstruct_device wrote
+ * (d_cluster_offsets[n_events] clusters, at most capacity, in d_module,
+ * d_x, d_y) and writes the hit positions to d_hx, d_hy, d_hz (capacity
+ * entries each); all device pointers owned by the caller.  Queued on
+ * `stream` behind the clusters (the same stream gives the ordering); the
+ * call returns without waiting and allocates nothing.
+ * Errors: HP_EINVAL (no geometry set, NULL pointers), HP_ECUDA.
+ */
+hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, const uint64_t *d_cluster_offsets,
+                         const uint32_t *d_module, const float *d_x, const float *d_y, float *d_hx, float *d_hy,
+                         float *d_hz, void *stream);
 
 /*
  * Serving (continuous batching).  hp_serve_start starts an admitter thread.

@@ -121,6 +121,35 @@ struct GatherEntry {
 cudaError_t launch_gather(const GatherEntry *table, uint32_t n_requests, uint64_t max_n, uint32_t *words,
                           uint16_t *modules, cudaStream_t stream);
 
+// Module placement for the clusters -> hits step, as the device holds it:
+// per module three affine rows (r_i0, r_i1, o_i, 0), i = x, y, z, so that
+// a hit is row_i . (u, v, 1).  Only the first two rotation columns matter
+// because the local point has w = 0.
+struct Placement {
+    const float4 *rows;  // [3 * M]
+    uint32_t M;
+    float pitch_row, pitch_col;
+    float half_rows, half_cols; // (rows - 1) / 2 and (cols - 1) / 2: the module centre in pixel units
+};
+
+// One hits launch: clusters in, hits out (all device-accessible pointers).
+struct HitsLaunch {
+    Placement p;
+    uint32_t E;
+    uint64_t capacity;                 // room in the cluster and hit arrays
+    const uint64_t *cluster_offsets;   // [E + 1]
+    const int32_t *event_status;       // [E] or null
+    const uint32_t *module;            // [capacity]
+    const float *x, *y;                // [capacity] centroids (pixel units)
+    uint64_t *hit_offsets;             // [E + 1] or null: copy of cluster_offsets
+    int32_t *hit_status;               // [E] or null: copy of event_status
+    uint32_t *hit_module;              // [capacity] or null: copy of module
+    float *hx, *hy, *hz;               // [capacity] global position
+};
+// Queue the hits kernel on `stream` (grid-stride; the cluster count is read
+// on the device, so nothing waits for the clusters to exist).
+cudaError_t launch_hits(const HitsLaunch &h, int max_blocks, cudaStream_t stream);
+
 // Launch parameters of a context (implemented by the runtime): geometry with
 // device calibration pointers, device ordinal, clustering grid size, and
 // whether the context has failed.

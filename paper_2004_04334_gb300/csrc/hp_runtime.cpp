@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -161,7 +162,18 @@ class Pool {
     uint32_t fail_next_ = 0;
 };
 
+// Event state word: completion, callback and release bits, and in bits 8
+// and up the number of consumers (hp_enqueue_hits) that still read the
+// event's outputs.  Every change is one atomic read-modify-write of this
+// word; the change that makes the event destroyable (complete, callback run,
+// released, no consumer left) is the one that frees it, exactly once.
 constexpr uint32_t kDone = 1u, kCbSet = 2u, kCbDone = 4u, kReleaseReq = 8u;
+constexpr uint32_t kHold = 1u << 8;
+
+bool destroyable(uint32_t s)
+{
+    return (s & kDone) && (s & kReleaseReq) && (!(s & kCbSet) || (s & kCbDone)) && (s >> 8) == 0;
+}
 
 struct Serve;
 struct Batch;
@@ -199,6 +211,16 @@ struct hp_ctx {
     std::mutex serve_mu;
     Serve *serve = nullptr;
     std::atomic<uint64_t> serve_batches{0}, serve_requests{0};
+    // hits: module placement (every version stays until hp_destroy, so queued
+    // work keeps the one it was queued with) and the consumer streams
+    std::mutex geom_mu;
+    std::vector<void *> placements;
+    hp::Placement place{};
+    bool has_place = false;
+    std::mutex aux_mu;
+    std::vector<cudaStream_t> aux_streams;
+    std::atomic<uint32_t> next_aux{0};
+    std::atomic<uint64_t> consumer_reuses{0}, consumer_waits{0};
 };
 
 struct hp_event {
@@ -228,6 +250,13 @@ struct hp_event {
     uint32_t index = 0;
     Block staging;               // the request's inputs (pinned), until its batch completes
     uint64_t coff_local[2] = {0, 0};
+    // Product<T> stream rule (Sec. 4.2): set by the first consumer, which takes this event's stream
+    std::atomic<bool> stream_taken{false};
+    // hits events: the consumed clusters event (held until this one's work has run) and the outputs
+    bool hits = false;
+    hp_event *product = nullptr;
+    uint32_t *h_hmodule = nullptr;
+    float *h_hx = nullptr, *h_hy = nullptr, *h_hz = nullptr;
 };
 
 namespace {
@@ -261,17 +290,29 @@ void destroy_event(hp_event *ev)
     delete ev;
 }
 
+// Set `bits` in the state word; free the event if that made it destroyable.
+uint32_t set_state(hp_event *ev, uint32_t bits)
+{
+    const uint32_t prev = ev->state.fetch_or(bits, std::memory_order_acq_rel);
+    if (!destroyable(prev) && destroyable(prev | bits)) destroy_event(ev);
+    return prev;
+}
+
+// A consumer no longer reads the event's outputs.
+void drop_hold(hp_event *ev)
+{
+    const uint32_t prev = ev->state.fetch_sub(kHold, std::memory_order_acq_rel);
+    if (!destroyable(prev) && destroyable(prev - kHold)) destroy_event(ev);
+}
+
 // Completion of one event on the host-function thread: the exactly-once
 // hand-off to the callback (Sec. 2 holder) and a deferred release.
 void complete_event(hp_event *ev)
 {
-    const uint32_t prev = ev->state.fetch_or(kDone, std::memory_order_acq_rel);
+    const uint32_t prev = set_state(ev, kDone);
     if (prev & kCbSet) {
         ev->cb(ev->user, ev, ev->status);
-        const uint32_t p2 = ev->state.fetch_or(kCbDone, std::memory_order_acq_rel);
-        if (p2 & kReleaseReq) destroy_event(ev);
-    } else if (prev & kReleaseReq) {
-        destroy_event(ev);
+        set_state(ev, kCbDone);
     }
 }
 
@@ -293,6 +334,25 @@ void CUDART_CB trampoline(void *p)
     ctx->dev_in_use.fetch_sub(ev->dev_charge);
     ctx->inflight.fetch_sub(1);
     ctx->completed.fetch_add(1);
+    complete_event(ev);
+}
+
+// Completion of a hits event: its status is that of the consumed product
+// (copied per event by the kernel); then the product loses this hold.
+void CUDART_CB hits_trampoline(void *p)
+{
+    hp_event *ev = static_cast<hp_event *>(p);
+    hp_status st = HP_OK;
+    for (uint32_t e = 0; e < ev->E; ++e)
+        if (ev->h_status[e] != 0) {
+            st = (hp_status)ev->h_status[e];
+            break;
+        }
+    ev->status = st;
+    ev->t_done = now_ns();
+    hp_event *prod = ev->product;
+    ev->product = nullptr;
+    drop_hold(prod);
     complete_event(ev);
 }
 
@@ -878,6 +938,44 @@ hp_status serve_stop(hp_ctx *ctx)
 
 } // namespace
 
+namespace {
+
+bool current_placement(hp_ctx *ctx, hp::Placement *p)
+{
+    std::lock_guard<std::mutex> g(ctx->geom_mu);
+    if (!ctx->has_place) return false;
+    *p = ctx->place;
+    return true;
+}
+
+// A stream for a consumer that cannot take its product's stream: one of a
+// second pool, disjoint from the producers' streams (created on first use).
+cudaStream_t consumer_stream(hp_ctx *ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->aux_mu);
+    if (ctx->aux_streams.empty()) {
+        for (size_t i = 0; i < ctx->streams.size(); ++i) {
+            cudaStream_t s;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            ctx->aux_streams.push_back(s);
+        }
+        if (ctx->aux_streams.empty()) return nullptr;
+    }
+    return ctx->aux_streams[ctx->next_aux.fetch_add(1) % ctx->aux_streams.size()];
+}
+
+// Device alias of a pointer into an event's mapped pinned host block.
+template <class T> T *device_alias(const Block &b, T *host)
+{
+    return reinterpret_cast<T *>(static_cast<unsigned char *>(b.dptr) +
+                                 (reinterpret_cast<unsigned char *>(host) - static_cast<unsigned char *>(b.ptr)));
+}
+
+} // namespace
+
 bool hp::context_launch_params(hp_ctx *ctx, hp::Geometry *g, int *device, int *cc_grid)
 {
     if (!ctx || ctx->failed.load()) return false;
@@ -952,6 +1050,7 @@ hp_status hp_destroy(hp_ctx *ctx)
     serve_stop(ctx); // drains a running serving loop (no-op otherwise)
     cudaSetDevice(ctx->device);
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+    for (cudaStream_t s : ctx->aux_streams) cudaStreamSynchronize(s);
     {
         std::lock_guard<std::mutex> g(ctx->ws_mu);
         for (auto &kv : ctx->stream_ws) {
@@ -973,6 +1072,8 @@ hp_status hp_destroy(hp_ctx *ctx)
         for (cudaEvent_t e : r.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
+    for (cudaStream_t s : ctx->aux_streams) cudaStreamDestroy(s);
+    for (void *p : ctx->placements) cudaFree(p);
     cudaFree(ctx->d_gain);
     const bool failed = ctx->failed.load() != 0;
     delete ctx;
@@ -1003,8 +1104,7 @@ hp_status hp_on_complete(hp_event *ev, hp_callback cb, void *user)
     if (prev & kCbSet) return HP_EINVAL;
     if (prev & kDone) {
         cb(user, ev, ev->status);
-        const uint32_t p2 = ev->state.fetch_or(kCbDone, std::memory_order_acq_rel);
-        if (p2 & kReleaseReq) destroy_event(ev);
+        set_state(ev, kCbDone);
     }
     return HP_OK;
 }
@@ -1018,7 +1118,7 @@ hp_status hp_event_query(hp_event *ev)
 
 hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *v)
 {
-    if (!ev || !v) return HP_EINVAL;
+    if (!ev || !v || ev->hits) return HP_EINVAL;
     if (!(ev->state.load(std::memory_order_acquire) & kDone)) return HP_ENOTREADY;
     v->n_events = ev->E;
     v->n_digis = ev->N;
@@ -1040,9 +1140,8 @@ hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *v)
 hp_status hp_release_event(hp_event *ev)
 {
     if (!ev) return HP_EINVAL;
-    const uint32_t prev = ev->state.fetch_or(kReleaseReq, std::memory_order_acq_rel);
+    const uint32_t prev = set_state(ev, kReleaseReq);
     if (prev & kReleaseReq) return HP_EINVAL;
-    if ((prev & kDone) && (!(prev & kCbSet) || (prev & kCbDone))) destroy_event(ev);
     return HP_OK;
 }
 
@@ -1053,6 +1152,208 @@ uint64_t hp_event_latency_ns(const hp_event *ev)
 {
     if (!ev || !(ev->state.load(std::memory_order_acquire) & kDone)) return 0;
     return ev->t_done - ev->t_enq;
+}
+
+hp_status hp_set_geometry(hp_ctx *ctx, const float *origin, const float *rot, float pitch_row, float pitch_col)
+{
+    if (!ctx || !origin || !rot) return HP_EINVAL;
+    if (!(pitch_row > 0.f) || !(pitch_col > 0.f) || !std::isfinite(pitch_row) || !std::isfinite(pitch_col))
+        return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    const uint32_t M = ctx->cfg.n_modules;
+    // affine rows (r_i0, r_i1, o_i, 0) of each module
+    std::vector<float> rows(12 * (size_t)M);
+    for (uint32_t m = 0; m < M; ++m)
+        for (int i = 0; i < 3; ++i) {
+            float *r = &rows[12 * (size_t)m + 4 * i];
+            r[0] = rot[9 * (size_t)m + 3 * i];
+            r[1] = rot[9 * (size_t)m + 3 * i + 1];
+            r[2] = origin[3 * (size_t)m + i];
+            r[3] = 0.f;
+        }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
+    void *d = nullptr;
+    if (cudaMalloc(&d, rows.size() * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ENOMEM;
+    }
+    if (cudaMemcpy(d, rows.data(), rows.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return fail(ctx);
+    }
+    std::lock_guard<std::mutex> g(ctx->geom_mu);
+    ctx->placements.push_back(d);
+    ctx->place.rows = static_cast<const float4 *>(d);
+    ctx->place.M = M;
+    ctx->place.pitch_row = pitch_row;
+    ctx->place.pitch_col = pitch_col;
+    ctx->place.half_rows = 0.5f * (float)(ctx->cfg.rows - 1);
+    ctx->place.half_cols = 0.5f * (float)(ctx->cfg.cols - 1);
+    ctx->has_place = true;
+    return HP_OK;
+}
+
+hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
+{
+    if (!prod || !out || flags != 0) return HP_EINVAL;
+    if (prod->request || prod->hits) return HP_EINVAL;
+    hp_ctx *ctx = prod->ctx;
+    if (ctx->failed.load()) return HP_ECUDA;
+    hp::Placement place;
+    if (!current_placement(ctx, &place)) return HP_EINVAL;
+    const uint32_t E = prod->E;
+    const uint64_t N = prod->N;
+
+    size_t hoff = 0;
+    const size_t h_coff = hoff;
+    hoff = align_up(hoff + 8 * (size_t)(E + 1), 256);
+    const size_t h_status = hoff;
+    hoff = align_up(hoff + 4 * (size_t)E, 256);
+    size_t h_arr[4];
+    for (int i = 0; i < 4; ++i) {
+        h_arr[i] = hoff;
+        hoff = align_up(hoff + 4 * N, 256);
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx); // the product's device (Sec. 4.2)
+    hp_event *ev = new (std::nothrow) hp_event();
+    if (!ev) return HP_ENOMEM;
+    ev->ctx = ctx;
+    ev->E = E;
+    ev->N = N;
+    ev->tag = prod->tag;
+    ev->hits = true;
+    if (ctx->hpool.alloc(hoff, &ev->host) != HP_OK) {
+        delete ev;
+        return HP_ENOMEM;
+    }
+    ev->done = take_cuda_event(ctx);
+    if (!ev->done) {
+        ctx->hpool.free(ev->host);
+        delete ev;
+        return fail(ctx);
+    }
+    unsigned char *hb = static_cast<unsigned char *>(ev->host.ptr);
+    ev->h_coff = reinterpret_cast<uint64_t *>(hb + h_coff);
+    ev->h_status = reinterpret_cast<int32_t *>(hb + h_status);
+    ev->h_hmodule = reinterpret_cast<uint32_t *>(hb + h_arr[0]);
+    ev->h_hx = reinterpret_cast<float *>(hb + h_arr[1]);
+    ev->h_hy = reinterpret_cast<float *>(hb + h_arr[2]);
+    ev->h_hz = reinterpret_cast<float *>(hb + h_arr[3]);
+
+    // ScopedContext (Sec. 4.2): the first consumer takes the product's stream;
+    // a later one takes another stream and waits on the product's CUDA event
+    // unless that event has already completed.
+    cudaStream_t s = prod->stream;
+    bool wait = false;
+    if (prod->stream_taken.exchange(true)) {
+        s = consumer_stream(ctx);
+        if (!s) {
+            ctx->hpool.free(ev->host);
+            {
+                std::lock_guard<std::mutex> g(ctx->cev_mu);
+                ctx->cev_free.push_back(ev->done);
+            }
+            delete ev;
+            return fail(ctx);
+        }
+        const cudaError_t q = cudaEventQuery(prod->done);
+        if (q == cudaErrorNotReady) {
+            cudaGetLastError();
+            wait = true;
+        } else if (q != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx);
+        }
+    }
+    ev->stream = s;
+    ev->product = prod;
+    prod->state.fetch_add(kHold, std::memory_order_acq_rel); // the product outlives this consumer's work
+    ev->t_enq = now_ns();
+    {
+        std::lock_guard<std::mutex> g(ctx->live_mu);
+        ctx->live.insert(ev);
+    }
+    hp::HitsLaunch h;
+    h.p = place;
+    h.E = E;
+    h.capacity = N;
+    h.cluster_offsets = device_alias(prod->host, prod->h_coff);
+    h.event_status = device_alias(prod->host, prod->h_status);
+    h.module = device_alias(prod->host, prod->h_module);
+    h.x = device_alias(prod->host, prod->h_x);
+    h.y = device_alias(prod->host, prod->h_y);
+    h.hit_offsets = device_alias(ev->host, ev->h_coff);
+    h.hit_status = device_alias(ev->host, ev->h_status);
+    h.hit_module = device_alias(ev->host, ev->h_hmodule);
+    h.hx = device_alias(ev->host, ev->h_hx);
+    h.hy = device_alias(ev->host, ev->h_hy);
+    h.hz = device_alias(ev->host, ev->h_hz);
+    cudaError_t err = cudaSuccess;
+    if (wait) err = cudaStreamWaitEvent(s, prod->done, 0);
+    if (err == cudaSuccess) err = hp::launch_hits(h, 4 * ctx->sm_count, s);
+    if (err == cudaSuccess) err = cudaEventRecord(ev->done, s);
+    if (err == cudaSuccess) err = cudaLaunchHostFunc(s, hits_trampoline, ev);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx); // the context is unusable; its memory is reclaimed by hp_destroy
+    }
+    if (wait)
+        ctx->consumer_waits.fetch_add(1);
+    else if (s == prod->stream)
+        ctx->consumer_reuses.fetch_add(1);
+    ctx->kernels.fetch_add(1);
+    *out = ev;
+    return HP_OK;
+}
+
+hp_status hp_fetch_hits(hp_event *ev, hp_hits *v)
+{
+    if (!ev || !v || !ev->hits) return HP_EINVAL;
+    if (!(ev->state.load(std::memory_order_acquire) & kDone)) return HP_ENOTREADY;
+    v->n_events = ev->E;
+    v->n_hits = ev->h_coff[ev->E];
+    if (v->n_hits > ev->N) v->n_hits = ev->N;
+    v->tag = ev->tag;
+    v->hit_offsets = ev->h_coff;
+    v->event_status = ev->h_status;
+    v->module = ev->h_hmodule;
+    v->x = ev->h_hx;
+    v->y = ev->h_hy;
+    v->z = ev->h_hz;
+    return ev->status;
+}
+
+hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, const uint64_t *d_cluster_offsets,
+                         const uint32_t *d_module, const float *d_x, const float *d_y, float *d_hx, float *d_hy,
+                         float *d_hz, void *stream)
+{
+    if (!ctx || !d_cluster_offsets) return HP_EINVAL;
+    if (capacity > 0 && (!d_module || !d_x || !d_y || !d_hx || !d_hy || !d_hz)) return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    hp::Placement place;
+    if (!current_placement(ctx, &place)) return HP_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
+    hp::HitsLaunch h;
+    h.p = place;
+    h.E = n_events;
+    h.capacity = capacity;
+    h.cluster_offsets = d_cluster_offsets;
+    h.event_status = nullptr;
+    h.module = d_module;
+    h.x = d_x;
+    h.y = d_y;
+    h.hit_offsets = nullptr;
+    h.hit_status = nullptr;
+    h.hit_module = nullptr;
+    h.hx = d_hx;
+    h.hy = d_hy;
+    h.hz = d_hz;
+    if (hp::launch_hits(h, 4 * ctx->sm_count, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx);
+    }
+    ctx->kernels.fetch_add(1);
+    return HP_OK;
 }
 
 hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
@@ -1300,6 +1601,8 @@ hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)
     o->kernel_launches = ctx->kernels.load();
     o->serve_batches = ctx->serve_batches.load();
     o->serve_requests = ctx->serve_requests.load();
+    o->consumer_stream_reuses = ctx->consumer_reuses.load();
+    o->consumer_stream_waits = ctx->consumer_waits.load();
     return ctx->failed.load() ? HP_ECUDA : HP_OK;
 }
 

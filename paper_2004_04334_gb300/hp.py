@@ -28,7 +28,8 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_event_cuda_event", "hp_event_latency_ns", "hp_reconstruct_device", "hp_reconstruct_device_noalloc",
            "hp_get_stats",
            "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations", "hp_serve_start", "hp_submit",
-           "hp_serve_stop", "hp_serve_replay")
+           "hp_serve_stop", "hp_serve_replay", "hp_set_geometry", "hp_enqueue_hits", "hp_fetch_hits",
+           "hp_hits_device")
 
 
 class HPError(RuntimeError):
@@ -63,7 +64,13 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "device_mallocs", "host_mallocs", "pool_hits", "device_bytes_in_use", "device_bytes_cached",
         "events_enqueued", "events_completed", "inflight", "h2d_bytes", "d2h_bytes", "kernel_launches",
-        "serve_batches", "serve_requests")]
+        "serve_batches", "serve_requests", "consumer_stream_reuses", "consumer_stream_waits")]
+
+
+class HitsView(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint32), ("n_hits", ctypes.c_uint64), ("tag", ctypes.c_uint64),
+                ("hit_offsets", ctypes.c_void_p), ("event_status", ctypes.c_void_p), ("module", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -112,6 +119,10 @@ def load(path: str = LIB_PATH):
             "hp_submit": (I, [V, V, V, U64, U64, V, V, P(V)]),
             "hp_serve_stop": (I, [V]),
             "hp_serve_replay": (I, [V, U32, U64, V, V, U32, V, V, V, V, V, P(U64)]),
+            "hp_set_geometry": (I, [V, V, V, ctypes.c_float, ctypes.c_float]),
+            "hp_enqueue_hits": (I, [V, U32, P(V)]),
+            "hp_fetch_hits": (I, [V, P(HitsView)]),
+            "hp_hits_device": (I, [V, U32, U64, V, V, V, V, V, V, V, V]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -155,6 +166,24 @@ class Result:
         return Result(int(self.event_status[e]), 1, np.array([0, b - a], np.uint64), self.event_status[e:e + 1],
                       self.module[a:b], self.id[a:b], self.charge[a:b], self.npix[a:b], self.x[a:b], self.y[a:b],
                       None, self.tag)
+
+
+@dataclass
+class HitsResult:
+    """Host copy of a hits event (see hp_hits in include/hp.h)."""
+    status: int
+    n_events: int
+    hit_offsets: np.ndarray
+    event_status: np.ndarray
+    module: np.ndarray
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    tag: int
+
+    @property
+    def n_hits(self) -> int:
+        return len(self.x)
 
 
 def _arr(ptr, n, dtype, copy=True):
@@ -247,12 +276,36 @@ class Event:
                       a(v.npix, C, np.int32), a(v.x, C, np.float32), a(v.y, C, np.float32),
                       a(v.label, N, np.int32) if v.label else None, int(v.tag))
 
+    def hits(self) -> "HitsEvent":
+        """Queue the clusters -> hits consumer of this event (hp_enqueue_hits)."""
+        h = ctypes.c_void_p()
+        _check(self._ctx._lib.hp_enqueue_hits(self._h, 0, ctypes.byref(h)), "hp_enqueue_hits")
+        return HitsEvent(self._ctx, h.value, self.n_events, self.n_digis)
+
     def release(self):
         if not self._released:
             self._released = True
             _check(self._ctx._lib.hp_release_event(self._h), "hp_release_event")
             with _events_lock:
                 _events.pop(self._id, None)
+
+
+class HitsEvent(Event):
+    """A hits event: the consumer of a clusters event (hp_enqueue_hits)."""
+
+    def fetch(self, copy: bool = True) -> HitsResult:
+        v = HitsView()
+        st = self._ctx._lib.hp_fetch_hits(self._h, ctypes.byref(v))
+        if st in (HP_ENOTREADY, HP_EINVAL):
+            raise HPError(st, "hp_fetch_hits")
+        E, H = v.n_events, v.n_hits
+        a = lambda p, n, t: _arr(p, n, t, copy)  # noqa: E731
+        return HitsResult(st, E, a(v.hit_offsets, E + 1, np.uint64), a(v.event_status, E, np.int32),
+                          a(v.module, H, np.uint32), a(v.x, H, np.float32), a(v.y, H, np.float32),
+                          a(v.z, H, np.float32), int(v.tag))
+
+    def hits(self):
+        raise HPError(HP_EINVAL, "hp_enqueue_hits: a hits event is not a clusters product")
 
 
 class Context:
@@ -323,6 +376,21 @@ class Context:
         _check(self._lib.hp_reconstruct_device(self._h, n_events, n_digis, d_offsets, d_words, d_modules,
                                                ctypes.byref(out.struct), ctypes.c_void_p(stream)),
                "hp_reconstruct_device")
+
+    def set_geometry(self, origin, rot, pitch_row, pitch_col):
+        """Install the module placement for hits (origin float[M,3] cm, rot float[M,3,3])."""
+        origin = np.ascontiguousarray(origin, np.float32).reshape(-1)
+        rot = np.ascontiguousarray(rot, np.float32).reshape(-1)
+        if len(origin) != 3 * self.n_modules or len(rot) != 9 * self.n_modules:
+            raise ValueError("origin/rot must have n_modules entries")
+        _check(self._lib.hp_set_geometry(self._h, origin.ctypes.data, rot.ctypes.data, pitch_row, pitch_col),
+               "hp_set_geometry")
+
+    def hits_device(self, n_events, capacity, d_cluster_offsets, d_module, d_x, d_y, d_hx, d_hy, d_hz,
+                    stream: int = 0):
+        """Queue the device-resident clusters -> hits pass (device addresses)."""
+        _check(self._lib.hp_hits_device(self._h, n_events, capacity, d_cluster_offsets, d_module, d_x, d_y, d_hx,
+                                        d_hy, d_hz, ctypes.c_void_p(stream)), "hp_hits_device")
 
     def serve_start(self, budget_bytes=0, max_batch_events=0, max_batch_digis=0, max_inflight_batches=0,
                     max_pending=0, want_labels=False):
