@@ -66,6 +66,13 @@ typedef enum hp_status {
 #define HP_INPUT_NOCOPY 0x2u /* enqueue: the input arrays are pinned host (or device)
                                 memory that stays valid until the event completes;
                                 they are read directly instead of being staged */
+#define HP_KEEP_ON_DEVICE 0x4u /* enqueue: keep the clusters (and labels) in device
+                                  memory until release; nothing but per-event status
+                                  and offsets goes to the host (see hp_enqueue_transfer) */
+
+/* what of hp_enqueue_transfer */
+#define HP_TRANSFER_CLUSTERS 0x1u
+#define HP_TRANSFER_LABELS 0x2u
 
 /*
  * Context configuration.  gain and pedestal are host arrays of n_modules
@@ -276,6 +283,70 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
                                         const hp_device_clusters *out, void *stream);
 
 /*
+ * Autotuner.  The clustering kernel has launch parameters whose best values
+ * depend on the launch shape (how many (event, module) items, how many
+ * digis per item):
+ *   tile_slots     capacity of the shared-memory tile of the block tier:
+ *                  items with more digis are clustered in global scratch;
+ *   blocks_per_sm  resident clustering blocks per SM, 2 or 3 (3 caps the
+ *                  kernel at 40 registers a thread and needs a smaller tile);
+ *   ticket_items   (event, module) items per work-queue ticket, 16, 8 or 4
+ *                  (halved further for launches too small to fill the GPU);
+ *   warp_max       largest item (digis) clustered by a single warp, 32 or 64.
+ * Labels and clusters are the same for every setting; only speed differs.
+ * Settings are kept per shape bucket (log2 of n_events * n_modules, log2 of
+ * the mean digis per item) and used by every later launch in the bucket
+ * (host, device, graph and serving paths); a bucket without an entry uses
+ * the defaults (4096 slots, 2 blocks, 16 items, 64 digis).
+ *
+ * hp_autotune times every candidate (hp_tuning_candidates) on the given
+ * device-resident inputs, `reps` passes each after one warm-up, on a private
+ * stream (blocking: a set-up call), stores the fastest for the shape's
+ * bucket and returns it; cand_ms[i] (if given, up to cap entries) receives
+ * candidate i's mean pass time in milliseconds.  `out` receives a valid
+ * result of the inputs.
+ * Environment: HP_TUNE=off ignores stored settings (defaults only);
+ * HP_TUNE=search makes hp_reconstruct_device tune a bucket the first time
+ * it sees it (that call blocks); HP_TUNE_CACHE=<path> loads settings from
+ * that file at hp_create (one JSON object per line, entries of other
+ * devices or module sizes ignored) and hp_autotune appends its results.
+ * Errors: as hp_reconstruct_device; hp_set_tuning returns HP_EINVAL for a
+ * setting outside the candidates' ranges (t == NULL clears the bucket).
+ */
+typedef struct hp_tuning {
+    uint32_t tile_slots;
+    uint32_t blocks_per_sm;
+    uint32_t ticket_items;
+    uint32_t warp_max;
+} hp_tuning;
+hp_status hp_tuning_candidates(hp_ctx *ctx, uint32_t cap, hp_tuning *list, uint32_t *n);
+hp_status hp_get_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, hp_tuning *out);
+hp_status hp_set_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const hp_tuning *t);
+hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                      const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
+                      uint32_t reps, uint32_t cap, double *cand_ms, hp_tuning *best, double *best_ms);
+
+/*
+ * CUDA-graph form of the device-resident entry: hp_graph_capture records
+ * one hp_reconstruct_device pass (a memset and five kernels) for fixed
+ * arguments into an executable CUDA graph with its own scratch;
+ * hp_graph_launch replays it on `stream` (one cudaGraphLaunch, no
+ * allocation, no host work per launch).  The graph keeps the pointers and
+ * sizes it was captured with: refill the same input buffers between
+ * launches.  Launches of one graph are serialised by CUDA.  (The paper
+ * found graphs too restrictive for its framework, Sec. 4; for a fixed-shape
+ * batch they only remove launch overhead.)  hp_graph_destroy waits for the
+ * device (it frees the scratch); hp_destroy destroys graphs left over.
+ * Errors: as hp_reconstruct_device; HP_ECUDA if capture fails.
+ */
+typedef struct hp_graph hp_graph;
+hp_status hp_graph_capture(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                           const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
+                           hp_graph **graph);
+hp_status hp_graph_launch(hp_graph *graph, void *stream);
+hp_status hp_graph_destroy(hp_graph *graph);
+
+/*
  * Hits: the clusters -> hits step of the paper's Fig. 1, the stage after the
  * clusters, run as a second module of a GPU chain (Sec. 4.2).
  *
@@ -323,7 +394,7 @@ typedef struct hp_hits {
  * product released while consumers are queued is freed only once they have
  * run.  The product must not have been released before this call, and must
  * be a clusters event of hp_enqueue_event/hp_enqueue_batch (not a serving
- * request, not a hits event).  flags is reserved (0).
+ * request, not a hits or transfer event).  flags is reserved (0).
  * Errors: HP_EINVAL (no geometry set, wrong kind of event), HP_ENOMEM,
  * HP_ECUDA.
  */
@@ -332,6 +403,26 @@ hp_status hp_enqueue_hits(hp_event *clusters, uint32_t flags, hp_event **out);
 /* produce() of a hits event: as hp_fetch_clusters (HP_ENOTREADY before
  * completion, else the status of the consumed product). */
 hp_status hp_fetch_hits(hp_event *ev, hp_hits *view);
+
+/*
+ * Transfer on demand (Sec. 4.3).  An event enqueued with HP_KEEP_ON_DEVICE
+ * keeps its results in device memory (held, and charged to the device
+ * budget, until hp_release_event); hp_fetch_clusters refuses it (HP_EINVAL).
+ * Device consumers read it in place: hp_enqueue_hits, or
+ * hp_event_device_clusters, which fills *view with the device addresses
+ * (valid until release; safe to read after completion or in the product's
+ * stream order).  hp_enqueue_transfer is the transfer module: a consumer
+ * under the same stream rules as hp_enqueue_hits that copies to pinned host
+ * memory the per-event offsets and statuses and, as `what` asks, the
+ * clusters (only those that exist: a kernel reads their count on the device
+ * and writes them over the C2C link) and/or the labels (the product must
+ * have been enqueued with HP_WANT_LABELS).  The result is a new event read
+ * with hp_fetch_clusters; arrays not transferred are NULL in its view.
+ * Errors: HP_EINVAL (product not kept on the device, bad `what`, labels not
+ * computed), HP_ENOMEM, HP_ECUDA.
+ */
+hp_status hp_event_device_clusters(hp_event *ev, hp_device_clusters *view);
+hp_status hp_enqueue_transfer(hp_event *product, uint32_t what, hp_event **out);
 
 /*
  * Device-resident hits: reads the clusters that hp_reconstruct_device wrote

@@ -19,17 +19,26 @@ constexpr uint32_t kErrTimeout = 8u;
 constexpr int kChunk = 4096;         // digis per histogram / scatter block
 constexpr int kHistThreads = 512;
 constexpr int kHistCap = 4096;       // (event, module) bins a block can histogram in shared memory
-constexpr int kCCThreads = 512;      // threads of a clustering block (two blocks per SM)
-constexpr int kGroup = kCCThreads / 32; // (event, module) items per work-queue ticket, one per warp
+constexpr int kCCThreads = 512;      // threads of a clustering block
+constexpr int kGroup = kCCThreads / 32; // most (event, module) items per work-queue ticket, one per warp
 constexpr int kWarpMax = 64;         // items with at most this many digis are clustered by one warp
-constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory
+constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory (default tile)
+
+// Launch parameters of the clustering kernel, chosen per launch shape by the
+// autotuner (defaults: the values above, two resident blocks per SM).
+struct Tuning {
+    uint32_t tile_slots = kSmemSlots; // block-tier capacity in shared memory; larger items use global scratch
+    uint32_t blocks_per_sm = 2;       // 2 (up to 64 registers a thread) or 3 (up to 40, smaller tile)
+    uint32_t ticket_max = kGroup;     // items per ticket before halving for small launches (<= kGroup)
+    uint32_t warp_max = kWarpMax;     // 32 or 64: largest item of the warp tier
+};
 
 // Items per work-queue ticket of a launch of EM items on `grid` clustering
-// blocks: kGroup, halved (down to 4) while there would be fewer than two
+// blocks: `gmax`, halved (down to 4) while there would be fewer than two
 // tickets per block, so that large items of small launches spread over blocks.
-__host__ __device__ inline uint32_t ticket_items(uint64_t EM, unsigned grid)
+__host__ __device__ inline uint32_t ticket_items(uint64_t EM, unsigned grid, uint32_t gmax)
 {
-    uint32_t g = kGroup;
+    uint32_t g = gmax;
     while (g > 4 && (EM + g - 1) / g < 2ull * grid) g >>= 1;
     return g;
 }
@@ -72,7 +81,7 @@ struct Workspace {
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event
     StagedCluster *staging; // [N]
-    unsigned long long *exact; // [cc_grid * 2 * kSmemSlots] 64-bit moments of heavy clusters
+    unsigned long long *exact; // [cc_grid * 2 * tile_slots] 64-bit moments of heavy clusters
     unsigned char *big;   // scratch of items too large for shared memory
     uint64_t big_slots;   // slots per block (slab mode) or in total (arena mode)
     int big_arena;        // 1: bump-allocated arena, 0: one slab per block
@@ -88,18 +97,21 @@ struct Launch {
     Outputs out;
     Workspace ws;
     int cc_grid;             // blocks of the clustering kernel
+    Tuning tune;
 };
 
 // Bytes of one global-tier slot: (Q, npix), two 64-bit and two 32-bit moments,
 // parent, padded to 8-byte multiples so every slot range stays 8-byte aligned.
 constexpr size_t kBigSlotBytes = 8 + 16 + 8 + 4 + 4;
 
-size_t cc_smem_bytes(uint32_t R, uint32_t C);
+size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots);
 // Lay out the workspace for (E, M, N) in `base` (nullptr: only compute size).
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
-                       Workspace *ws);
-// Configure kernel attributes once per device; returns blocks per SM of the clustering kernel.
-cudaError_t init_kernels(int device, uint32_t R, uint32_t C, int *cc_blocks_per_sm);
+                       const Tuning &tune, Workspace *ws);
+// Configure kernel attributes once per device.  max_tile[b] receives the
+// largest tile (slots) with which b clustering blocks stay resident per SM
+// (0 if b blocks cannot be resident), for b = 2 and 3; max_tile[0..1] unused.
+cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4]);
 // Kernels of one launch, in order; marks[i] (if given) is recorded before
 // kernel i and marks[kNumKernels] after the last one.
 constexpr int kNumKernels = 5;
@@ -149,6 +161,13 @@ struct HitsLaunch {
 // Queue the hits kernel on `stream` (grid-stride; the cluster count is read
 // on the device, so nothing waits for the clusters to exist).
 cudaError_t launch_hits(const HitsLaunch &h, int max_blocks, cudaStream_t stream);
+
+// Transfer on demand: copy a product's outputs (`src`, device memory) to
+// `dst` (mapped pinned host memory): cluster offsets and event statuses
+// always, and, if `clusters`, the cluster arrays of the clusters that exist
+// (their count is read on the device, so only those bytes cross the link).
+cudaError_t launch_copy_out(const Outputs &src, const Outputs &dst, uint32_t E, bool clusters, int max_blocks,
+                            cudaStream_t stream);
 
 // Launch parameters of a context (implemented by the runtime): geometry with
 // device calibration pointers, device ordinal, clustering grid size, and

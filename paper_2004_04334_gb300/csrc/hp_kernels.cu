@@ -984,7 +984,8 @@ struct Pending {
     uint32_t b[kGroup];
 };
 
-__global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch L)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ BlockShared bs;
@@ -996,17 +997,18 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
     const uint32_t R = L.g.R, C = L.g.C, M = L.g.M;
     const uint32_t nwords = (R * C + 31) >> 5;
     const uint32_t tid = threadIdx.x;
+    const uint32_t T = L.tune.tile_slots, warp_max = L.tune.warp_max;
     Tile sm;
     sm.qn = reinterpret_cast<unsigned long long *>(dsm);
-    sm.m = reinterpret_cast<int2 *>(sm.qn + kSmemSlots);
-    sm.parent = reinterpret_cast<uint32_t *>(sm.m + kSmemSlots);
-    sm.exact = L.ws.exact + (size_t)blockIdx.x * 2 * kSmemSlots;
-    uint32_t *abits = sm.parent + kSmemSlots;
+    sm.m = reinterpret_cast<int2 *>(sm.qn + T);
+    sm.parent = reinterpret_cast<uint32_t *>(sm.m + T);
+    sm.exact = L.ws.exact + (size_t)blockIdx.x * 2 * T;
+    uint32_t *abits = sm.parent + T;
     uint32_t *sbits = abits + nwords;
     uint32_t *spre = sbits + nwords;
 
     const uint64_t EM = (uint64_t)L.E * M;
-    const uint32_t G = ticket_items(EM, gridDim.x);
+    const uint32_t G = ticket_items(EM, gridDim.x, L.tune.ticket_max);
     const uint64_t ngroups = (EM + G - 1) / G;
     const unsigned long long kAgg = 1ull << 62;
     if (tid == 0) {
@@ -1035,7 +1037,7 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
                 {   // warp tier: one warp per small item
                     const uint32_t wi = tid >> 5;
                     const uint32_t n = s_n[wi];
-                    if (n > 0 && n <= (uint32_t)kWarpMax) {
+                    if (n > 0 && n <= warp_max) {
                         const ItemCtx it = make_item(L, item0 + wi, s_b[wi], n);
                         const uint32_t K = n <= 32 ? warp_item<1>(L, it) : warp_item<2>(L, it);
                         if ((tid & 31) == 0) s_K[wi] = K;
@@ -1044,10 +1046,10 @@ __global__ void __launch_bounds__(kCCThreads, 2) cc_kernel(const Launch L)
                 __syncthreads();
                 for (int i = 0; i < kGroup; ++i) { // block tier: larger items one at a time
                     const uint32_t n = s_n[i];
-                    if (n <= (uint32_t)kWarpMax) continue;
+                    if (n <= warp_max) continue;
                     const ItemCtx it = make_item(L, item0 + i, s_b[i], n);
                     uint32_t K;
-                    if (n <= (uint32_t)kSmemSlots) {
+                    if (n <= T) {
                         K = block_item<false>(L, it, abits, sbits, spre, sm, bs);
                     } else {
                         if (tid == 0) {
@@ -1180,14 +1182,14 @@ cudaError_t launch_gather(const GatherEntry *table, uint32_t n_requests, uint64_
     return cudaGetLastError();
 }
 
-size_t cc_smem_bytes(uint32_t R, uint32_t C)
+size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots)
 {
     const size_t nwords = ((size_t)R * C + 31) / 32;
-    return (size_t)kSmemSlots * (8 + 8 + 4) + nwords * 4 * 3;
+    return (size_t)tile_slots * (8 + 8 + 4) + nwords * 4 * 3;
 }
 
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
-                       Workspace *ws)
+                       const Tuning &tune, Workspace *ws)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) -> unsigned char * {
@@ -1197,7 +1199,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
         return base ? static_cast<unsigned char *>(base) + o : nullptr;
     };
     const uint64_t EM = (uint64_t)E * M;
-    const uint32_t G = ticket_items(EM, (unsigned)(cc_grid > 0 ? cc_grid : 1));
+    const uint32_t G = ticket_items(EM, (unsigned)(cc_grid > 0 ? cc_grid : 1), tune.ticket_max);
     const uint64_t ngroups = (EM + G - 1) / G;
     Workspace w{};
     w.ctl = reinterpret_cast<uint32_t *>(take(64));
@@ -1211,7 +1213,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.staging = reinterpret_cast<StagedCluster *>(take(sizeof(StagedCluster) * N));
-    w.exact = reinterpret_cast<unsigned long long *>(take(16ull * kSmemSlots * (cc_grid > 0 ? cc_grid : 1)));
+    w.exact = reinterpret_cast<unsigned long long *>(take(16ull * tune.tile_slots * (cc_grid > 0 ? cc_grid : 1)));
     const uint64_t slab_slots = std::min<uint64_t>((uint64_t)R * C, N);
     const uint64_t slab_total = slab_slots * (uint64_t)(cc_grid > 0 ? cc_grid : 1);
     w.big_arena = N <= slab_total ? 1 : 0;
@@ -1222,20 +1224,40 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     return off;
 }
 
-cudaError_t init_kernels(int device, uint32_t R, uint32_t C, int *cc_blocks_per_sm)
+namespace {
+
+// Largest tile (a multiple of 256 slots, at most kSmemSlots) with which
+// `blocks` blocks of `kern` stay resident on one SM; 0 if none does.
+template <class K> cudaError_t fit_tile(K kern, int blocks, uint32_t R, uint32_t C, uint32_t *tile)
+{
+    *tile = 0;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)cc_smem_bytes(R, C, kSmemSlots));
+    if (err != cudaSuccess) return err;
+    for (uint32_t t = kSmemSlots; t >= 256; t -= 256) {
+        int nb = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kCCThreads, cc_smem_bytes(R, C, t));
+        if (err != cudaSuccess) return err;
+        if (nb >= blocks) {
+            *tile = t;
+            break;
+        }
+    }
+    return cudaSuccess;
+}
+
+} // namespace
+
+cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4])
 {
     cudaError_t err = cudaSetDevice(device);
     if (err != cudaSuccess) return err;
-    const size_t smem = cc_smem_bytes(R, C);
-    err = cudaFuncSetAttribute(cc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (err != cudaSuccess) return err;
-    int nb = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cc_kernel, kCCThreads, smem);
+    max_tile[0] = max_tile[1] = 0;
+    err = fit_tile(cc_kernel<2>, 2, R, C, &max_tile[2]);
     if (err != cudaSuccess) return err;
-    *cc_blocks_per_sm = nb > 0 ? nb : 1;
-    return cudaSuccess;
+    return fit_tile(cc_kernel<3>, 3, R, C, &max_tile[3]);
 }
 
 const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel", "scatter_kernel", "cc_kernel",
@@ -1264,7 +1286,11 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
         ++nk;
     }
     mark(3);
-    cc_kernel<<<L.cc_grid, kCCThreads, cc_smem_bytes(L.g.R, L.g.C), stream>>>(L);
+    const size_t cc_smem = cc_smem_bytes(L.g.R, L.g.C, L.tune.tile_slots);
+    if (L.tune.blocks_per_sm >= 3)
+        cc_kernel<3><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
+    else
+        cc_kernel<2><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
     ++nk;
     mark(4);
     finalize_kernel<<<(L.E + 255) / 256, 256, 0, stream>>>(L);

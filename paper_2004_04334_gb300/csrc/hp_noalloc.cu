@@ -65,7 +65,8 @@ extern "C" hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_event
     grid = (int)(groups < (uint64_t)grid ? groups : (uint64_t)grid);
     if (grid > kMaxGrid) grid = kMaxGrid;
     if (grid < 1) grid = 1;
-    if (hp::carve_workspace(nullptr, n_events, g.M, n_digis, g.R, g.C, grid, nullptr) > kScratchBytes)
+    const hp::Tuning tune; // the default tuning: the scratch limits are sized for it
+    if (hp::carve_workspace(nullptr, n_events, g.M, n_digis, g.R, g.C, grid, tune, nullptr) > kScratchBytes)
         return HP_ECAPACITY;
     if (cudaSetDevice(device) != cudaSuccess) return HP_ECUDA;
     void *base = nullptr;
@@ -90,8 +91,9 @@ extern "C" hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_event
     L.out.cluster_offsets = out->cluster_offsets;
     L.out.event_status = out->event_status;
     L.out.label = out->label;
-    hp::carve_workspace(base, n_events, g.M, n_digis, g.R, g.C, grid, &L.ws);
+    hp::carve_workspace(base, n_events, g.M, n_digis, g.R, g.C, grid, tune, &L.ws);
     L.cc_grid = grid;
+    L.tune = tune;
     uint64_t nk = 0;
     if (hp::launch_reconstruct(L, static_cast<cudaStream_t>(stream), &nk, nullptr) != cudaSuccess) {
         cudaGetLastError();

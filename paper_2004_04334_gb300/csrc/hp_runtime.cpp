@@ -16,12 +16,15 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
 #include <new>
 #include <set>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -184,8 +187,13 @@ struct hp_ctx {
     hp_config cfg{};
     int device = 0;
     int sm_count = 0;
-    int cc_per_sm = 1;
-    int cc_grid = 1;
+    uint32_t max_tile[4] = {0, 0, 0, 0}; // largest tile per resident-blocks count (init_kernels)
+    char device_name[256] = {0};
+    // autotuner (hp_autotune): tuning per launch-shape bucket, optional cache file
+    std::mutex tune_mu;
+    std::map<std::pair<int, int>, hp::Tuning> tuned;
+    int tune_mode = 1; // 0 off (defaults only), 1 use tuned buckets, 2 also search on first device call
+    std::string tune_cache;
     int32_t *d_gain = nullptr, *d_ped = nullptr;
     std::vector<cudaStream_t> streams;
     std::atomic<uint32_t> next_stream{0};
@@ -221,6 +229,16 @@ struct hp_ctx {
     std::vector<cudaStream_t> aux_streams;
     std::atomic<uint32_t> next_aux{0};
     std::atomic<uint64_t> consumer_reuses{0}, consumer_waits{0};
+    // captured device passes (hp_graph_capture), destroyed with the context
+    std::mutex graph_mu;
+    std::set<hp_graph *> graphs;
+};
+
+struct hp_graph {
+    hp_ctx *ctx = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *ws = nullptr;    // the graph's own scratch (its launches are serialised by CUDA)
+    uint64_t kernels = 0;  // kernels per launch
 };
 
 struct hp_event {
@@ -252,8 +270,17 @@ struct hp_event {
     uint64_t coff_local[2] = {0, 0};
     // Product<T> stream rule (Sec. 4.2): set by the first consumer, which takes this event's stream
     std::atomic<bool> stream_taken{false};
-    // hits events: the consumed clusters event (held until this one's work has run) and the outputs
+    // device-visible addresses of the outputs: aliases of the mapped host
+    // arrays, or device memory (dout) with HP_KEEP_ON_DEVICE; label is set
+    // only while the labels stay on the device
+    hp::Outputs dv{};
+    bool on_device = false;
+    Block dout;
+    size_t dout_charge = 0;
+    // consumers: hits events and transfer events hold the consumed clusters
+    // event until their own work has run
     bool hits = false;
+    bool transfer = false;
     hp_event *product = nullptr;
     uint32_t *h_hmodule = nullptr;
     float *h_hx = nullptr, *h_hy = nullptr, *h_hz = nullptr;
@@ -280,6 +307,10 @@ void destroy_event(hp_event *ev)
         if (ev->batch) release_batch_ref(ev->batch);
     } else {
         ctx->hpool.free(ev->host);
+        if (ev->dout.ptr) {
+            ctx->dpool.free(ev->dout);
+            ctx->dev_in_use.fetch_sub(ev->dout_charge);
+        }
         std::lock_guard<std::mutex> g(ctx->cev_mu);
         ctx->cev_free.push_back(ev->done);
     }
@@ -337,9 +368,10 @@ void CUDART_CB trampoline(void *p)
     complete_event(ev);
 }
 
-// Completion of a hits event: its status is that of the consumed product
-// (copied per event by the kernel); then the product loses this hold.
-void CUDART_CB hits_trampoline(void *p)
+// Completion of a consumer (hits or transfer) event: its status is that of
+// the consumed product (copied per event by its kernel); then the product
+// loses this hold.
+void CUDART_CB consumer_trampoline(void *p)
 {
     hp_event *ev = static_cast<hp_event *>(p);
     hp_status st = HP_OK;
@@ -402,11 +434,142 @@ hp::Geometry geometry(const hp_ctx *ctx)
     return g;
 }
 
-int cc_grid_for(const hp_ctx *ctx, uint32_t E)
+// Launch shape bucket of the autotuner: log2 of the (event, module) items
+// and log2 of the mean digis per item.
+std::pair<int, int> tune_bucket(const hp_ctx *ctx, uint32_t E, uint64_t N)
 {
+    const uint64_t EM = std::max<uint64_t>(1, (uint64_t)E * ctx->cfg.n_modules);
+    const uint64_t per = std::max<uint64_t>(1, N / EM);
+    return {63 - __builtin_clzll((unsigned long long)EM), 63 - __builtin_clzll((unsigned long long)per)};
+}
+
+// Launch parameters of the clustering kernel for a launch of E events and N
+// digis: the tuned entry of its bucket, else the defaults.
+struct Shape {
+    hp::Tuning tune;
+    int grid = 1;
+};
+
+Shape shape_with(const hp_ctx *ctx, uint32_t E, const hp::Tuning &t)
+{
+    Shape sh;
+    sh.tune = t;
     // enough blocks for tickets of the smallest size (see ticket_items)
     const uint64_t groups = ((uint64_t)E * ctx->cfg.n_modules + 3) / 4;
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>(groups, (uint64_t)ctx->cc_grid));
+    const uint64_t resident = (uint64_t)ctx->sm_count * t.blocks_per_sm;
+    sh.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(groups, resident));
+    return sh;
+}
+
+Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N)
+{
+    hp::Tuning t;
+    if (ctx->tune_mode != 0) {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        auto it = ctx->tuned.find(tune_bucket(ctx, E, N));
+        if (it != ctx->tuned.end()) t = it->second;
+    }
+    return shape_with(ctx, E, t);
+}
+
+bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t)
+{
+    if (t.blocks_per_sm != 2 && t.blocks_per_sm != 3) return false;
+    if (t.tile_slots < 256 || t.tile_slots > ctx->max_tile[t.blocks_per_sm] || t.tile_slots % 256) return false;
+    if (t.ticket_max != 4 && t.ticket_max != 8 && t.ticket_max != 16) return false;
+    return t.warp_max == 32 || t.warp_max == 64;
+}
+
+// The autotuner's search space on this device: the default tile at two
+// resident blocks per SM and the largest tile that keeps three resident,
+// each with tickets of 16, 8 or 4 items and a warp tier up to 64 or 32 digis.
+std::vector<hp::Tuning> tuning_candidates(const hp_ctx *ctx)
+{
+    std::vector<hp::Tuning> c;
+    for (uint32_t b = 2; b <= 3; ++b) {
+        const uint32_t tile = b == 2 ? (uint32_t)hp::kSmemSlots : ctx->max_tile[3];
+        if (tile < 256) continue;
+        for (uint32_t tk : {16u, 8u, 4u})
+            for (uint32_t wm : {64u, 32u}) {
+                hp::Tuning t;
+                t.tile_slots = tile;
+                t.blocks_per_sm = b;
+                t.ticket_max = tk;
+                t.warp_max = wm;
+                c.push_back(t);
+            }
+    }
+    return c;
+}
+
+// Value of "key": in a one-line JSON object (numbers only), or -1.
+double json_number(const std::string &line, const char *key)
+{
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t p = line.find(k);
+    if (p == std::string::npos) return -1;
+    return std::strtod(line.c_str() + p + k.size(), nullptr);
+}
+
+std::string json_string(const std::string &line, const char *key)
+{
+    const std::string k = std::string("\"") + key + "\": \"";
+    const size_t p = line.find(k);
+    if (p == std::string::npos) return "";
+    const size_t q = line.find('"', p + k.size());
+    return q == std::string::npos ? "" : line.substr(p + k.size(), q - p - k.size());
+}
+
+// HP_TUNE = off | cache (default) | search; HP_TUNE_CACHE = path of the
+// cache file (one JSON object per line, appended by hp_autotune).  Entries
+// for another device or module size are ignored.
+void load_tuning(hp_ctx *ctx)
+{
+    const char *mode = std::getenv("HP_TUNE");
+    if (mode && !std::strcmp(mode, "off")) ctx->tune_mode = 0;
+    if (mode && !std::strcmp(mode, "search")) ctx->tune_mode = 2;
+    const char *path = std::getenv("HP_TUNE_CACHE");
+    if (!path || !*path) return;
+    ctx->tune_cache = path;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char buf[1024];
+    while (std::fgets(buf, sizeof buf, f)) {
+        const std::string line(buf);
+        if (json_string(line, "device") != ctx->device_name) continue;
+        if (json_number(line, "rows") != ctx->cfg.rows || json_number(line, "cols") != ctx->cfg.cols) continue;
+        hp::Tuning t;
+        t.tile_slots = (uint32_t)json_number(line, "tile_slots");
+        t.blocks_per_sm = (uint32_t)json_number(line, "blocks_per_sm");
+        t.ticket_max = (uint32_t)json_number(line, "ticket_items");
+        t.warp_max = (uint32_t)json_number(line, "warp_max");
+        const int a = (int)json_number(line, "items_log2"), b = (int)json_number(line, "digis_per_item_log2");
+        if (a < 0 || b < 0 || !valid_tuning(ctx, t)) continue;
+        ctx->tuned[{a, b}] = t; // later lines win
+    }
+    std::fclose(f);
+}
+
+void save_tuning(hp_ctx *ctx, std::pair<int, int> bucket, const hp::Tuning &t, double ms)
+{
+    if (ctx->tune_cache.empty()) return;
+    FILE *f = std::fopen(ctx->tune_cache.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"device\": \"%s\", \"rows\": %u, \"cols\": %u, \"items_log2\": %d, "
+                 "\"digis_per_item_log2\": %d, \"tile_slots\": %u, \"blocks_per_sm\": %u, \"ticket_items\": %u, "
+                 "\"warp_max\": %u, \"ms\": %.4f}\n",
+                 ctx->device_name, ctx->cfg.rows, ctx->cfg.cols, bucket.first, bucket.second, t.tile_slots,
+                 t.blocks_per_sm, t.ticket_max, t.warp_max, ms);
+    std::fclose(f);
+}
+
+void to_public(const hp::Tuning &t, hp_tuning *o)
+{
+    o->tile_slots = t.tile_slots;
+    o->blocks_per_sm = t.blocks_per_sm;
+    o->ticket_items = t.ticket_max;
+    o->warp_max = t.warp_max;
 }
 
 bool device_pointer(const void *p)
@@ -460,11 +623,13 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     flags |= ctx->cfg.flags;
     const bool labels = (flags & HP_WANT_LABELS) != 0;
     const bool nocopy = (flags & HP_INPUT_NOCOPY) != 0;
+    const bool keep = (flags & HP_KEEP_ON_DEVICE) != 0;
 
     // device block: inputs, labels, workspace
-    const int grid = cc_grid_for(ctx, E);
+    const Shape sh = shape_for(ctx, E, N);
+    const int grid = sh.grid;
     const size_t ws_bytes = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols,
-                                                grid, nullptr);
+                                                grid, sh.tune, nullptr);
     size_t doff = 0;
     const size_t d_words = doff;
     doff = align_up(doff + 4 * N, 256);
@@ -476,7 +641,22 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     if (labels) doff = align_up(doff + 4 * N, 256);
     const size_t d_ws = doff;
     doff += ws_bytes;
-    const size_t dev_bytes = round_bin(doff);
+    // outputs kept in device memory (HP_KEEP_ON_DEVICE): their own block, held until release
+    size_t ooff = 0, o_arr[6], o_coff = 0, o_status = 0, o_label = 0;
+    if (keep) {
+        for (int i = 0; i < 6; ++i) {
+            o_arr[i] = ooff;
+            ooff = align_up(ooff + 4 * N, 256);
+        }
+        o_coff = ooff;
+        ooff = align_up(ooff + 8 * (size_t)(E + 1), 256);
+        o_status = ooff;
+        ooff = align_up(ooff + 4 * (size_t)E, 256);
+        o_label = ooff;
+        if (labels) ooff = align_up(ooff + 4 * N, 256);
+    }
+    const size_t out_bytes = keep ? round_bin(ooff) : 0;
+    const size_t dev_bytes = round_bin(doff) + out_bytes;
 
     // pinned host block: staged inputs, outputs
     size_t hoff = 0;
@@ -493,10 +673,10 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     size_t h_arr[6];
     for (int i = 0; i < 6; ++i) {
         h_arr[i] = hoff;
-        hoff = align_up(hoff + 4 * N, 256);
+        if (!keep) hoff = align_up(hoff + 4 * N, 256);
     }
     const size_t h_label = hoff;
-    if (labels) hoff = align_up(hoff + 4 * N, 256);
+    if (labels && !keep) hoff = align_up(hoff + 4 * N, 256);
 
     // admission: in-flight limit and device budget (non-blocking: HP_EAGAIN)
     const uint64_t maxin = ctx->cfg.max_inflight ? ctx->cfg.max_inflight : 256;
@@ -524,19 +704,27 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     ev->N = N;
     ev->flags = flags;
     ev->tag = tag;
-    ev->dev_charge = dev_bytes;
+    ev->dev_charge = dev_bytes - out_bytes;
+    ev->dout_charge = out_bytes;
     if (ctx->dpool.alloc(doff, &ev->dev) != HP_OK) {
+        delete ev;
+        return rollback(HP_ENOMEM);
+    }
+    if (keep && ctx->dpool.alloc(ooff, &ev->dout) != HP_OK) {
+        ctx->dpool.free(ev->dev);
         delete ev;
         return rollback(HP_ENOMEM);
     }
     if (ctx->hpool.alloc(hoff, &ev->host) != HP_OK) {
         ctx->dpool.free(ev->dev);
+        ctx->dpool.free(ev->dout);
         delete ev;
         return rollback(HP_ENOMEM);
     }
     ev->done = take_cuda_event(ctx);
     if (!ev->done) {
         ctx->dpool.free(ev->dev);
+        ctx->dpool.free(ev->dout);
         ctx->hpool.free(ev->host);
         delete ev;
         return rollback(fail(ctx));
@@ -565,13 +753,16 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     }
     ev->h_coff = reinterpret_cast<uint64_t *>(hb + h_coff);
     ev->h_status = reinterpret_cast<int32_t *>(hb + h_status);
-    ev->h_module = reinterpret_cast<uint32_t *>(hb + h_arr[0]);
-    ev->h_id = reinterpret_cast<int32_t *>(hb + h_arr[1]);
-    ev->h_charge = reinterpret_cast<int32_t *>(hb + h_arr[2]);
-    ev->h_npix = reinterpret_cast<int32_t *>(hb + h_arr[3]);
-    ev->h_x = reinterpret_cast<float *>(hb + h_arr[4]);
-    ev->h_y = reinterpret_cast<float *>(hb + h_arr[5]);
-    ev->h_label = labels ? reinterpret_cast<int32_t *>(hb + h_label) : nullptr;
+    if (!keep) {
+        ev->h_module = reinterpret_cast<uint32_t *>(hb + h_arr[0]);
+        ev->h_id = reinterpret_cast<int32_t *>(hb + h_arr[1]);
+        ev->h_charge = reinterpret_cast<int32_t *>(hb + h_arr[2]);
+        ev->h_npix = reinterpret_cast<int32_t *>(hb + h_arr[3]);
+        ev->h_x = reinterpret_cast<float *>(hb + h_arr[4]);
+        ev->h_y = reinterpret_cast<float *>(hb + h_arr[5]);
+        ev->h_label = labels ? reinterpret_cast<int32_t *>(hb + h_label) : nullptr;
+    }
+    ev->on_device = keep;
 
     hp::Launch L;
     L.g = geometry(ctx);
@@ -580,19 +771,24 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     L.offsets = reinterpret_cast<const uint64_t *>(db + d_offs);
     L.words = dev_input ? static_cast<const uint32_t *>(words) : reinterpret_cast<const uint32_t *>(db + d_words);
     L.modules = dev_input ? static_cast<const uint16_t *>(mods) : reinterpret_cast<const uint16_t *>(db + d_mods);
-    // cluster outputs go straight to mapped pinned host memory (written once by the kernel)
+    // cluster outputs go straight to mapped pinned host memory (written once
+    // by the kernel), or stay in device memory until a transfer asks for them
+    unsigned char *ob = keep ? static_cast<unsigned char *>(ev->dout.ptr) : hd;
     L.out.capacity = N;
-    L.out.module = reinterpret_cast<uint32_t *>(hd + h_arr[0]);
-    L.out.id = reinterpret_cast<int32_t *>(hd + h_arr[1]);
-    L.out.charge = reinterpret_cast<int32_t *>(hd + h_arr[2]);
-    L.out.npix = reinterpret_cast<int32_t *>(hd + h_arr[3]);
-    L.out.x = reinterpret_cast<float *>(hd + h_arr[4]);
-    L.out.y = reinterpret_cast<float *>(hd + h_arr[5]);
-    L.out.cluster_offsets = reinterpret_cast<uint64_t *>(hd + h_coff);
-    L.out.event_status = reinterpret_cast<int32_t *>(hd + h_status);
-    L.out.label = labels ? reinterpret_cast<int32_t *>(db + d_label) : nullptr;
-    hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, &L.ws);
+    L.out.module = reinterpret_cast<uint32_t *>(ob + (keep ? o_arr[0] : h_arr[0]));
+    L.out.id = reinterpret_cast<int32_t *>(ob + (keep ? o_arr[1] : h_arr[1]));
+    L.out.charge = reinterpret_cast<int32_t *>(ob + (keep ? o_arr[2] : h_arr[2]));
+    L.out.npix = reinterpret_cast<int32_t *>(ob + (keep ? o_arr[3] : h_arr[3]));
+    L.out.x = reinterpret_cast<float *>(ob + (keep ? o_arr[4] : h_arr[4]));
+    L.out.y = reinterpret_cast<float *>(ob + (keep ? o_arr[5] : h_arr[5]));
+    L.out.cluster_offsets = reinterpret_cast<uint64_t *>(ob + (keep ? o_coff : h_coff));
+    L.out.event_status = reinterpret_cast<int32_t *>(ob + (keep ? o_status : h_status));
+    L.out.label = labels ? reinterpret_cast<int32_t *>(keep ? ob + o_label : db + d_label) : nullptr;
+    ev->dv = L.out;
+    if (!keep) ev->dv.label = nullptr; // the device labels go back to the pool at completion
+    hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, sh.tune, &L.ws);
     L.cc_grid = grid;
+    L.tune = sh.tune;
 
     const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
     cudaStream_t s = ctx->streams[si];
@@ -611,9 +807,15 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     }
     uint64_t nk = 0;
     if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
-    if (err == cudaSuccess && labels && N) {
+    if (err == cudaSuccess && labels && N && !keep) {
         err = cudaMemcpyAsync(ev->h_label, db + d_label, 4 * N, cudaMemcpyDeviceToHost, s);
         ctx->d2h.fetch_add(4 * N);
+    }
+    if (err == cudaSuccess && keep) { // per-event status and offsets only: the completion needs them
+        err = cudaMemcpyAsync(ev->h_coff, L.out.cluster_offsets, 8 * (size_t)(E + 1), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(ev->h_status, L.out.event_status, 4 * (size_t)E, cudaMemcpyDeviceToHost, s);
+        ctx->d2h.fetch_add(8ull * (E + 1) + 4ull * E);
     }
     if (err == cudaSuccess) err = cudaEventRecord(ev->done, s);
     if (err == cudaSuccess) err = cudaLaunchHostFunc(s, trampoline, ev);
@@ -728,15 +930,15 @@ void CUDART_CB batch_done(void *p)
 struct BatchLayout {
     size_t d_words, d_mods, d_offs, d_label, d_ws, dev_bytes;
     size_t h_offs, h_coff, h_status, h_arr[6], h_label, h_table, host_bytes;
-    int grid;
+    Shape sh;
 };
 
-BatchLayout batch_layout(const hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
+BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
 {
     BatchLayout l;
-    l.grid = cc_grid_for(ctx, E);
-    const size_t ws = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.grid,
-                                          nullptr);
+    l.sh = shape_for(ctx, E, N);
+    const size_t ws = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols,
+                                          l.sh.grid, l.sh.tune, nullptr);
     size_t d = 0;
     l.d_words = d;
     d = align_up(d + 4 * N, 256);
@@ -848,8 +1050,10 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     L.out.cluster_offsets = reinterpret_cast<uint64_t *>(hd + l.h_coff);
     L.out.event_status = reinterpret_cast<int32_t *>(hd + l.h_status);
     L.out.label = labels ? reinterpret_cast<int32_t *>(db + l.d_label) : nullptr;
-    hp::carve_workspace(db + l.d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.grid, &L.ws);
-    L.cc_grid = l.grid;
+    hp::carve_workspace(db + l.d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.sh.grid, l.sh.tune,
+                        &L.ws);
+    L.cc_grid = l.sh.grid;
+    L.tune = l.sh.tune;
 
     const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
     cudaStream_t s = ctx->streams[si];
@@ -967,6 +1171,55 @@ cudaStream_t consumer_stream(hp_ctx *ctx)
     return ctx->aux_streams[ctx->next_aux.fetch_add(1) % ctx->aux_streams.size()];
 }
 
+// ScopedContext (Sec. 4.2) for consumer `ev` of product `prod`: the first
+// consumer takes the product's stream; a later one takes another stream and,
+// unless the product's CUDA event has completed, must queue a wait on it
+// (*wait).  On success the consumer holds the product and is live; on
+// failure `ev` and its buffers are freed.
+hp_status scope_consumer(hp_ctx *ctx, hp_event *prod, hp_event *ev, bool *wait)
+{
+    cudaStream_t s = prod->stream;
+    *wait = false;
+    hp_status st = HP_OK;
+    if (prod->stream_taken.exchange(true)) {
+        s = consumer_stream(ctx);
+        if (!s) {
+            st = fail(ctx);
+        } else {
+            const cudaError_t q = cudaEventQuery(prod->done);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();
+                *wait = true;
+            } else if (q != cudaSuccess) {
+                cudaGetLastError();
+                st = fail(ctx);
+            }
+        }
+    }
+    if (st != HP_OK) {
+        ctx->hpool.free(ev->host);
+        {
+            std::lock_guard<std::mutex> g(ctx->cev_mu);
+            ctx->cev_free.push_back(ev->done);
+        }
+        delete ev;
+        return st;
+    }
+    ev->stream = s;
+    ev->product = prod;
+    prod->state.fetch_add(kHold, std::memory_order_acq_rel); // the product outlives this consumer's work
+    ev->t_enq = now_ns();
+    {
+        std::lock_guard<std::mutex> g(ctx->live_mu);
+        ctx->live.insert(ev);
+    }
+    if (*wait)
+        ctx->consumer_waits.fetch_add(1);
+    else if (s == prod->stream)
+        ctx->consumer_reuses.fetch_add(1);
+    return HP_OK;
+}
+
 // Device alias of a pointer into an event's mapped pinned host block.
 template <class T> T *device_alias(const Block &b, T *host)
 {
@@ -976,12 +1229,70 @@ template <class T> T *device_alias(const Block &b, T *host)
 
 } // namespace
 
+namespace {
+
+hp_status check_device_args(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                            const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out)
+{
+    if (!ctx || !out || !d_offsets || n_events < 1) return HP_EINVAL;
+    if (ctx->failed.load()) return HP_ECUDA;
+    if (n_digis >= 0xFFFFFFFFull) return HP_EINVAL;
+    if (n_digis > 0 && (!d_words || !d_module_ids)) return HP_EINVAL;
+    if (((uintptr_t)d_words & 3) || ((uintptr_t)d_module_ids & 1) || ((uintptr_t)d_offsets & 7)) return HP_EINVAL;
+    if (!out->module || !out->id || !out->charge || !out->npix || !out->x || !out->y || !out->cluster_offsets ||
+        !out->event_status)
+        return HP_EINVAL;
+    const uint64_t EM = (uint64_t)n_events * ctx->cfg.n_modules;
+    if (EM > (1ull << 31)) return HP_EINVAL;
+    return HP_OK;
+}
+
+// Queue one device-resident pass with its scratch at `base`.
+cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                        const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
+                        const Shape &sh, void *base, cudaStream_t s, uint64_t *nk, cudaEvent_t *marks)
+{
+    hp::Launch L;
+    L.g = geometry(ctx);
+    L.E = n_events;
+    L.N = n_digis;
+    L.offsets = d_offsets;
+    L.words = d_words;
+    L.modules = d_module_ids;
+    L.out.capacity = out->capacity;
+    L.out.module = out->module;
+    L.out.id = out->id;
+    L.out.charge = out->charge;
+    L.out.npix = out->npix;
+    L.out.x = out->x;
+    L.out.y = out->y;
+    L.out.cluster_offsets = out->cluster_offsets;
+    L.out.event_status = out->event_status;
+    L.out.label = out->label;
+    hp::carve_workspace(base, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows, ctx->cfg.cols, sh.grid, sh.tune,
+                        &L.ws);
+    L.cc_grid = sh.grid;
+    L.tune = sh.tune;
+    return hp::launch_reconstruct(L, s, nk, marks);
+}
+
+void destroy_graph(hp_graph *g)
+{
+    cudaSetDevice(g->ctx->device);
+    cudaGraphExecDestroy(g->exec);
+    cudaFree(g->ws); // synchronises the device: no launch of the graph is left running
+    cudaGetLastError();
+    delete g;
+}
+
+} // namespace
+
 bool hp::context_launch_params(hp_ctx *ctx, hp::Geometry *g, int *device, int *cc_grid)
 {
     if (!ctx || ctx->failed.load()) return false;
     *g = geometry(ctx);
     *device = ctx->device;
-    *cc_grid = ctx->cc_grid;
+    *cc_grid = ctx->sm_count * (int)hp::Tuning().blocks_per_sm;
     return true;
 }
 
@@ -1026,8 +1337,14 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
     if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(HP_ECUDA);
     if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
         return bail(HP_ECUDA);
-    if (hp::init_kernels(cfg->device, cfg->rows, cfg->cols, &ctx->cc_per_sm) != cudaSuccess) return bail(HP_ECUDA);
-    ctx->cc_grid = ctx->sm_count * ctx->cc_per_sm;
+    if (hp::init_kernels(cfg->device, cfg->rows, cfg->cols, ctx->max_tile) != cudaSuccess) return bail(HP_ECUDA);
+    if (ctx->max_tile[2] < (uint32_t)hp::kSmemSlots) return bail(HP_EINVAL); // the default tile must fit
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, cfg->device) == cudaSuccess)
+            std::snprintf(ctx->device_name, sizeof ctx->device_name, "%s", prop.name);
+    }
+    load_tuning(ctx);
     const size_t M = cfg->n_modules;
     if (cudaMalloc(&ctx->d_gain, 8 * M) != cudaSuccess) return bail(HP_ENOMEM);
     ctx->d_ped = ctx->d_gain + M;
@@ -1049,6 +1366,8 @@ hp_status hp_destroy(hp_ctx *ctx)
     if (!ctx) return HP_EINVAL;
     serve_stop(ctx); // drains a running serving loop (no-op otherwise)
     cudaSetDevice(ctx->device);
+    for (hp_graph *g : ctx->graphs) destroy_graph(g);
+    ctx->graphs.clear();
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
     for (cudaStream_t s : ctx->aux_streams) cudaStreamSynchronize(s);
     {
@@ -1118,7 +1437,7 @@ hp_status hp_event_query(hp_event *ev)
 
 hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *v)
 {
-    if (!ev || !v || ev->hits) return HP_EINVAL;
+    if (!ev || !v || ev->hits || ev->on_device) return HP_EINVAL;
     if (!(ev->state.load(std::memory_order_acquire) & kDone)) return HP_ENOTREADY;
     v->n_events = ev->E;
     v->n_digis = ev->N;
@@ -1196,7 +1515,7 @@ hp_status hp_set_geometry(hp_ctx *ctx, const float *origin, const float *rot, fl
 hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
 {
     if (!prod || !out || flags != 0) return HP_EINVAL;
-    if (prod->request || prod->hits) return HP_EINVAL;
+    if (prod->request || prod->hits || prod->transfer) return HP_EINVAL;
     hp_ctx *ctx = prod->ctx;
     if (ctx->failed.load()) return HP_ECUDA;
     hp::Placement place;
@@ -1240,48 +1559,19 @@ hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
     ev->h_hy = reinterpret_cast<float *>(hb + h_arr[2]);
     ev->h_hz = reinterpret_cast<float *>(hb + h_arr[3]);
 
-    // ScopedContext (Sec. 4.2): the first consumer takes the product's stream;
-    // a later one takes another stream and waits on the product's CUDA event
-    // unless that event has already completed.
-    cudaStream_t s = prod->stream;
     bool wait = false;
-    if (prod->stream_taken.exchange(true)) {
-        s = consumer_stream(ctx);
-        if (!s) {
-            ctx->hpool.free(ev->host);
-            {
-                std::lock_guard<std::mutex> g(ctx->cev_mu);
-                ctx->cev_free.push_back(ev->done);
-            }
-            delete ev;
-            return fail(ctx);
-        }
-        const cudaError_t q = cudaEventQuery(prod->done);
-        if (q == cudaErrorNotReady) {
-            cudaGetLastError();
-            wait = true;
-        } else if (q != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx);
-        }
-    }
-    ev->stream = s;
-    ev->product = prod;
-    prod->state.fetch_add(kHold, std::memory_order_acq_rel); // the product outlives this consumer's work
-    ev->t_enq = now_ns();
-    {
-        std::lock_guard<std::mutex> g(ctx->live_mu);
-        ctx->live.insert(ev);
-    }
+    const hp_status sst = scope_consumer(ctx, prod, ev, &wait);
+    if (sst != HP_OK) return sst;
+    cudaStream_t s = ev->stream;
     hp::HitsLaunch h;
     h.p = place;
     h.E = E;
     h.capacity = N;
-    h.cluster_offsets = device_alias(prod->host, prod->h_coff);
-    h.event_status = device_alias(prod->host, prod->h_status);
-    h.module = device_alias(prod->host, prod->h_module);
-    h.x = device_alias(prod->host, prod->h_x);
-    h.y = device_alias(prod->host, prod->h_y);
+    h.cluster_offsets = prod->dv.cluster_offsets;
+    h.event_status = prod->dv.event_status;
+    h.module = prod->dv.module;
+    h.x = prod->dv.x;
+    h.y = prod->dv.y;
     h.hit_offsets = device_alias(ev->host, ev->h_coff);
     h.hit_status = device_alias(ev->host, ev->h_status);
     h.hit_module = device_alias(ev->host, ev->h_hmodule);
@@ -1290,17 +1580,13 @@ hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
     h.hz = device_alias(ev->host, ev->h_hz);
     cudaError_t err = cudaSuccess;
     if (wait) err = cudaStreamWaitEvent(s, prod->done, 0);
-    if (err == cudaSuccess) err = hp::launch_hits(h, 4 * ctx->sm_count, s);
+    if (err == cudaSuccess) err = hp::launch_hits(h, 8 * ctx->sm_count, s);
     if (err == cudaSuccess) err = cudaEventRecord(ev->done, s);
-    if (err == cudaSuccess) err = cudaLaunchHostFunc(s, hits_trampoline, ev);
+    if (err == cudaSuccess) err = cudaLaunchHostFunc(s, consumer_trampoline, ev);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx); // the context is unusable; its memory is reclaimed by hp_destroy
     }
-    if (wait)
-        ctx->consumer_waits.fetch_add(1);
-    else if (s == prod->stream)
-        ctx->consumer_reuses.fetch_add(1);
     ctx->kernels.fetch_add(1);
     *out = ev;
     return HP_OK;
@@ -1321,6 +1607,109 @@ hp_status hp_fetch_hits(hp_event *ev, hp_hits *v)
     v->y = ev->h_hy;
     v->z = ev->h_hz;
     return ev->status;
+}
+
+hp_status hp_event_device_clusters(hp_event *ev, hp_device_clusters *v)
+{
+    if (!ev || !v || !ev->on_device) return HP_EINVAL;
+    v->capacity = ev->dv.capacity;
+    v->module = ev->dv.module;
+    v->id = ev->dv.id;
+    v->charge = ev->dv.charge;
+    v->npix = ev->dv.npix;
+    v->x = ev->dv.x;
+    v->y = ev->dv.y;
+    v->cluster_offsets = ev->dv.cluster_offsets;
+    v->event_status = ev->dv.event_status;
+    v->label = ev->dv.label;
+    return HP_OK;
+}
+
+hp_status hp_enqueue_transfer(hp_event *prod, uint32_t what, hp_event **out)
+{
+    if (!prod || !out) return HP_EINVAL;
+    if (!prod->on_device || prod->hits || prod->transfer || prod->request) return HP_EINVAL;
+    if (what == 0 || (what & ~(uint32_t)(HP_TRANSFER_CLUSTERS | HP_TRANSFER_LABELS))) return HP_EINVAL;
+    const bool clusters = (what & HP_TRANSFER_CLUSTERS) != 0, labels = (what & HP_TRANSFER_LABELS) != 0;
+    if (labels && !prod->dv.label) return HP_EINVAL;
+    hp_ctx *ctx = prod->ctx;
+    if (ctx->failed.load()) return HP_ECUDA;
+    const uint32_t E = prod->E;
+    const uint64_t N = prod->N;
+    size_t hoff = 0;
+    const size_t h_coff = hoff;
+    hoff = align_up(hoff + 8 * (size_t)(E + 1), 256);
+    const size_t h_status = hoff;
+    hoff = align_up(hoff + 4 * (size_t)E, 256);
+    size_t h_arr[6];
+    for (int i = 0; i < 6; ++i) {
+        h_arr[i] = hoff;
+        if (clusters) hoff = align_up(hoff + 4 * N, 256);
+    }
+    const size_t h_label = hoff;
+    if (labels) hoff = align_up(hoff + 4 * N, 256);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx); // the product's device (Sec. 4.2)
+    hp_event *ev = new (std::nothrow) hp_event();
+    if (!ev) return HP_ENOMEM;
+    ev->ctx = ctx;
+    ev->E = E;
+    ev->N = N;
+    ev->tag = prod->tag;
+    ev->transfer = true;
+    if (ctx->hpool.alloc(hoff, &ev->host) != HP_OK) {
+        delete ev;
+        return HP_ENOMEM;
+    }
+    ev->done = take_cuda_event(ctx);
+    if (!ev->done) {
+        ctx->hpool.free(ev->host);
+        delete ev;
+        return fail(ctx);
+    }
+    unsigned char *hb = static_cast<unsigned char *>(ev->host.ptr);
+    ev->h_coff = reinterpret_cast<uint64_t *>(hb + h_coff);
+    ev->h_status = reinterpret_cast<int32_t *>(hb + h_status);
+    if (clusters) {
+        ev->h_module = reinterpret_cast<uint32_t *>(hb + h_arr[0]);
+        ev->h_id = reinterpret_cast<int32_t *>(hb + h_arr[1]);
+        ev->h_charge = reinterpret_cast<int32_t *>(hb + h_arr[2]);
+        ev->h_npix = reinterpret_cast<int32_t *>(hb + h_arr[3]);
+        ev->h_x = reinterpret_cast<float *>(hb + h_arr[4]);
+        ev->h_y = reinterpret_cast<float *>(hb + h_arr[5]);
+    }
+    ev->h_label = labels ? reinterpret_cast<int32_t *>(hb + h_label) : nullptr;
+    bool wait = false;
+    const hp_status sst = scope_consumer(ctx, prod, ev, &wait);
+    if (sst != HP_OK) return sst;
+    cudaStream_t s = ev->stream;
+    hp::Outputs dst{};
+    dst.capacity = N;
+    dst.cluster_offsets = device_alias(ev->host, ev->h_coff);
+    dst.event_status = device_alias(ev->host, ev->h_status);
+    if (clusters) {
+        dst.module = device_alias(ev->host, ev->h_module);
+        dst.id = device_alias(ev->host, ev->h_id);
+        dst.charge = device_alias(ev->host, ev->h_charge);
+        dst.npix = device_alias(ev->host, ev->h_npix);
+        dst.x = device_alias(ev->host, ev->h_x);
+        dst.y = device_alias(ev->host, ev->h_y);
+    }
+    cudaError_t err = cudaSuccess;
+    if (wait) err = cudaStreamWaitEvent(s, prod->done, 0);
+    if (err == cudaSuccess) err = hp::launch_copy_out(prod->dv, dst, E, clusters, 8 * ctx->sm_count, s);
+    if (err == cudaSuccess && labels && N) {
+        err = cudaMemcpyAsync(ev->h_label, prod->dv.label, 4 * N, cudaMemcpyDeviceToHost, s);
+        ctx->d2h.fetch_add(4 * N);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev->done, s);
+    if (err == cudaSuccess) err = cudaLaunchHostFunc(s, consumer_trampoline, ev);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx); // the context is unusable; its memory is reclaimed by hp_destroy
+    }
+    ctx->kernels.fetch_add(1);
+    *out = ev;
+    return HP_OK;
 }
 
 hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, const uint64_t *d_cluster_offsets,
@@ -1348,7 +1737,7 @@ hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, cons
     h.hx = d_hx;
     h.hy = d_hy;
     h.hz = d_hz;
-    if (hp::launch_hits(h, 4 * ctx->sm_count, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    if (hp::launch_hits(h, 8 * ctx->sm_count, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx);
     }
@@ -1360,21 +1749,26 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
                                 const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
                                 void *stream)
 {
-    if (!ctx || !out || !d_offsets || n_events < 1) return HP_EINVAL;
-    if (ctx->failed.load()) return HP_ECUDA;
-    if (n_digis >= 0xFFFFFFFFull) return HP_EINVAL;
-    if (n_digis > 0 && (!d_words || !d_module_ids)) return HP_EINVAL;
-    if (((uintptr_t)d_words & 3) || ((uintptr_t)d_module_ids & 1) || ((uintptr_t)d_offsets & 7)) return HP_EINVAL;
-    if (!out->module || !out->id || !out->charge || !out->npix || !out->x || !out->y || !out->cluster_offsets ||
-        !out->event_status)
-        return HP_EINVAL;
-    const uint64_t EM = (uint64_t)n_events * ctx->cfg.n_modules;
-    if (EM > (1ull << 31)) return HP_EINVAL;
+    hp_status st = check_device_args(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out);
+    if (st != HP_OK) return st;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int grid = cc_grid_for(ctx, n_events);
+    if (ctx->tune_mode == 2) {
+        bool known;
+        {
+            std::lock_guard<std::mutex> g(ctx->tune_mu);
+            known = ctx->tuned.count(tune_bucket(ctx, n_events, n_digis)) != 0;
+        }
+        if (!known) { // search mode: tune this bucket once, on this call's inputs (blocking)
+            hp_tuning best;
+            st = hp_autotune(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, 3, 0, nullptr, &best,
+                             nullptr);
+            if (st != HP_OK) return st;
+        }
+    }
+    const Shape sh = shape_for(ctx, n_events, n_digis);
     const size_t need = hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
-                                            ctx->cfg.cols, grid, nullptr);
+                                            ctx->cfg.cols, sh.grid, sh.tune, nullptr);
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> g(ctx->ws_mu);
@@ -1396,32 +1790,192 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
         }
         base = b.ptr;
     }
-    hp::Launch L;
-    L.g = geometry(ctx);
-    L.E = n_events;
-    L.N = n_digis;
-    L.offsets = d_offsets;
-    L.words = d_words;
-    L.modules = d_module_ids;
-    L.out.capacity = out->capacity;
-    L.out.module = out->module;
-    L.out.id = out->id;
-    L.out.charge = out->charge;
-    L.out.npix = out->npix;
-    L.out.x = out->x;
-    L.out.y = out->y;
-    L.out.cluster_offsets = out->cluster_offsets;
-    L.out.event_status = out->event_status;
-    L.out.label = out->label;
-    hp::carve_workspace(base, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows, ctx->cfg.cols, grid, &L.ws);
-    L.cc_grid = grid;
     uint64_t nk = 0;
-    cudaError_t err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
-    if (err != cudaSuccess) {
+    if (device_pass(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, sh, base, s, &nk,
+                    profile_marks(ctx)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx);
     }
     ctx->kernels.fetch_add(nk);
+    return HP_OK;
+}
+
+hp_status hp_tuning_candidates(hp_ctx *ctx, uint32_t cap, hp_tuning *list, uint32_t *n)
+{
+    if (!ctx || !n || (cap && !list)) return HP_EINVAL;
+    const std::vector<hp::Tuning> c = tuning_candidates(ctx);
+    *n = (uint32_t)c.size();
+    for (uint32_t i = 0; i < c.size() && i < cap; ++i) to_public(c[i], &list[i]);
+    return HP_OK;
+}
+
+hp_status hp_get_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, hp_tuning *out)
+{
+    if (!ctx || !out || n_events < 1) return HP_EINVAL;
+    to_public(shape_for(ctx, n_events, n_digis).tune, out);
+    return HP_OK;
+}
+
+hp_status hp_set_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const hp_tuning *t)
+{
+    if (!ctx || n_events < 1) return HP_EINVAL;
+    const auto bucket = tune_bucket(ctx, n_events, n_digis);
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    if (!t) {
+        ctx->tuned.erase(bucket);
+        return HP_OK;
+    }
+    hp::Tuning x;
+    x.tile_slots = t->tile_slots;
+    x.blocks_per_sm = t->blocks_per_sm;
+    x.ticket_max = t->ticket_items;
+    x.warp_max = t->warp_max;
+    if (!valid_tuning(ctx, x)) return HP_EINVAL;
+    ctx->tuned[bucket] = x;
+    return HP_OK;
+}
+
+hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                      const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
+                      uint32_t reps, uint32_t cap, double *cand_ms, hp_tuning *best, double *best_ms)
+{
+    hp_status st = check_device_args(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out);
+    if (st != HP_OK) return st;
+    if (reps < 1) reps = 1;
+    const std::vector<hp::Tuning> cands = tuning_candidates(ctx);
+    if (cands.empty()) return HP_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
+    size_t need = 0;
+    for (const hp::Tuning &t : cands) {
+        const Shape sh = shape_with(ctx, n_events, t);
+        need = std::max(need, hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
+                                                  ctx->cfg.cols, sh.grid, sh.tune, nullptr));
+    }
+    void *ws = nullptr;
+    if (cudaMalloc(&ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return HP_ENOMEM;
+    }
+    ctx->ws_mallocs.fetch_add(1);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto done = [&](hp_status r) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+        cudaFree(ws);
+        cudaGetLastError();
+        return r;
+    };
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        return done(fail(ctx));
+    double best_t = 1e300;
+    size_t bi = 0;
+    uint64_t nk = 0;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const Shape sh = shape_with(ctx, n_events, cands[i]);
+        cudaError_t err = device_pass(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, sh, ws, s, &nk,
+                                      nullptr); // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+        for (uint32_t r = 0; r < reps && err == cudaSuccess; ++r)
+            err = device_pass(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, sh, ws, s, &nk, nullptr);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) return done(fail(ctx));
+        const double per = (double)ms / reps;
+        if (cand_ms && i < cap) cand_ms[i] = per;
+        if (per < best_t) {
+            best_t = per;
+            bi = i;
+        }
+    }
+    ctx->kernels.fetch_add(nk);
+    const auto bucket = tune_bucket(ctx, n_events, n_digis);
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        ctx->tuned[bucket] = cands[bi];
+    }
+    save_tuning(ctx, bucket, cands[bi], best_t);
+    if (best) to_public(cands[bi], best);
+    if (best_ms) *best_ms = best_t;
+    return done(HP_OK);
+}
+
+hp_status hp_graph_capture(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                           const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
+                           hp_graph **graph)
+{
+    if (!graph) return HP_EINVAL;
+    *graph = nullptr;
+    hp_status st = check_device_args(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out);
+    if (st != HP_OK) return st;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
+    hp_graph *g = new (std::nothrow) hp_graph();
+    if (!g) return HP_ENOMEM;
+    g->ctx = ctx;
+    const Shape sh = shape_for(ctx, n_events, n_digis);
+    const size_t need = hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
+                                            ctx->cfg.cols, sh.grid, sh.tune, nullptr);
+    if (cudaMalloc(&g->ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return HP_ENOMEM;
+    }
+    ctx->ws_mallocs.fetch_add(1);
+    cudaStream_t s = nullptr;
+    cudaGraph_t cg = nullptr;
+    auto bail = [&](hp_status r) {
+        cudaGetLastError();
+        if (cg) cudaGraphDestroy(cg);
+        if (s) cudaStreamDestroy(s);
+        cudaFree(g->ws);
+        delete g;
+        cudaGetLastError();
+        return r;
+    };
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(ctx));
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return bail(fail(ctx));
+    const cudaError_t le = device_pass(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, sh, g->ws, s,
+                                       &g->kernels, nullptr);
+    const cudaError_t ce = cudaStreamEndCapture(s, &cg);
+    if (le != cudaSuccess || ce != cudaSuccess || !cg) return bail(fail(ctx));
+    if (cudaGraphInstantiate(&g->exec, cg, 0) != cudaSuccess) return bail(fail(ctx));
+    cudaGraphDestroy(cg);
+    cudaStreamDestroy(s);
+    {
+        std::lock_guard<std::mutex> l(ctx->graph_mu);
+        ctx->graphs.insert(g);
+    }
+    *graph = g;
+    return HP_OK;
+}
+
+hp_status hp_graph_launch(hp_graph *g, void *stream)
+{
+    if (!g) return HP_EINVAL;
+    hp_ctx *ctx = g->ctx;
+    if (ctx->failed.load()) return HP_ECUDA;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
+    if (cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx);
+    }
+    ctx->kernels.fetch_add(g->kernels);
+    return HP_OK;
+}
+
+hp_status hp_graph_destroy(hp_graph *g)
+{
+    if (!g) return HP_EINVAL;
+    hp_ctx *ctx = g->ctx;
+    {
+        std::lock_guard<std::mutex> l(ctx->graph_mu);
+        ctx->graphs.erase(g);
+    }
+    destroy_graph(g);
     return HP_OK;
 }
 

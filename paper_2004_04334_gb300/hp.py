@@ -21,6 +21,9 @@ HP_OK, HP_EAGAIN, HP_ENOTREADY, HP_EINVAL, HP_EBADDIGI, HP_EDUP, HP_ECAPACITY, H
     range(10)
 HP_WANT_LABELS = 0x1
 HP_INPUT_NOCOPY = 0x2
+HP_KEEP_ON_DEVICE = 0x4
+HP_TRANSFER_CLUSTERS = 0x1
+HP_TRANSFER_LABELS = 0x2
 
 # Every function that include/hp.h declares.
 EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "hp_enqueue_batch", "hp_on_complete",
@@ -29,7 +32,8 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_get_stats",
            "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations", "hp_serve_start", "hp_submit",
            "hp_serve_stop", "hp_serve_replay", "hp_set_geometry", "hp_enqueue_hits", "hp_fetch_hits",
-           "hp_hits_device")
+           "hp_hits_device", "hp_graph_capture", "hp_graph_launch", "hp_graph_destroy", "hp_tuning_candidates",
+           "hp_get_tuning", "hp_set_tuning", "hp_autotune", "hp_event_device_clusters", "hp_enqueue_transfer")
 
 
 class HPError(RuntimeError):
@@ -65,6 +69,14 @@ class Stats(ctypes.Structure):
         "device_mallocs", "host_mallocs", "pool_hits", "device_bytes_in_use", "device_bytes_cached",
         "events_enqueued", "events_completed", "inflight", "h2d_bytes", "d2h_bytes", "kernel_launches",
         "serve_batches", "serve_requests", "consumer_stream_reuses", "consumer_stream_waits")]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_slots", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("ticket_items", ctypes.c_uint32),
+                ("warp_max", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 class HitsView(ctypes.Structure):
@@ -123,6 +135,16 @@ def load(path: str = LIB_PATH):
             "hp_enqueue_hits": (I, [V, U32, P(V)]),
             "hp_fetch_hits": (I, [V, P(HitsView)]),
             "hp_hits_device": (I, [V, U32, U64, V, V, V, V, V, V, V, V]),
+            "hp_graph_capture": (I, [V, U32, U64, V, V, V, P(DeviceClusters), P(V)]),
+            "hp_graph_launch": (I, [V, V]),
+            "hp_graph_destroy": (I, [V]),
+            "hp_tuning_candidates": (I, [V, U32, P(Tuning), P(U32)]),
+            "hp_event_device_clusters": (I, [V, P(DeviceClusters)]),
+            "hp_enqueue_transfer": (I, [V, U32, P(V)]),
+            "hp_get_tuning": (I, [V, U32, U64, P(Tuning)]),
+            "hp_set_tuning": (I, [V, U32, U64, P(Tuning)]),
+            "hp_autotune": (I, [V, U32, U64, V, V, V, P(DeviceClusters), U32, U32, P(ctypes.c_double), P(Tuning),
+                                P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -269,12 +291,26 @@ class Event:
         st = self._ctx._lib.hp_fetch_clusters(self._h, ctypes.byref(v))
         if st == HP_ENOTREADY:
             raise HPError(st, "hp_fetch_clusters")
+        if st == HP_EINVAL:
+            raise HPError(st, "hp_fetch_clusters")
         E, N, C = v.n_events, v.n_digis, v.n_clusters
         a = lambda p, n, t: _arr(p, n, t, copy)  # noqa: E731
         return Result(st, E, a(v.cluster_offsets, E + 1, np.uint64), a(v.event_status, E, np.int32),
                       a(v.module, C, np.uint32), a(v.id, C, np.int32), a(v.charge, C, np.int32),
                       a(v.npix, C, np.int32), a(v.x, C, np.float32), a(v.y, C, np.float32),
                       a(v.label, N, np.int32) if v.label else None, int(v.tag))
+
+    def transfer(self, what: int = HP_TRANSFER_CLUSTERS) -> "Event":
+        """Queue the transfer module of a HP_KEEP_ON_DEVICE event (hp_enqueue_transfer)."""
+        h = ctypes.c_void_p()
+        _check(self._ctx._lib.hp_enqueue_transfer(self._h, what, ctypes.byref(h)), "hp_enqueue_transfer")
+        return Event(self._ctx, h.value, self.n_events, self.n_digis)
+
+    def device_clusters(self) -> DeviceClusters:
+        """Device addresses of a HP_KEEP_ON_DEVICE event's results (hp_event_device_clusters)."""
+        v = DeviceClusters()
+        _check(self._ctx._lib.hp_event_device_clusters(self._h, ctypes.byref(v)), "hp_event_device_clusters")
+        return v
 
     def hits(self) -> "HitsEvent":
         """Queue the clusters -> hits consumer of this event (hp_enqueue_hits)."""
@@ -377,6 +413,49 @@ class Context:
                                                ctypes.byref(out.struct), ctypes.c_void_p(stream)),
                "hp_reconstruct_device")
 
+    def graph_capture(self, n_events, n_digis, d_offsets, d_words, d_modules, out: "DeviceOutputs") -> "Graph":
+        """Capture one device-resident pass into a CUDA graph (hp_graph_capture)."""
+        h = ctypes.c_void_p()
+        _check(self._lib.hp_graph_capture(self._h, n_events, n_digis, d_offsets, d_words, d_modules,
+                                          ctypes.byref(out.struct), ctypes.byref(h)), "hp_graph_capture")
+        return Graph(self, h.value)
+
+    def tuning_candidates(self) -> list:
+        """The autotuner's search space on this device (list of dicts)."""
+        n = ctypes.c_uint32()
+        _check(self._lib.hp_tuning_candidates(self._h, 0, None, ctypes.byref(n)), "hp_tuning_candidates")
+        arr = (Tuning * max(1, n.value))()
+        _check(self._lib.hp_tuning_candidates(self._h, n.value, arr, ctypes.byref(n)), "hp_tuning_candidates")
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def get_tuning(self, n_events, n_digis) -> dict:
+        """The clustering-kernel settings a launch of this shape uses."""
+        t = Tuning()
+        _check(self._lib.hp_get_tuning(self._h, n_events, n_digis, ctypes.byref(t)), "hp_get_tuning")
+        return t.as_dict()
+
+    def try_set_tuning(self, n_events, n_digis, tuning) -> int:
+        """Set (dict) or clear (None) the settings of this shape's bucket; returns the status."""
+        if tuning is None:
+            return self._lib.hp_set_tuning(self._h, n_events, n_digis, None)
+        t = Tuning(**tuning)
+        return self._lib.hp_set_tuning(self._h, n_events, n_digis, ctypes.byref(t))
+
+    def set_tuning(self, n_events, n_digis, tuning):
+        _check(self.try_set_tuning(n_events, n_digis, tuning), "hp_set_tuning")
+
+    def autotune(self, n_events, n_digis, d_offsets, d_words, d_modules, out: "DeviceOutputs", reps: int = 3):
+        """Time every candidate on these device inputs and keep the fastest for
+        the shape's bucket.  Returns (best dict, best ms, [ms per candidate])."""
+        n = len(self.tuning_candidates())
+        ms = (ctypes.c_double * max(1, n))()
+        best = Tuning()
+        best_ms = ctypes.c_double()
+        _check(self._lib.hp_autotune(self._h, n_events, n_digis, d_offsets, d_words, d_modules,
+                                     ctypes.byref(out.struct), reps, n, ms, ctypes.byref(best),
+                                     ctypes.byref(best_ms)), "hp_autotune")
+        return best.as_dict(), best_ms.value, [ms[i] for i in range(n)]
+
     def set_geometry(self, origin, rot, pitch_row, pitch_col):
         """Install the module placement for hits (origin float[M,3] cm, rot float[M,3,3])."""
         origin = np.ascontiguousarray(origin, np.float32).reshape(-1)
@@ -461,6 +540,22 @@ class Context:
         s = Stats()
         _check(self._lib.hp_get_stats(self._h, ctypes.byref(s)), "hp_get_stats")
         return {n: int(getattr(s, n)) for n, _ in Stats._fields_}
+
+
+class Graph:
+    """A captured device-resident pass (see hp_graph_capture)."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self._ctx = ctx
+        self._h = ctypes.c_void_p(handle)
+
+    def launch(self, stream: int = 0):
+        _check(self._ctx._lib.hp_graph_launch(self._h, ctypes.c_void_p(stream)), "hp_graph_launch")
+
+    def destroy(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(self._ctx._lib.hp_graph_destroy(h), "hp_graph_destroy")
 
 
 class DeviceOutputs:
