@@ -69,6 +69,12 @@ def _args():
                    help="Poisson arrival rates (events/s) of the serving measurement")
     p.add_argument("--serving-events", type=int, default=2000, help="requests per serving rate")
     p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
+    p.add_argument("--e2e-depth", type=int, default=2, help="batches in flight in the end-to-end measurement")
+    p.add_argument("--serving-inflight", type=int, default=0, help="serving batches in flight (0: library default)")
+    p.add_argument("--serving-profile", action="store_true",
+                   help="diagnostic: stage timers on every serving batch (summed kernel time)")
+    p.add_argument("--serving-nocopy", action="store_true",
+                   help="serving inputs submitted from pinned buffers and copied by DMA (no staging copy)")
     return p.parse_args()
 
 
@@ -343,7 +349,8 @@ def run_ours(a):
         e2e, per_event = _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world)
     ctx.close()
     if not a.device_only and rank == 0:
-        serving = run_serving(local, [float(x) for x in a.serving_rates.split(",") if x], a.serving_events)
+        serving = run_serving(local, [float(x) for x in a.serving_rates.split(",") if x], a.serving_events,
+                              nocopy=a.serving_nocopy, inflight=a.serving_inflight)
 
     if rank == 0:
         line = {
@@ -438,7 +445,7 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
     # end to end through the public enqueue API: pinned host inputs, H2D, pass, results in host memory
     pw = torch.from_numpy(w.words.view(np.int32)).pin_memory()
     pm = torch.from_numpy(w.modules.view(np.int16)).pin_memory()
-    depth = 2  # batches in flight: the next batch's copies overlap this one's kernels
+    depth = a.e2e_depth  # batches in flight: the next batch's copies overlap this one's kernels
     for _ in range(2):  # warm the pools at the timed depth (one device + pinned block per batch in flight)
         evs = [ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY) for _ in range(depth)]
         for ev in evs:
@@ -467,7 +474,7 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
         t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_e2e = float(t.item())
-    e2e = {"value": world * E * a.steps / t_e2e, "unit": "events/s",
+    e2e = {"value": world * E * a.steps / t_e2e, "unit": "events/s", "batches_in_flight": depth,
            "h2d_bytes_per_step": 6 * N + 8 * (E + 1),
            "d2h_bytes_per_step": 4 * N + 24 * n_clusters + 8 * (E + 1) + 4 * E,
            "mdigis_per_s": world * N * a.steps / t_e2e / 1e6}
@@ -509,7 +516,8 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
     return e2e, per_event
 
 
-def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=16 << 30):
+def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=16 << 30, nocopy=False,
+                profile=False, inflight=0):
     """Serving workload: Poisson arrivals at each rate, event sizes lognormal
     (median 80k digis, sigma 0.8, capped at 500k), 4 native submitter threads
     with completion callbacks (hp_serve_replay), a 16 GB device budget,
@@ -521,25 +529,41 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
     pool = [w.event(e) for e in range(w.n_events)]
     out = []
     with hp.Context(w.n_modules, w.gain, w.pedestal, device=local, want_labels=True, n_streams=4) as ctx:
-        ctx.serve_start(budget_bytes=budget, want_labels=True)
+        ctx.serve_start(budget_bytes=budget, want_labels=True, nocopy=nocopy, max_inflight_batches=inflight)
         # warm the pools with every pool event, a few at a time and all at once
         ctx.serve_replay(pool, np.zeros(2 * len(pool)), np.arange(2 * len(pool)) % len(pool), submitters)
         for k, rate in enumerate(rates):
             gaps = synth.exponential(synth.child_seed(synth.BASE_SEED + 5, 1000 + k), n_requests, rate)
             arrival = np.cumsum(gaps) - gaps[0]
             idx = np.arange(n_requests) % len(pool)
+            # steady state: a warm-up stretch at this rate first (pool bins of its batch sizes)
+            nw = min(n_requests, 2000)
+            ctx.serve_replay(pool, arrival[:nw], idx[:nw], submitters)
+            s0 = ctx.stats()
+            if profile:  # stage timers on every batch: summed kernel time (diagnostic; adds event records)
+                ctx.profile_enable(1 << 20)
             lat, st, span = ctx.serve_replay(pool, arrival, idx, submitters)
+            prof = ctx.profile_read() if profile else {}
+            ctx.profile_enable(0)
+            s1 = ctx.stats()
             nd = sum(len(pool[i][0]) for i in idx)
+            nb = max(1, s1["serve_batches"] - s0["serve_batches"])
             out.append({"rate_offered": rate, "requests": n_requests,
                         "sustained_events_per_s": n_requests / span,
                         "mdigis_per_s": nd / span / 1e6,
                         "latency_ms_p50": float(np.percentile(lat, 50) * 1e3),
                         "latency_ms_p99": float(np.percentile(lat, 99) * 1e3),
-                        "errors": int((st != 0).sum())})
+                        "errors": int((st != 0).sum()),
+                        "mean_batch": n_requests / nb,
+                        "submit_us_per_request": (s1["serve_submit_ns"] - s0["serve_submit_ns"]) / n_requests / 1e3,
+                        "admitter_busy": (s1["serve_launch_ns"] - s0["serve_launch_ns"]) / 1e9 / span,
+                        "completion_busy": (s1["serve_complete_ns"] - s0["serve_complete_ns"]) / 1e9 / span,
+                        "kernel_busy": (sum(v[1] for v in prof.values()) / 1e3 / span) if profile else None})
         stats = ctx.stats()
         ctx.serve_stop()
     return {"workload": f"serving: lognormal sizes (median 80k, sigma 0.8, cap 500k), pool of {pool_events} "
-                        f"events, {submitters} native submitter threads, {budget >> 30} GB budget",
+                        f"events, {submitters} native submitter threads, {budget >> 30} GB budget, "
+                        f"inputs {'read in place from pinned buffers' if nocopy else 'copied into pinned staging'}",
             "batches": stats["serve_batches"], "requests": stats["serve_requests"], "rates": out}
 
 
@@ -552,7 +576,8 @@ def main():
         from paper_2004_04334_gb300 import build
         build.build()
         print(json.dumps(run_serving(local, [float(x) for x in a.serving_rates.split(",") if x],
-                                     a.serving_events)), flush=True)
+                                     a.serving_events, nocopy=a.serving_nocopy,
+                                     profile=a.serving_profile, inflight=a.serving_inflight)), flush=True)
     else:
         run_ours(a)
 

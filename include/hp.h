@@ -154,8 +154,12 @@ typedef struct hp_stats {
     uint64_t kernel_launches;   /* kernels launched by the library */
     uint64_t serve_batches;     /* batches launched by the serving loop */
     uint64_t serve_requests;    /* requests accepted by hp_submit */
-    uint64_t consumer_stream_reuses; /* hp_enqueue_hits calls that took the product's own stream */
-    uint64_t consumer_stream_waits;  /* hp_enqueue_hits calls that queued cudaStreamWaitEvent */
+    uint64_t consumer_stream_reuses; /* consumer calls (hits, transfer) that took the product's own stream */
+    uint64_t consumer_stream_waits;  /* consumer calls that queued cudaStreamWaitEvent */
+    uint64_t serve_submit_ns;   /* serving: total time spent inside hp_submit (all threads) */
+    uint64_t serve_launch_ns;   /* serving: total admitter time launching batches */
+    uint64_t serve_complete_ns; /* serving: total time in batch completion host functions (callbacks included) */
+    uint64_t serve_max_batch;   /* serving: most requests in one batch */
 } hp_stats;
 
 /* Serving loop configuration (hp_serve_start). */
@@ -165,7 +169,9 @@ typedef struct hp_serve_config {
     uint64_t max_batch_digis;      /* digis per batch; 0 = 32 Mi */
     uint32_t max_inflight_batches; /* batches on the device at once; 0 = 4 */
     uint32_t max_pending;          /* queued requests before hp_submit says HP_EAGAIN; 0 = 65536 */
-    uint32_t flags;                /* HP_WANT_LABELS */
+    uint32_t flags;                /* HP_WANT_LABELS; HP_INPUT_NOCOPY: hp_submit does not copy the inputs,
+                                      the batch copies them by DMA, so they must stay valid (and should
+                                      be pinned) until the request completes */
 } hp_serve_config;
 
 const char *hp_status_string(hp_status st);
@@ -440,7 +446,9 @@ hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, cons
 /*
  * Serving (continuous batching).  hp_serve_start starts an admitter thread.
  * hp_submit is a non-blocking acquire() of one event (Sec. 2): it copies the
- * inputs into pooled pinned staging and queues the request; it returns
+ * inputs into pooled pinned staging (or, with HP_INPUT_NOCOPY in the serving
+ * flags, keeps the caller's pointers for the batch to copy by DMA) and
+ * queues the request; it returns
  * HP_EAGAIN only when max_pending requests already wait.  The admitter
  * launches everything queued as one batch whenever fewer than
  * max_inflight_batches batches run and the batch fits the device budget
@@ -465,7 +473,8 @@ hp_status hp_serve_stop(hp_ctx *ctx);
  * threads replay a schedule of n_requests arrivals.  Request i arrives
  * arrival_ns[i] after the start (non-decreasing per thread is not required)
  * and submits pool event event_index[i] (pool_words/pool_modules/pool_n, n_pool
- * events, host memory).  Each completion callback records the request's
+ * events, host memory; with HP_INPUT_NOCOPY serving it first copies the pool
+ * into one pinned block, as a data source writing to pinned buffers would).  Each completion callback records the request's
  * submit-to-completion latency in latency_ns[i] and its status in status[i],
  * then releases it.  The call returns when every request has completed;
  * *span_ns is the time from the start to the last completion.  Requires a

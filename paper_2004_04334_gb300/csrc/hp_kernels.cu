@@ -694,16 +694,31 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     __syncthreads();
 
     // occupancy and survivor bitmaps; validation and duplicate detection
-    for_digis(bw, n, [&](uint32_t, uint32_t w) {
-        const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, adc = (w >> 17) & 0xFFu;
-        if (r >= R || c >= C || adc == 0 || (w >> 25) != 0) {
-            atomicOr(&bs.flag, kErrBadDigi);
-            return;
+    {   // the item's words are loaded four per thread at a time, so that
+        // their latencies overlap instead of adding up
+        auto body = [&](uint32_t w) {
+            const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, adc = (w >> 17) & 0xFFu;
+            if (r >= R || c >= C || adc == 0 || (w >> 25) != 0) {
+                atomicOr(&bs.flag, kErrBadDigi);
+                return;
+            }
+            const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
+            if (atomicOr(&abits[lin >> 5], bit) & bit) atomicOr(&bs.flag, kErrDup);
+            if (charge(w) >= thr) atomicOr(&sbits[lin >> 5], bit);
+        };
+#pragma unroll 1
+        for (uint32_t k0 = tid; k0 < n; k0 += 4 * kCCThreads) {
+            uint32_t wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = k0 + u * kCCThreads;
+                wv[u] = k < n ? __ldg(bw + k) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u * kCCThreads < n) body(wv[u]);
         }
-        const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
-        if (atomicOr(&abits[lin >> 5], bit) & bit) atomicOr(&bs.flag, kErrDup);
-        if (charge(w) >= thr) atomicOr(&sbits[lin >> 5], bit);
-    });
+    }
     __syncthreads();
     const uint32_t flag = bs.flag;
     if (flag) {
@@ -1034,6 +1049,21 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                     s_K[tid] = 0;
                 }
                 __syncthreads();
+                {   // pull the ticket's buckets (words and digi indices, contiguous
+                    // over its items) into L2, one 128-byte line per thread, so
+                    // that the items after the first do not wait on DRAM
+                    uint32_t last = 0;
+                    for (uint32_t i = 0; i < G; ++i)
+                        if (s_n[i]) last = i;
+                    const uint64_t b0 = s_b[0], b1 = (uint64_t)s_b[last] + s_n[last];
+                    const uint64_t lines = b1 > b0 ? ((b1 - b0) * 4 + 127) / 128 : 0;
+                    for (uint64_t li = tid; li < 2 * lines; li += kCCThreads) {
+                        const uint32_t *base = li < lines ? L.ws.bucket_w : L.ws.bucket_i;
+                        const uint64_t off = b0 * 4 + (li % lines) * 128; // < b1 * 4: inside the array
+                        if (off < b1 * 4)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(base) + off));
+                    }
+                }
                 {   // warp tier: one warp per small item
                     const uint32_t wi = tid >> 5;
                     const uint32_t n = s_n[wi];

@@ -41,6 +41,17 @@ uint64_t now_ns()
 }
 
 // Bin sizes: four bins per power of two, 4 KiB minimum (at most 25% slack).
+// Serving sizes vary from batch to batch and request to request: rounding
+// them up to a power of two keeps the number of distinct pool bins small, so
+// a steady stream reuses cached blocks instead of allocating (cudaMalloc
+// synchronises the device) at the cost of at most 2x memory.
+size_t round_pow2(size_t bytes)
+{
+    size_t p = 4096;
+    while (p < bytes) p <<= 1;
+    return p;
+}
+
 size_t round_bin(size_t bytes)
 {
     if (bytes <= 4096) return 4096;
@@ -219,6 +230,7 @@ struct hp_ctx {
     std::mutex serve_mu;
     Serve *serve = nullptr;
     std::atomic<uint64_t> serve_batches{0}, serve_requests{0};
+    std::atomic<uint64_t> serve_submit_ns{0}, serve_launch_ns{0}, serve_complete_ns{0}, serve_max_batch{0};
     // hits: module placement (every version stays until hp_destroy, so queued
     // work keeps the one it was queued with) and the consumer streams
     std::mutex geom_mu;
@@ -267,6 +279,9 @@ struct hp_event {
     Batch *batch = nullptr;
     uint32_t index = 0;
     Block staging;               // the request's inputs (pinned), until its batch completes
+    const uint32_t *in_words = nullptr;  // inputs of the request: device alias of the staging, or the
+    const uint16_t *in_mods = nullptr;   // caller's buffers (in_direct, HP_INPUT_NOCOPY)
+    bool in_direct = false;
     uint64_t coff_local[2] = {0, 0};
     // Product<T> stream rule (Sec. 4.2): set by the first consumer, which takes this event's stream
     std::atomic<bool> stream_taken{false};
@@ -895,6 +910,11 @@ void CUDART_CB batch_done(void *p)
     Batch *b = static_cast<Batch *>(p);
     hp_ctx *ctx = b->ctx;
     const uint64_t now = now_ns();
+    struct Timer { // time spent in this host function
+        hp_ctx *c;
+        uint64_t t;
+        ~Timer() { c->serve_complete_ns.fetch_add(now_ns() - t); }
+    } timer{ctx, now};
     for (uint32_t e = 0; e < b->E; ++e) {
         hp_event *r = b->reqs[e];
         const uint64_t c0 = b->h_coff[e], c1 = b->h_coff[e + 1];
@@ -972,11 +992,9 @@ BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
 void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
 {
     const uint32_t E = (uint32_t)take.size();
-    uint64_t N = 0, max_n = 0;
-    for (hp_event *r : take) {
-        N += r->N;
-        max_n = std::max<uint64_t>(max_n, r->N);
-    }
+    const uint64_t t_start = now_ns();
+    uint64_t N = 0;
+    for (hp_event *r : take) N += r->N;
     const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
     const BatchLayout l = batch_layout(ctx, E, N, labels);
     Batch *b = new (std::nothrow) Batch();
@@ -995,16 +1013,16 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->N = N;
     b->labels = labels;
     b->reqs = take;
-    if (ctx->dpool.alloc(l.dev_bytes, &b->dev) != HP_OK) {
+    if (ctx->dpool.alloc(round_pow2(l.dev_bytes), &b->dev) != HP_OK) {
         delete b;
         return give_up(HP_ENOMEM);
     }
-    if (ctx->hpool.alloc(l.host_bytes, &b->host) != HP_OK) {
+    if (ctx->hpool.alloc(round_pow2(l.host_bytes), &b->host) != HP_OK) {
         ctx->dpool.free(b->dev);
         delete b;
         return give_up(HP_ENOMEM);
     }
-    b->dev_charge = round_bin(l.dev_bytes);
+    b->dev_charge = round_pow2(l.dev_bytes);
     ctx->dev_in_use.fetch_add(b->dev_charge);
     b->refs.store(E + 1);
     for (hp_event *r : take) r->batch = b;
@@ -1023,14 +1041,18 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->h_label = labels ? reinterpret_cast<int32_t *>(hb + l.h_label) : nullptr;
     hp::GatherEntry *table = reinterpret_cast<hp::GatherEntry *>(hb + l.h_table);
     b->h_offs[0] = 0;
+    uint32_t n_gather = 0;
+    uint64_t max_gather = 0;
     for (uint32_t e = 0; e < E; ++e) {
         hp_event *r = take[e];
         b->h_offs[e + 1] = b->h_offs[e] + r->N;
-        const unsigned char *sd = static_cast<const unsigned char *>(r->staging.dptr);
-        table[e].words = reinterpret_cast<const uint32_t *>(sd);
-        table[e].modules = reinterpret_cast<const uint16_t *>(sd + align_up(4 * r->N, 256));
-        table[e].n = r->N;
-        table[e].off = b->h_offs[e];
+        if (r->in_direct || !r->N) continue;
+        table[n_gather].words = r->in_words;
+        table[n_gather].modules = r->in_mods;
+        table[n_gather].n = r->N;
+        table[n_gather].off = b->h_offs[e];
+        max_gather = std::max<uint64_t>(max_gather, r->N);
+        ++n_gather;
     }
 
     hp::Launch L;
@@ -1059,11 +1081,20 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     cudaStream_t s = ctx->streams[si];
     uint64_t nk = 0;
     cudaError_t err = cudaMemcpyAsync(db + l.d_offs, b->h_offs, 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
-    if (err == cudaSuccess)
-        err = hp::launch_gather(reinterpret_cast<const hp::GatherEntry *>(hd + l.h_table), E, max_n,
-                                reinterpret_cast<uint32_t *>(db + l.d_words),
-                                reinterpret_cast<uint16_t *>(db + l.d_mods), s);
-    nk += (N > 0);
+    uint32_t *dw = reinterpret_cast<uint32_t *>(db + l.d_words);
+    uint16_t *dm = reinterpret_cast<uint16_t *>(db + l.d_mods);
+    for (uint32_t e = 0; e < E && err == cudaSuccess; ++e) {
+        hp_event *r = take[e];
+        if (!r->in_direct || !r->N) continue;
+        err = cudaMemcpyAsync(dw + b->h_offs[e], r->in_words, 4 * r->N, cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(dm + b->h_offs[e], r->in_mods, 2 * r->N, cudaMemcpyHostToDevice, s);
+    }
+    if (err == cudaSuccess && n_gather) {
+        err = hp::launch_gather(reinterpret_cast<const hp::GatherEntry *>(hd + l.h_table), n_gather, max_gather, dw,
+                                dm, s);
+        ++nk;
+    }
     if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
     if (err == cudaSuccess && labels && N)
         err = cudaMemcpyAsync(b->h_label, db + l.d_label, 4 * N, cudaMemcpyDeviceToHost, s);
@@ -1078,6 +1109,10 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     if (labels) ctx->d2h.fetch_add(4 * N);
     ctx->kernels.fetch_add(nk);
     ctx->serve_batches.fetch_add(1);
+    ctx->serve_launch_ns.fetch_add(now_ns() - t_start);
+    uint64_t mb = ctx->serve_max_batch.load();
+    while (E > mb && !ctx->serve_max_batch.compare_exchange_weak(mb, E)) {
+    }
 }
 
 void admitter_main(hp_ctx *ctx, Serve *sv)
@@ -1106,7 +1141,7 @@ void admitter_main(hp_ctx *ctx, Serve *sv)
                 sv->pending.pop_front();
             }
             if (budget) {
-                const size_t need = round_bin(batch_layout(ctx, (uint32_t)take.size(), nd, labels).dev_bytes);
+                const size_t need = round_pow2(batch_layout(ctx, (uint32_t)take.size(), nd, labels).dev_bytes);
                 sv->cv.wait(lk, [&] {
                     return sv->inflight_batches == 0 || ctx->dev_in_use.load() + need <= budget;
                 });
@@ -2005,6 +2040,7 @@ hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_i
     if (ctx->failed.load()) return HP_ECUDA;
     if (n_digis >= 0xFFFFFFFFull) return HP_EINVAL;
     if (n_digis > 0 && (!words || !module_ids)) return HP_EINVAL;
+    const uint64_t t_start = now_ns();
     Serve *sv = nullptr;
     {
         std::lock_guard<std::mutex> g(ctx->serve_mu);
@@ -2025,15 +2061,26 @@ hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_i
     ev->N = n_digis;
     ev->tag = tag;
     ev->flags = sv->cfg.flags | ctx->cfg.flags;
-    const size_t wbytes = align_up(4 * n_digis, 256);
-    if (ctx->hpool.alloc(wbytes + 2 * n_digis + 256, &ev->staging) != HP_OK) {
-        delete ev;
-        return HP_ENOMEM;
-    }
-    unsigned char *st = static_cast<unsigned char *>(ev->staging.ptr);
-    if (n_digis) {
-        std::memcpy(st, words, 4 * n_digis);
-        std::memcpy(st + wbytes, module_ids, 2 * n_digis);
+    if (ev->flags & HP_INPUT_NOCOPY) {
+        // the caller's buffers stay where they are until the batch copies
+        // them (one cudaMemcpyAsync each: DMA from pinned memory)
+        ev->in_words = words;
+        ev->in_mods = module_ids;
+        ev->in_direct = true;
+    } else {
+        const size_t wbytes = align_up(4 * n_digis, 256);
+        if (ctx->hpool.alloc(round_pow2(wbytes + 2 * n_digis + 256), &ev->staging) != HP_OK) {
+            delete ev;
+            return HP_ENOMEM;
+        }
+        unsigned char *st = static_cast<unsigned char *>(ev->staging.ptr);
+        if (n_digis) {
+            std::memcpy(st, words, 4 * n_digis);
+            std::memcpy(st + wbytes, module_ids, 2 * n_digis);
+        }
+        const unsigned char *sd = static_cast<const unsigned char *>(ev->staging.dptr);
+        ev->in_words = reinterpret_cast<const uint32_t *>(sd);
+        ev->in_mods = reinterpret_cast<const uint16_t *>(sd + wbytes);
     }
     if (cb) {
         ev->cb = cb;
@@ -2055,6 +2102,7 @@ hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_i
     sv->cv.notify_one();
     ctx->serve_requests.fetch_add(1);
     ctx->enqueued.fetch_add(1);
+    ctx->serve_submit_ns.fetch_add(now_ns() - t_start);
     *out = ev;
     return HP_OK;
 }
@@ -2092,6 +2140,37 @@ hp_status hp_serve_replay(hp_ctx *ctx, uint32_t n_threads, uint64_t n_requests, 
         uint64_t i;
     };
     std::vector<Slot> slots(n_requests);
+    // a serving loop that reads inputs in place (HP_INPUT_NOCOPY) needs them
+    // in pinned memory: the driver then submits from a pinned copy of the pool
+    bool nocopy = false;
+    {
+        std::lock_guard<std::mutex> g(ctx->serve_mu);
+        nocopy = ctx->serve && ((ctx->serve->cfg.flags | ctx->cfg.flags) & HP_INPUT_NOCOPY);
+    }
+    std::vector<const uint32_t *> pw(pool_words, pool_words + n_pool);
+    std::vector<const uint16_t *> pm(pool_modules, pool_modules + n_pool);
+    void *pinned = nullptr;
+    if (nocopy) {
+        size_t total = 0;
+        for (uint32_t e = 0; e < n_pool; ++e) total += align_up(4 * pool_n[e], 256) + align_up(2 * pool_n[e], 256);
+        if (cudaHostAlloc(&pinned, std::max<size_t>(total, 256), cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return HP_ENOMEM;
+        }
+        unsigned char *q = static_cast<unsigned char *>(pinned);
+        for (uint32_t e = 0; e < n_pool; ++e) {
+            std::memcpy(q, pool_words[e], 4 * pool_n[e]);
+            pw[e] = reinterpret_cast<const uint32_t *>(q);
+            q += align_up(4 * pool_n[e], 256);
+            std::memcpy(q, pool_modules[e], 2 * pool_n[e]);
+            pm[e] = reinterpret_cast<const uint16_t *>(q);
+            q += align_up(2 * pool_n[e], 256);
+        }
+    }
+    auto unregister = [&]() {
+        if (pinned) cudaFreeHost(pinned);
+        cudaGetLastError();
+    };
     auto cb = [](void *user, hp_event *ev, hp_status st) {
         Slot *sl = static_cast<Slot *>(user);
         sl->sh->latency[sl->i] = hp_event_latency_ns(ev);
@@ -2114,7 +2193,7 @@ hp_status hp_serve_replay(hp_ctx *ctx, uint32_t n_threads, uint64_t n_requests, 
             const uint32_t e = event_index[i];
             hp_event *ev = nullptr;
             for (;;) {
-                const hp_status st = hp_submit(ctx, pool_words[e], pool_modules[e], pool_n[e], i, +cb, &slots[i], &ev);
+                const hp_status st = hp_submit(ctx, pw[e], pm[e], pool_n[e], i, +cb, &slots[i], &ev);
                 if (st == HP_OK) break;
                 if (st != HP_EAGAIN) {
                     std::lock_guard<std::mutex> g(sh.mu);
@@ -2135,6 +2214,7 @@ hp_status hp_serve_replay(hp_ctx *ctx, uint32_t n_threads, uint64_t n_requests, 
         std::unique_lock<std::mutex> lk(sh.mu);
         sh.cv.wait(lk, [&] { return sh.remaining == 0; });
     }
+    unregister();
     *span_ns = sh.last_done > t0 ? sh.last_done - t0 : 0;
     return sh.submit_error;
 }
@@ -2155,6 +2235,10 @@ hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)
     o->kernel_launches = ctx->kernels.load();
     o->serve_batches = ctx->serve_batches.load();
     o->serve_requests = ctx->serve_requests.load();
+    o->serve_submit_ns = ctx->serve_submit_ns.load();
+    o->serve_launch_ns = ctx->serve_launch_ns.load();
+    o->serve_complete_ns = ctx->serve_complete_ns.load();
+    o->serve_max_batch = ctx->serve_max_batch.load();
     o->consumer_stream_reuses = ctx->consumer_reuses.load();
     o->consumer_stream_waits = ctx->consumer_waits.load();
     return ctx->failed.load() ? HP_ECUDA : HP_OK;

@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "device_mallocs", "host_mallocs", "pool_hits", "device_bytes_in_use", "device_bytes_cached",
         "events_enqueued", "events_completed", "inflight", "h2d_bytes", "d2h_bytes", "kernel_launches",
-        "serve_batches", "serve_requests", "consumer_stream_reuses", "consumer_stream_waits")]
+        "serve_batches", "serve_requests", "consumer_stream_reuses", "consumer_stream_waits", "serve_submit_ns",
+        "serve_launch_ns", "serve_complete_ns", "serve_max_batch")]
 
 
 class Tuning(ctypes.Structure):
@@ -472,10 +473,10 @@ class Context:
                                         d_hy, d_hz, ctypes.c_void_p(stream)), "hp_hits_device")
 
     def serve_start(self, budget_bytes=0, max_batch_events=0, max_batch_digis=0, max_inflight_batches=0,
-                    max_pending=0, want_labels=False):
+                    max_pending=0, want_labels=False, nocopy=False):
         """Start the continuous-batching serving loop (see hp_serve_start)."""
         cfg = ServeConfig(budget_bytes, max_batch_events, max_batch_digis, max_inflight_batches, max_pending,
-                          HP_WANT_LABELS if want_labels else 0)
+                          (HP_WANT_LABELS if want_labels else 0) | (HP_INPUT_NOCOPY if nocopy else 0))
         _check(self._lib.hp_serve_start(self._h, ctypes.byref(cfg)), "hp_serve_start")
 
     def try_submit(self, words, modules, tag=0):

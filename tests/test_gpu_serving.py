@@ -148,3 +148,41 @@ def test_native_replay_driver(pool):
     assert np.all(st == 0) and np.all(lat > 0)
     assert span >= arrival[-1] - arrival[0]
     assert s["serve_requests"] == 200 and s["serve_batches"] <= 200
+
+
+def test_nocopy_serving_reads_pinned_inputs_in_place(pool):
+    """HP_INPUT_NOCOPY serving: hp_submit keeps the caller's (pinned) buffers,
+    the batch copies them by DMA; results equal the event processed alone."""
+    import torch
+
+    w = pool
+    with hp.Context(w.n_modules, w.gain, w.pedestal, want_labels=True, n_streams=4) as ctx:
+        alone = [_alone(ctx, w, e) for e in range(w.n_events)]
+        pinned = []
+        for e in range(w.n_events):
+            words, mods = w.event(e)
+            pw = torch.from_numpy(words.view(np.int32).copy()).pin_memory()
+            pm = torch.from_numpy(mods.view(np.int16).copy()).pin_memory()
+            pinned.append((pw, pm))
+        ctx.serve_start(budget_bytes=16 << 30, want_labels=True, nocopy=True)
+        before = ctx.stats()["serve_submit_ns"]
+        order = [e for _ in range(2) for e in np.random.default_rng(3).permutation(w.n_events)]
+        evs = []
+        for i, e in enumerate(order):
+            pw, pm = pinned[e]
+            words = pw.numpy().view(np.uint32)
+            mods = pm.numpy().view(np.uint16)
+            evs.append(ctx.submit(words, mods, tag=i))
+        for i, ev in enumerate(evs):
+            assert ev.wait(120) == hp.HP_OK
+            r, a = ev.fetch(), alone[order[i]]
+            for f in ("module", "id", "charge", "npix", "x", "y", "label"):
+                assert np.array_equal(getattr(r, f), getattr(a, f)), (i, f)
+            ev.release()
+        assert ctx.stats()["serve_submit_ns"] > before
+        # the native driver in the same mode (it submits from a pinned copy of its pool)
+        events = [w.event(e) for e in range(w.n_events)]
+        arrival = np.cumsum(np.random.default_rng(5).exponential(1 / 5000.0, 100))
+        lat, st, _ = ctx.serve_replay(events, arrival, np.arange(100) % len(events), 4)
+        assert np.all(st == 0) and np.all(lat > 0)
+        ctx.serve_stop()
