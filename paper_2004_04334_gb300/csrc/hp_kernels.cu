@@ -836,8 +836,8 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         __syncthreads();
     }
 
-    if (it.label_e) {
-        for_digis(bw, n, [&](uint32_t k, uint32_t w) {
+    if (it.label_e) { // loads of four digis (word and index) issued together, as for the bitmaps
+        auto label_of = [&](uint32_t w) -> int32_t {
             const uint32_t lin = lin_of(w);
             int32_t lab = -1;
             if (has_bit(sbits, lin)) {
@@ -847,8 +847,22 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
                 const uint32_t px = (p & kMark) ? p : t.parent[x];
                 lab = (int32_t)(t.qn[x] >> 17) >= cthr ? (int32_t)(px & ~kMark) : -2;
             }
-            it.label_e[__ldg(bi + k)] = lab;
-        });
+            return lab;
+        };
+#pragma unroll 1
+        for (uint32_t k0 = tid; k0 < n; k0 += 4 * kCCThreads) {
+            uint32_t wv[4], iv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = k0 + u * kCCThreads;
+                const bool in = k < n;
+                wv[u] = in ? __ldg(bw + k) : 0u;
+                iv[u] = in ? __ldg(bi + k) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u * kCCThreads < n) it.label_e[iv[u]] = label_of(wv[u]);
+        }
     }
 
     // Kept roots in slot order (= id order): one ballot per 32 consecutive
