@@ -65,7 +65,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--device-only", action="store_true",
                    help="only the device-resident timed loop (for profiler captures)")
-    p.add_argument("--serving-rates", default="5000,20000",
+    p.add_argument("--serving-rates", default="5000,20000,50000",
                    help="Poisson arrival rates (events/s) of the serving measurement")
     p.add_argument("--serving-events", type=int, default=2000, help="requests per serving rate")
     p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
@@ -73,8 +73,9 @@ def _args():
     p.add_argument("--serving-inflight", type=int, default=0, help="serving batches in flight (0: library default)")
     p.add_argument("--serving-profile", action="store_true",
                    help="diagnostic: stage timers on every serving batch (summed kernel time)")
-    p.add_argument("--serving-nocopy", action="store_true",
-                   help="serving inputs submitted from pinned buffers and copied by DMA (no staging copy)")
+    p.add_argument("--serving-staging", action="store_true",
+                   help="serving inputs copied into pinned staging by hp_submit (default: submitted from pinned "
+                        "buffers and copied by DMA)")
     return p.parse_args()
 
 
@@ -83,6 +84,31 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def rank_seed(rank: int, world: int):
+    """Seed of a rank's replica: the workload's own seed on one GPU, a
+    distinct one per rank otherwise (replicas process different events)."""
+    return None if world == 1 else synth.BASE_SEED + 3 + 1000 * rank
+
+
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """The slowest rank's time: a MAX all-reduce over the process group (no
+    collective on one rank).  device: where the reduced tensor lives (the
+    rank's GPU under NCCL, None for the CPU under gloo)."""
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+
+    v = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def job_value(units_per_rank: int, steps: int, t: float, world: int) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank * steps / t
 
 
 def _peaks():
@@ -258,7 +284,7 @@ def run_ours(a):
     build.build()
 
     # each rank reconstructs its own shard of events (a replica), seeded by rank
-    seed = None if world == 1 else synth.BASE_SEED + 3 + 1000 * rank
+    seed = rank_seed(rank, world)
     w = synth.workload(a.workload, seed=seed)
     E, N, M = w.n_events, w.n_digis, w.n_modules
 
@@ -326,11 +352,8 @@ def run_ours(a):
     barrier()
     prof = ctx.profile_read()
     ctx.profile_enable(0)
-    if world > 1:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(t.item())
-    value = world * E * a.steps / t_dev
+    t_dev = max_over_ranks(t_dev, world, dev)
+    value = job_value(E, a.steps, t_dev, world)
     mdigis = world * N * a.steps / t_dev / 1e6
 
     # dominant kernel roofline
@@ -350,7 +373,7 @@ def run_ours(a):
     ctx.close()
     if not a.device_only and rank == 0:
         serving = run_serving(local, [float(x) for x in a.serving_rates.split(",") if x], a.serving_events,
-                              nocopy=a.serving_nocopy, inflight=a.serving_inflight)
+                              nocopy=not a.serving_staging, inflight=a.serving_inflight)
 
     if rank == 0:
         line = {
@@ -417,13 +440,10 @@ def _chain(a, ctx, w, out, n_clusters, dev, stream, step, barrier, world):
     barrier()
     t = c0.elapsed_time(c1) / 1000.0
     hits_s = sum(m0.elapsed_time(m1) for m0, m1 in marks) / 1000.0 / a.steps
-    if world > 1:
-        v = torch.tensor([t], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(v, op=torch.distributed.ReduceOp.MAX)
-        t = float(v.item())
+    t = max_over_ranks(t, world, dev)
     kb = 24 * n_clusters + 48 * M + 8 * (E + 1)
     peak, peak_kind = _peaks()
-    return {"value": world * E * a.steps / t, "unit": "events/s", "ms_per_step": 1000 * t / a.steps,
+    return {"value": job_value(E, a.steps, t, world), "unit": "events/s", "ms_per_step": 1000 * t / a.steps,
             "what": "hp_reconstruct_device + hp_hits_device per step on one stream",
             "hits_kernel": {"mean_launch_ms": hits_s * 1000, "hits_per_launch": n_clusters,
                             "algorithmic_bytes_per_launch": kb, "achieved": kb / hits_s / 1e9, "unit": "GB/s",
@@ -470,11 +490,8 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
     barrier()
     t_e2e = time.perf_counter() - t0
     assert st == hp.HP_OK and nc == n_clusters
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * E * a.steps / t_e2e, "unit": "events/s", "batches_in_flight": depth,
+    t_e2e = max_over_ranks(t_e2e, world, dev)
+    e2e = {"value": job_value(E, a.steps, t_e2e, world), "unit": "events/s", "batches_in_flight": depth,
            "h2d_bytes_per_step": 6 * N + 8 * (E + 1),
            "d2h_bytes_per_step": 4 * N + 24 * n_clusters + 8 * (E + 1) + 4 * E,
            "mdigis_per_s": world * N * a.steps / t_e2e / 1e6}
@@ -576,7 +593,7 @@ def main():
         from paper_2004_04334_gb300 import build
         build.build()
         print(json.dumps(run_serving(local, [float(x) for x in a.serving_rates.split(",") if x],
-                                     a.serving_events, nocopy=a.serving_nocopy,
+                                     a.serving_events, nocopy=not a.serving_staging,
                                      profile=a.serving_profile, inflight=a.serving_inflight)), flush=True)
     else:
         run_ours(a)

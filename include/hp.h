@@ -167,7 +167,7 @@ typedef struct hp_serve_config {
     size_t device_budget_bytes;    /* device bytes in-flight batches may hold; 0 = no limit */
     uint32_t max_batch_events;     /* requests per batch; 0 = 256 */
     uint64_t max_batch_digis;      /* digis per batch; 0 = 32 Mi */
-    uint32_t max_inflight_batches; /* batches on the device at once; 0 = 4 */
+    uint32_t max_inflight_batches; /* batches on the device at once; 0 = 2 (one copying while one computes) */
     uint32_t max_pending;          /* queued requests before hp_submit says HP_EAGAIN; 0 = 65536 */
     uint32_t flags;                /* HP_WANT_LABELS; HP_INPUT_NOCOPY: hp_submit does not copy the inputs,
                                       the batch copies them by DMA, so they must stay valid (and should
@@ -296,8 +296,9 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
  *                  items with more digis are clustered in global scratch;
  *   blocks_per_sm  resident clustering blocks per SM, 2 or 3 (3 caps the
  *                  kernel at 40 registers a thread and needs a smaller tile);
- *   ticket_items   (event, module) items per work-queue ticket, 16, 8 or 4
- *                  (halved further for launches too small to fill the GPU);
+ *   ticket_items   (event, module) items per work-queue ticket, 16, 8, 4
+ *                  or 2 (halved down to 4 for launches too small to fill the
+ *                  GPU);
  *   warp_max       largest item (digis) clustered by a single warp, 32 or 64.
  * Labels and clusters are the same for every setting; only speed differs.
  * Settings are kept per shape bucket (log2 of n_events * n_modules, log2 of

@@ -42,9 +42,12 @@ uint64_t now_ns()
 
 // Bin sizes: four bins per power of two, 4 KiB minimum (at most 25% slack).
 // Serving sizes vary from batch to batch and request to request: rounding
-// them up to a power of two keeps the number of distinct pool bins small, so
-// a steady stream reuses cached blocks instead of allocating (cudaMalloc
-// synchronises the device) at the cost of at most 2x memory.
+// them up to a power of two keeps the number of distinct pool bins small, and
+// serving allocations may take any cached block up to kServeRatio times their
+// size, so a steady stream reuses cached blocks instead of allocating
+// (cudaMalloc synchronises the device; cudaHostAlloc takes milliseconds),
+// at the cost of memory.
+constexpr size_t kServeRatio = 256;
 size_t round_pow2(size_t bytes)
 {
     size_t p = 4096;
@@ -74,7 +77,9 @@ class Pool {
   public:
     explicit Pool(bool host) : host_(host) {}
 
-    hp_status alloc(size_t bytes, Block *out)
+    // max_ratio: the largest cached block (relative to the request) that may
+    // serve it; a large ratio trades memory for fewer backend calls.
+    hp_status alloc(size_t bytes, Block *out, size_t max_ratio = 2)
     {
         const size_t b = round_bin(bytes);
         {
@@ -83,8 +88,8 @@ class Pool {
                 --fail_next_;
                 return HP_ENOMEM;
             }
-            auto it = free_.lower_bound(b); // best fit among cached blocks of up to twice the size
-            if (it != free_.end() && it->first <= 2 * b) {
+            auto it = free_.lower_bound(b); // best fit among cached blocks of up to max_ratio times the size
+            if (it != free_.end() && it->first <= max_ratio * b) {
                 *out = it->second;
                 free_.erase(it);
                 ++hits_;
@@ -491,20 +496,20 @@ bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t)
 {
     if (t.blocks_per_sm != 2 && t.blocks_per_sm != 3) return false;
     if (t.tile_slots < 256 || t.tile_slots > ctx->max_tile[t.blocks_per_sm] || t.tile_slots % 256) return false;
-    if (t.ticket_max != 4 && t.ticket_max != 8 && t.ticket_max != 16) return false;
+    if (t.ticket_max != 2 && t.ticket_max != 4 && t.ticket_max != 8 && t.ticket_max != 16) return false;
     return t.warp_max == 32 || t.warp_max == 64;
 }
 
 // The autotuner's search space on this device: the default tile at two
 // resident blocks per SM and the largest tile that keeps three resident,
-// each with tickets of 16, 8 or 4 items and a warp tier up to 64 or 32 digis.
+// each with tickets of 16, 8, 4 or 2 items and a warp tier up to 64 or 32 digis.
 std::vector<hp::Tuning> tuning_candidates(const hp_ctx *ctx)
 {
     std::vector<hp::Tuning> c;
     for (uint32_t b = 2; b <= 3; ++b) {
         const uint32_t tile = b == 2 ? (uint32_t)hp::kSmemSlots : ctx->max_tile[3];
         if (tile < 256) continue;
-        for (uint32_t tk : {16u, 8u, 4u})
+        for (uint32_t tk : {16u, 8u, 4u, 2u})
             for (uint32_t wm : {64u, 32u}) {
                 hp::Tuning t;
                 t.tile_slots = tile;
@@ -1013,11 +1018,11 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->N = N;
     b->labels = labels;
     b->reqs = take;
-    if (ctx->dpool.alloc(round_pow2(l.dev_bytes), &b->dev) != HP_OK) {
+    if (ctx->dpool.alloc(round_pow2(l.dev_bytes), &b->dev, kServeRatio) != HP_OK) {
         delete b;
         return give_up(HP_ENOMEM);
     }
-    if (ctx->hpool.alloc(round_pow2(l.host_bytes), &b->host) != HP_OK) {
+    if (ctx->hpool.alloc(round_pow2(l.host_bytes), &b->host, kServeRatio) != HP_OK) {
         ctx->dpool.free(b->dev);
         delete b;
         return give_up(HP_ENOMEM);
@@ -1120,7 +1125,7 @@ void admitter_main(hp_ctx *ctx, Serve *sv)
     cudaSetDevice(ctx->device);
     const uint32_t max_events = sv->cfg.max_batch_events ? sv->cfg.max_batch_events : 256;
     const uint64_t max_digis = sv->cfg.max_batch_digis ? sv->cfg.max_batch_digis : (32ull << 20);
-    const uint32_t max_batches = sv->cfg.max_inflight_batches ? sv->cfg.max_inflight_batches : 4;
+    const uint32_t max_batches = sv->cfg.max_inflight_batches ? sv->cfg.max_inflight_batches : 2;
     const size_t budget = sv->cfg.device_budget_bytes;
     const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
     for (;;) {
@@ -2069,7 +2074,7 @@ hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_i
         ev->in_direct = true;
     } else {
         const size_t wbytes = align_up(4 * n_digis, 256);
-        if (ctx->hpool.alloc(round_pow2(wbytes + 2 * n_digis + 256), &ev->staging) != HP_OK) {
+        if (ctx->hpool.alloc(round_pow2(wbytes + 2 * n_digis + 256), &ev->staging, kServeRatio) != HP_OK) {
             delete ev;
             return HP_ENOMEM;
         }
