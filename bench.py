@@ -546,6 +546,7 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
     pool = [w.event(e) for e in range(w.n_events)]
     out = []
     with hp.Context(w.n_modules, w.gain, w.pedestal, device=local, want_labels=True, n_streams=4) as ctx:
+        tuned = pretune_batches(ctx, w, local)
         ctx.serve_start(budget_bytes=budget, want_labels=True, nocopy=nocopy, max_inflight_batches=inflight)
         # warm the pools with every pool event, a few at a time and all at once
         ctx.serve_replay(pool, np.zeros(2 * len(pool)), np.arange(2 * len(pool)) % len(pool), submitters)
@@ -581,7 +582,33 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
     return {"workload": f"serving: lognormal sizes (median 80k, sigma 0.8, cap 500k), pool of {pool_events} "
                         f"events, {submitters} native submitter threads, {budget >> 30} GB budget, "
                         f"inputs {'read in place from pinned buffers' if nocopy else 'copied into pinned staging'}",
-            "batches": stats["serve_batches"], "requests": stats["serve_requests"], "rates": out}
+            "batches": stats["serve_batches"], "requests": stats["serve_requests"], "pretuned_buckets": tuned,
+            "rates": out}
+
+
+def pretune_batches(ctx, w, local, sizes=(1, 2, 4, 8, 16, 32, 64, 128, 256), reps=2):
+    """Autotune the shape buckets that serving batches fall in: for each batch
+    size, random samples of the event pool as device-resident batches (the
+    settings stay in the context for every later launch of those buckets).
+    Returns the number of (size, sample) pairs tuned."""
+    import torch
+
+    from paper_2004_04334_gb300 import hp
+
+    dev = torch.device(f"cuda:{local}")
+    rng = np.random.default_rng(synth.child_seed(synth.BASE_SEED + 5, 77))
+    n = 0
+    for E in sizes:
+        for _ in range(reps):
+            sub = w.subset(rng.integers(0, w.n_events, E))
+            dw = torch.from_numpy(sub.words.view(np.int32)).to(dev)
+            dm = torch.from_numpy(sub.modules.view(np.int16)).to(dev)
+            do = torch.from_numpy(sub.offsets.view(np.int64)).to(dev)
+            out = hp.DeviceOutputs(sub.n_events, sub.n_digis, dev, labels=False)
+            ctx.autotune(sub.n_events, sub.n_digis, do.data_ptr(), dw.data_ptr(), dm.data_ptr(), out, reps=2)
+            n += 1
+    torch.cuda.synchronize(dev)
+    return n
 
 
 def main():

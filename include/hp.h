@@ -16,7 +16,14 @@
  *        device id, stream and CUDA event of the work that made the result;
  *   hp_enqueue_hits                       a second module consuming that
  *        product under the ScopedContext stream rules of Sec. 4.2 (the
- *        clusters -> hits step of Fig. 1).
+ *        clusters -> hits step of Fig. 1);
+ *   HP_KEEP_ON_DEVICE, hp_enqueue_transfer   transfer on demand (Sec. 4.3):
+ *        results stay on the device unless a transfer module asks for them.
+ *
+ * Besides: a device-resident entry (hp_reconstruct_device, its CUDA-graph
+ * form hp_graph_*, an allocation-free variant), an autotuner for the
+ * clustering kernel's launch parameters (hp_autotune), a continuous-batching
+ * serving loop (hp_serve_*), stage timers and counters.
  *
  * The device work is the raw -> clusters step of the paper's Fig. 1: decode
  * digi words, bucket them by module, calibrate q = adc * gain[m] - pedestal[m]
@@ -294,8 +301,9 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
  * digis per item):
  *   tile_slots     capacity of the shared-memory tile of the block tier:
  *                  items with more digis are clustered in global scratch;
- *   blocks_per_sm  resident clustering blocks per SM, 2 or 3 (3 caps the
- *                  kernel at 40 registers a thread and needs a smaller tile);
+ *   blocks_per_sm  resident clustering blocks per SM, 1, 2 or 3 (1 allows
+ *                  the largest tile; 3 caps the kernel at 40 registers a
+ *                  thread and needs a smaller tile);
  *   ticket_items   (event, module) items per work-queue ticket, 16, 8, 4
  *                  or 2 (halved down to 4 for launches too small to fill the
  *                  GPU);
@@ -401,7 +409,8 @@ typedef struct hp_hits {
  * product released while consumers are queued is freed only once they have
  * run.  The product must not have been released before this call, and must
  * be a clusters event of hp_enqueue_event/hp_enqueue_batch (not a serving
- * request, not a hits or transfer event).  flags is reserved (0).
+ * request, not a hits or transfer event).  flags is reserved (0).  It
+ * makes CUDA calls, so it must not be called from a completion callback.
  * Errors: HP_EINVAL (no geometry set, wrong kind of event), HP_ENOMEM,
  * HP_ECUDA.
  */

@@ -23,12 +23,13 @@ constexpr int kCCThreads = 512;      // threads of a clustering block
 constexpr int kGroup = kCCThreads / 32; // most (event, module) items per work-queue ticket, one per warp
 constexpr int kWarpMax = 64;         // items with at most this many digis are clustered by one warp
 constexpr int kSmemSlots = 4096;     // digis of an item a block clusters in shared memory (default tile)
+constexpr int kMaxTileSlots = 16384; // largest tile considered (one block per SM)
 
 // Launch parameters of the clustering kernel, chosen per launch shape by the
 // autotuner (defaults: the values above, two resident blocks per SM).
 struct Tuning {
     uint32_t tile_slots = kSmemSlots; // block-tier capacity in shared memory; larger items use global scratch
-    uint32_t blocks_per_sm = 2;       // 2 (up to 64 registers a thread) or 3 (up to 40, smaller tile)
+    uint32_t blocks_per_sm = 2;       // 1 (largest tile), 2 (up to 64 registers a thread) or 3 (up to 40, smaller tile)
     uint32_t ticket_max = kGroup;     // items per ticket before halving for small launches (<= kGroup)
     uint32_t warp_max = kWarpMax;     // 32 or 64: largest item of the warp tier
 };
@@ -110,7 +111,8 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
                        const Tuning &tune, Workspace *ws);
 // Configure kernel attributes once per device.  max_tile[b] receives the
 // largest tile (slots) with which b clustering blocks stay resident per SM
-// (0 if b blocks cannot be resident), for b = 2 and 3; max_tile[0..1] unused.
+// (0 if b blocks cannot be resident), for b = 1, 2 and 3 (at most
+// kMaxTileSlots for one block, kSmemSlots otherwise); max_tile[0] unused.
 cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4]);
 // Kernels of one launch, in order; marks[i] (if given) is recorded before
 // kernel i and marks[kNumKernels] after the last one.

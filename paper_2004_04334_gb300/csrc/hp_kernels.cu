@@ -1270,15 +1270,26 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
 
 namespace {
 
-// Largest tile (a multiple of 256 slots, at most kSmemSlots) with which
-// `blocks` blocks of `kern` stay resident on one SM; 0 if none does.
-template <class K> cudaError_t fit_tile(K kern, int blocks, uint32_t R, uint32_t C, uint32_t *tile)
+// Largest tile (a multiple of 256 slots, at most max_slots) with which
+// `blocks` blocks of `kern` stay resident on one SM; 0 if none does.  Also
+// raises the kernel's dynamic shared memory limit to what that tile needs.
+template <class K>
+cudaError_t fit_tile(K kern, int device, int blocks, uint32_t R, uint32_t C, uint32_t max_slots, uint32_t *tile)
 {
     *tile = 0;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)cc_smem_bytes(R, C, kSmemSlots));
+    int optin = 0;
+    cudaError_t err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (err != cudaSuccess) return err;
-    for (uint32_t t = kSmemSlots; t >= 256; t -= 256) {
+    cudaFuncAttributes fa;
+    err = cudaFuncGetAttributes(&fa, kern);
+    if (err != cudaSuccess) return err;
+    const size_t limit = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    uint32_t t = max_slots;
+    while (t >= 256 && cc_smem_bytes(R, C, t) > limit) t -= 256;
+    if (t < 256) return cudaSuccess;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cc_smem_bytes(R, C, t));
+    if (err != cudaSuccess) return err;
+    for (; t >= 256; t -= 256) {
         int nb = 0;
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kCCThreads, cc_smem_bytes(R, C, t));
         if (err != cudaSuccess) return err;
@@ -1298,10 +1309,12 @@ cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (err != cudaSuccess) return err;
-    max_tile[0] = max_tile[1] = 0;
-    err = fit_tile(cc_kernel<2>, 2, R, C, &max_tile[2]);
+    max_tile[0] = 0;
+    err = fit_tile(cc_kernel<1>, device, 1, R, C, kMaxTileSlots, &max_tile[1]);
     if (err != cudaSuccess) return err;
-    return fit_tile(cc_kernel<3>, 3, R, C, &max_tile[3]);
+    err = fit_tile(cc_kernel<2>, device, 2, R, C, kSmemSlots, &max_tile[2]);
+    if (err != cudaSuccess) return err;
+    return fit_tile(cc_kernel<3>, device, 3, R, C, kSmemSlots, &max_tile[3]);
 }
 
 const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel", "scatter_kernel", "cc_kernel",
@@ -1333,6 +1346,8 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     const size_t cc_smem = cc_smem_bytes(L.g.R, L.g.C, L.tune.tile_slots);
     if (L.tune.blocks_per_sm >= 3)
         cc_kernel<3><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
+    else if (L.tune.blocks_per_sm == 1)
+        cc_kernel<1><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
     else
         cc_kernel<2><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
     ++nk;

@@ -494,20 +494,21 @@ Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N)
 
 bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t)
 {
-    if (t.blocks_per_sm != 2 && t.blocks_per_sm != 3) return false;
+    if (t.blocks_per_sm < 1 || t.blocks_per_sm > 3) return false;
     if (t.tile_slots < 256 || t.tile_slots > ctx->max_tile[t.blocks_per_sm] || t.tile_slots % 256) return false;
     if (t.ticket_max != 2 && t.ticket_max != 4 && t.ticket_max != 8 && t.ticket_max != 16) return false;
     return t.warp_max == 32 || t.warp_max == 64;
 }
 
 // The autotuner's search space on this device: the default tile at two
-// resident blocks per SM and the largest tile that keeps three resident,
-// each with tickets of 16, 8, 4 or 2 items and a warp tier up to 64 or 32 digis.
+// resident blocks per SM, the largest tile that keeps three resident, and
+// the largest tile of a single block, each with tickets of 16, 8, 4 or 2
+// items and a warp tier up to 64 or 32 digis.
 std::vector<hp::Tuning> tuning_candidates(const hp_ctx *ctx)
 {
     std::vector<hp::Tuning> c;
-    for (uint32_t b = 2; b <= 3; ++b) {
-        const uint32_t tile = b == 2 ? (uint32_t)hp::kSmemSlots : ctx->max_tile[3];
+    for (uint32_t b = 1; b <= 3; ++b) {
+        const uint32_t tile = b == 2 ? (uint32_t)hp::kSmemSlots : ctx->max_tile[b];
         if (tile < 256) continue;
         for (uint32_t tk : {16u, 8u, 4u, 2u})
             for (uint32_t wm : {64u, 32u}) {
