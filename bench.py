@@ -70,6 +70,9 @@ def _args():
     p.add_argument("--serving-events", type=int, default=2000, help="requests per serving rate")
     p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
     p.add_argument("--e2e-depth", type=int, default=2, help="batches in flight in the end-to-end measurement")
+    p.add_argument("--tuning", default="",
+                   help="tile_slots,blocks_per_sm,ticket_items,warp_max: use these clustering settings instead of "
+                        "autotuning (for profiler captures of one configuration)")
     p.add_argument("--serving-inflight", type=int, default=0, help="serving batches in flight (0: library default)")
     p.add_argument("--serving-profile", action="store_true",
                    help="diagnostic: stage timers on every serving batch (summed kernel time)")
@@ -319,10 +322,15 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
 
     # autotuner: pick the clustering kernel's settings for this launch shape
-    tuned, tuned_ms, cand_ms = ctx.autotune(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
-                                            reps=3)
-    tuning = {"chosen": tuned, "candidates": [dict(c, ms=round(m, 4)) for c, m in
-                                              zip(ctx.tuning_candidates(), cand_ms)]}
+    if a.tuning:
+        keys = ("tile_slots", "blocks_per_sm", "ticket_items", "warp_max")
+        ctx.set_tuning(E, N, dict(zip(keys, (int(x) for x in a.tuning.split(",")))))
+        tuning = {"chosen": ctx.get_tuning(E, N), "candidates": "not searched (--tuning)"}
+    else:
+        tuned, tuned_ms, cand_ms = ctx.autotune(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(),
+                                                out, reps=3)
+        tuning = {"chosen": tuned, "candidates": [dict(c, ms=round(m, 4)) for c, m in
+                                                  zip(ctx.tuning_candidates(), cand_ms)]}
 
     # device-resident timed region: the pass captured once in a CUDA graph, replayed per step
     graph = ctx.graph_capture(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out)
@@ -576,7 +584,9 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
                         "submit_us_per_request": (s1["serve_submit_ns"] - s0["serve_submit_ns"]) / n_requests / 1e3,
                         "admitter_busy": (s1["serve_launch_ns"] - s0["serve_launch_ns"]) / 1e9 / span,
                         "completion_busy": (s1["serve_complete_ns"] - s0["serve_complete_ns"]) / 1e9 / span,
-                        "kernel_busy": (sum(v[1] for v in prof.values()) / 1e3 / span) if profile else None})
+                        "kernel_busy": (sum(v[1] for v in prof.values()) / 1e3 / span) if profile else None,
+                        "pool_backend_allocs": (s1["device_mallocs"] + s1["host_mallocs"]) -
+                                               (s0["device_mallocs"] + s0["host_mallocs"])})
         stats = ctx.stats()
         ctx.serve_stop()
     return {"workload": f"serving: lognormal sizes (median 80k, sigma 0.8, cap 500k), pool of {pool_events} "
