@@ -550,8 +550,14 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
     Returns per-rate sustained events/s and p50/p99 submit-to-callback latency."""
     from paper_2004_04334_gb300 import hp
 
+    import torch
+
     w = synth.workload("serving", n_events=pool_events)
     pool = [w.event(e) for e in range(w.n_events)]
+    if nocopy:  # the data source's buffers: pinned, read by DMA in place
+        pinned = [(torch.from_numpy(a.view(np.int32).copy()).pin_memory(),
+                   torch.from_numpy(b.view(np.int16).copy()).pin_memory()) for a, b in pool]
+        pool = [(a.numpy().view(np.uint32), b.numpy().view(np.uint16)) for a, b in pinned]
     out = []
     with hp.Context(w.n_modules, w.gain, w.pedestal, device=local, want_labels=True, n_streams=4) as ctx:
         tuned = pretune_batches(ctx, w, local)

@@ -483,8 +483,9 @@ hp_status hp_serve_stop(hp_ctx *ctx);
  * threads replay a schedule of n_requests arrivals.  Request i arrives
  * arrival_ns[i] after the start (non-decreasing per thread is not required)
  * and submits pool event event_index[i] (pool_words/pool_modules/pool_n, n_pool
- * events, host memory; with HP_INPUT_NOCOPY serving it first copies the pool
- * into one pinned block, as a data source writing to pinned buffers would).  Each completion callback records the request's
+ * events, host memory; with HP_INPUT_NOCOPY serving a pool that is not all
+ * in pinned memory is first copied into one pinned block, as a data source
+ * writing to pinned buffers would provide it).  Each completion callback records the request's
  * submit-to-completion latency in latency_ns[i] and its status in status[i],
  * then releases it.  The call returns when every request has completed;
  * *span_ns is the time from the start to the last completion.  Requires a

@@ -593,6 +593,17 @@ void to_public(const hp::Tuning &t, hp_tuning *o)
     o->warp_max = t.warp_max;
 }
 
+// Page-locked host memory (cudaHostAlloc or registered).
+bool pinned_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 bool device_pointer(const void *p)
 {
     cudaPointerAttributes a;
@@ -2156,7 +2167,10 @@ hp_status hp_serve_replay(hp_ctx *ctx, uint32_t n_threads, uint64_t n_requests, 
     std::vector<const uint32_t *> pw(pool_words, pool_words + n_pool);
     std::vector<const uint16_t *> pm(pool_modules, pool_modules + n_pool);
     void *pinned = nullptr;
-    if (nocopy) {
+    bool copy_pool = false; // a pool the caller already keeps in pinned memory is used as it is
+    for (uint32_t e = 0; nocopy && e < n_pool && !copy_pool; ++e)
+        copy_pool = pool_n[e] && (!pinned_host(pool_words[e]) || !pinned_host(pool_modules[e]));
+    if (copy_pool) {
         size_t total = 0;
         for (uint32_t e = 0; e < n_pool; ++e) total += align_up(4 * pool_n[e], 256) + align_up(2 * pool_n[e], 256);
         if (cudaHostAlloc(&pinned, std::max<size_t>(total, 256), cudaHostAllocPortable) != cudaSuccess) {
