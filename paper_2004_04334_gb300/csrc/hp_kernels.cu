@@ -13,27 +13,31 @@
 //   scatter_kernel  bucket scatter: each digi's word and in-event index go to
 //                   its item's bucket (block-local ranks in shared memory,
 //                   one global atomic per non-empty bin to reserve a range)
-//   cc_kernel       persistent clustering: blocks take tickets of kGroup
-//                   consecutive items; items of <= 32 digis are clustered by
-//                   one warp in registers, larger items by the whole block on
-//                   a shared-memory pixel bitmap with rank-addressed
-//                   union-find (items beyond the shared-memory capacity keep
-//                   their slot arrays in global scratch); clusters are then
-//                   written in (event, module, id) order through a chained
-//                   scan over the tickets
+//   cc_kernel       persistent clustering: blocks take tickets of up to
+//                   kGroup consecutive items (the count is a tuning
+//                   parameter); small items (up to 32 or 64 digis) are
+//                   clustered by one warp in registers, larger items by the
+//                   whole block on a shared-memory pixel bitmap with
+//                   rank-addressed union-find (items beyond the tile keep
+//                   their slot arrays in global scratch); kept clusters are
+//                   staged per item and written in (event, module, id) order
+//                   once their ticket's prefix is known (a cooperative
+//                   frontier over the tickets' cluster counts)
 //   finalize_kernel per-event status codes
 //
 // Clustering of one module (block tier): set a bit per digi in an occupancy
 // bitmap (a bit already set is a duplicate) and a bit per surviving pixel in
 // a survivor bitmap; an exclusive prefix popcount over the survivor bitmap
 // gives every surviving pixel a dense slot = its rank in row-major order, so
-// slot order is linear-pixel order.  Each surviving pixel unions with its
-// surviving backward 8-neighbours (left, and the three above) by atomicMin
-// linking of roots (smaller slot wins), so every root is the smallest slot,
-// i.e. the smallest linear index, of its cluster.  Charges, pixel counts and
-// moments relative to the root pixel accumulate in 64-bit integers; the
-// ordinal of a kept cluster is the rank of its root among kept roots in slot
-// order, so the per-module output is already sorted by id.
+// slot order is linear-pixel order.  Every pixel starts linked to the first
+// pixel of its horizontal run; runs of adjacent rows that touch (8-adjacency)
+// are joined by atomicMin linking of roots (smaller slot wins), so every root
+// is the smallest slot, i.e. the smallest linear index, of its cluster.
+// Charge and pixel count accumulate per root in one 64-bit word, the two
+// moments sum(q * row), sum(q * col) in 32 bits (an item with a cluster heavy
+// enough to overflow them is re-summed exactly in 64 bits); the ordinal of a
+// kept cluster is the rank of its root among kept roots in slot order, so the
+// per-module output is already sorted by id.
 #include <algorithm>
 #include <climits>
 #include <cstdint>

@@ -11,6 +11,11 @@
 // path once the pools are warm (Sec. 4.1): every buffer comes from a
 // caching pool whose cudaMalloc / cudaHostAlloc calls only happen while it
 // grows.
+//
+// Also here: consumers of a product (hits, transfers) under the stream
+// rules of Sec. 4.2, the device-resident entry and its CUDA-graph form, the
+// autotuner of the clustering kernel's launch parameters, and the
+// continuous-batching serving loop with its native load driver.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
