@@ -519,6 +519,17 @@ hp_status hp_profile_read(hp_ctx *ctx, uint32_t cap, const char **names, double 
  */
 hp_status hp_debug_fail_allocations(hp_ctx *ctx, uint32_t count);
 
+/*
+ * Test hook for failure detection: in the next `count` launches (host or
+ * device entry; not serving batches or graphs captured later) the
+ * clustering kernel keeps one work ticket's cluster count back, so its one
+ * kind of device-side wait (the ordered output's wait for earlier tickets)
+ * expires after its limit of one second instead of completing.  The launch
+ * then ends normally with every event's status HP_ETIMEOUT (results
+ * invalid), and the context stays usable.  Nothing faults or hangs.
+ */
+hp_status hp_debug_expire_waits(hp_ctx *ctx, uint32_t count);
+
 #ifdef __cplusplus
 }
 #endif

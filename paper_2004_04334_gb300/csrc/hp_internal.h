@@ -99,7 +99,13 @@ struct Launch {
     Workspace ws;
     int cc_grid;             // blocks of the clustering kernel
     Tuning tune;
+    uint32_t debug = 0;      // test hooks (kDebug*)
 };
+
+// Test hook: the clustering kernel never publishes ticket 0's cluster count,
+// so the bounded waits of the ordered output expire and the launch reports
+// HP_ETIMEOUT (the wait's limit is one second).
+constexpr uint32_t kDebugWithholdTicket0 = 1u;
 
 // Bytes of one global-tier slot: (Q, npix), two 64-bit and two 32-bit moments,
 // parent, padded to 8-byte multiples so every slot range stays 8-byte aligned.

@@ -49,7 +49,8 @@ namespace hp {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint32_t kSpinLimit = 1u << 24;          // iterations of a blocking wait, at most
+constexpr unsigned long long kWaitNs = 1000000000ull; // and at most one second of it
 
 struct ItemCtx {
     uint32_t e, m, b, n;
@@ -63,6 +64,13 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
@@ -979,8 +987,10 @@ __device__ void advance_frontier(unsigned long long *chain, uint32_t *frontier, 
 
 // Resolve ticket g (one full warp): its exclusive prefix once the frontier
 // has passed it.  Non-blocking mode returns false if it has not; blocking
-// mode keeps pushing the frontier, bounded by kSpinLimit (then kErrTimeout).
-// Every aggregate is published without waiting, so every blocking wait ends.
+// mode keeps pushing the frontier, for at most kSpinLimit iterations and
+// kWaitNs of wall time, then reports kErrTimeout (and every later blocking
+// wait of the launch gives up at once).  Every aggregate is published
+// without waiting, so a blocking wait only expires if one never is.
 __device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uint64_t ngroups, uint64_t g,
                               unsigned long long agg, bool blocking, unsigned long long *excl_out,
                               uint32_t *launch_err)
@@ -988,10 +998,20 @@ __device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uin
     const unsigned long long kFlagInc = 1ull << 63, kMask = (1ull << 62) - 1;
     const uint32_t lane = threadIdx.x & 31;
     const unsigned long long *inc = chain + ngroups;
+    unsigned long long t0 = 0;
     for (uint32_t spins = 0;; ++spins) {
         unsigned long long v = 0;
-        if (lane == 0) v = ld_acquire(&inc[g]);
+        uint32_t failed = 0;
+        if (lane == 0) {
+            v = ld_acquire(&inc[g]);
+            failed = *(volatile uint32_t *)launch_err & kErrTimeout;
+        }
         v = __shfl_sync(kFull, v, 0);
+        failed = __shfl_sync(kFull, failed, 0);
+        if (blocking && failed && !(v & kFlagInc)) {
+            *excl_out = 0;
+            return true;
+        }
         if (!(v & kFlagInc)) {
             advance_frontier(chain, frontier, ngroups);
             if (lane == 0) v = ld_acquire(&inc[g]);
@@ -1002,7 +1022,11 @@ __device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uin
             return true;
         }
         if (!blocking) return false;
-        if (spins > kSpinLimit) {
+        unsigned long long now = 0;
+        if (lane == 0) now = global_ns();
+        now = __shfl_sync(kFull, now, 0);
+        if (spins == 0) t0 = now;
+        if (spins > kSpinLimit || now - t0 > kWaitNs) {
             if (lane == 0) atomicOr(launch_err, kErrTimeout);
             *excl_out = 0;
             return true;
@@ -1133,7 +1157,9 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                         agg += s_K[i];
                     }
                     __threadfence();
-                    st_release(&L.ws.chain[g], kAgg | agg);
+                    // (the test hook kDebugWithholdTicket0 keeps ticket 0's aggregate
+                    // back, so that the blocking waits on it expire)
+                    if (g != 0 || !(L.debug & kDebugWithholdTicket0)) st_release(&L.ws.chain[g], kAgg | agg);
                     ++s_tail;
                 }
                 __syncthreads();

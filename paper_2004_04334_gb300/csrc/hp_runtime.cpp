@@ -251,6 +251,7 @@ struct hp_ctx {
     std::vector<cudaStream_t> aux_streams;
     std::atomic<uint32_t> next_aux{0};
     std::atomic<uint64_t> consumer_reuses{0}, consumer_waits{0};
+    std::atomic<uint32_t> debug_withhold{0}; // hp_debug_expire_waits: launches left to withhold ticket 0
     // captured device passes (hp_graph_capture), destroyed with the context
     std::mutex graph_mu;
     std::set<hp_graph *> graphs;
@@ -495,6 +496,15 @@ Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N)
         if (it != ctx->tuned.end()) t = it->second;
     }
     return shape_with(ctx, E, t);
+}
+
+// Test hooks for the next launch (hp_debug_expire_waits).
+uint32_t take_debug(hp_ctx *ctx)
+{
+    uint32_t n = ctx->debug_withhold.load();
+    while (n > 0 && !ctx->debug_withhold.compare_exchange_weak(n, n - 1)) {
+    }
+    return n > 0 ? hp::kDebugWithholdTicket0 : 0u;
 }
 
 bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t)
@@ -826,6 +836,7 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, sh.tune, &L.ws);
     L.cc_grid = grid;
     L.tune = sh.tune;
+    L.debug = take_debug(ctx);
 
     const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
     cudaStream_t s = ctx->streams[si];
@@ -1307,7 +1318,8 @@ hp_status check_device_args(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, co
 // Queue one device-resident pass with its scratch at `base`.
 cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
                         const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
-                        const Shape &sh, void *base, cudaStream_t s, uint64_t *nk, cudaEvent_t *marks)
+                        const Shape &sh, void *base, cudaStream_t s, uint64_t *nk, cudaEvent_t *marks,
+                        uint32_t debug = 0)
 {
     hp::Launch L;
     L.g = geometry(ctx);
@@ -1330,6 +1342,7 @@ cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const 
                         &L.ws);
     L.cc_grid = sh.grid;
     L.tune = sh.tune;
+    L.debug = debug;
     return hp::launch_reconstruct(L, s, nk, marks);
 }
 
@@ -1849,7 +1862,7 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
     }
     uint64_t nk = 0;
     if (device_pass(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, sh, base, s, &nk,
-                    profile_marks(ctx)) != cudaSuccess) {
+                    profile_marks(ctx), take_debug(ctx)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx);
     }
@@ -2304,6 +2317,13 @@ hp_status hp_profile_read(hp_ctx *ctx, uint32_t cap, const char **names, double 
         if (total_ms) total_ms[i] = ms[i];
         if (launches) launches[i] = cnt[i];
     }
+    return HP_OK;
+}
+
+hp_status hp_debug_expire_waits(hp_ctx *ctx, uint32_t count)
+{
+    if (!ctx) return HP_EINVAL;
+    ctx->debug_withhold.store(count);
     return HP_OK;
 }
 

@@ -33,7 +33,8 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_profile_enable", "hp_profile_read", "hp_debug_fail_allocations", "hp_serve_start", "hp_submit",
            "hp_serve_stop", "hp_serve_replay", "hp_set_geometry", "hp_enqueue_hits", "hp_fetch_hits",
            "hp_hits_device", "hp_graph_capture", "hp_graph_launch", "hp_graph_destroy", "hp_tuning_candidates",
-           "hp_get_tuning", "hp_set_tuning", "hp_autotune", "hp_event_device_clusters", "hp_enqueue_transfer")
+           "hp_get_tuning", "hp_set_tuning", "hp_autotune", "hp_event_device_clusters", "hp_enqueue_transfer",
+           "hp_debug_expire_waits")
 
 
 class HPError(RuntimeError):
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH):
             "hp_profile_enable": (I, [V, U32]),
             "hp_profile_read": (I, [V, U32, P(ctypes.c_char_p), P(ctypes.c_double), P(U64), P(U32)]),
             "hp_debug_fail_allocations": (I, [V, U32]),
+            "hp_debug_expire_waits": (I, [V, U32]),
             "hp_serve_start": (I, [V, P(ServeConfig)]),
             "hp_submit": (I, [V, V, V, U64, U64, V, V, P(V)]),
             "hp_serve_stop": (I, [V]),
@@ -519,6 +521,10 @@ class Context:
     def serve_stop(self):
         """Launch what is queued and wait for every batch."""
         _check(self._lib.hp_serve_stop(self._h), "hp_serve_stop")
+
+    def debug_expire_waits(self, count: int):
+        """Test hook: the next `count` launches let their bounded device wait expire (HP_ETIMEOUT)."""
+        _check(self._lib.hp_debug_expire_waits(self._h, count), "hp_debug_expire_waits")
 
     def debug_fail_allocations(self, count: int):
         _check(self._lib.hp_debug_fail_allocations(self._h, count), "hp_debug_fail_allocations")
