@@ -33,10 +33,26 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
-def test_library_targets_sm103a(lib):
-    # the fatbin carries sm_103a code: the arch string is in the cubin's ELF header notes
-    data = open(hp.LIB_PATH, "rb").read()
-    assert b"sm_103a" in data or b"sm_103" in data
+def test_library_is_built_for_sm103a_only():
+    # one -gencode, for sm_103a (checked on the build command, not the binary)
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _declared_arity():
+    src = open(os.path.join(ROOT, "include", "hp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(hp_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    arity = _declared_arity()
+    assert set(arity) == set(hp.EXPORTS)
+    for name, n in arity.items():
+        assert len(getattr(lib, name).argtypes) == n, name
 
 
 def test_status_strings(lib):
