@@ -190,8 +190,8 @@ def kernel_bytes(name, n_digis, n_events, n_modules, n_clusters):
         return 6 * n_digis
     if name == "cc_kernel":
         return 4 * n_digis + 24 * n_clusters + 8 * n_modules * n_events
-    if name == "fused_kernel":
-        return algorithmic_bytes(n_digis, n_events, n_modules, n_clusters)
+    if name == "hits_kernel":
+        return 24 * n_clusters + 48 * n_modules + 8 * (n_events + 1)
     return 0
 
 
