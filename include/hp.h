@@ -147,6 +147,14 @@ typedef struct hp_device_clusters {
     int32_t *label;            /* [n_digis] or NULL (labels not computed) */
 } hp_device_clusters;
 
+/* Launch settings of the clustering kernel (see hp_autotune). */
+typedef struct hp_tuning {
+    uint32_t tile_slots;
+    uint32_t blocks_per_sm;
+    uint32_t ticket_items;
+    uint32_t warp_max;
+} hp_tuning;
+
 /* Counters of the context (monotonic unless stated). */
 typedef struct hp_stats {
     uint64_t device_mallocs;    /* cudaMalloc calls made by the caching pool */
@@ -246,6 +254,28 @@ hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *view);
  */
 hp_status hp_release_event(hp_event *ev);
 
+/*
+ * Provenance (Sec. 3: the framework records, per event, on which technology
+ * a product was made): the device (name, ordinal, compute capability), the
+ * library build, the path that made the product and, for clustering
+ * products, the clustering kernel's settings (hp_tuning) it ran with.
+ * Valid until hp_release_event; makes no CUDA call.
+ */
+#define HP_PATH_EVENT 1u    /* hp_enqueue_event */
+#define HP_PATH_BATCH 2u    /* hp_enqueue_batch */
+#define HP_PATH_SERVING 3u  /* a serving request (hp_submit) */
+#define HP_PATH_HITS 4u     /* hp_enqueue_hits */
+#define HP_PATH_TRANSFER 5u /* hp_enqueue_transfer */
+typedef struct hp_provenance {
+    char device_name[64];
+    int device;
+    int cc_major, cc_minor;
+    const char *library; /* static string */
+    uint32_t path;       /* HP_PATH_* */
+    hp_tuning tuning;    /* zero for hits and transfer products */
+} hp_provenance;
+hp_status hp_event_provenance(const hp_event *ev, hp_provenance *out);
+
 /* Product<T> metadata (Sec. 4.2): device ordinal, producing stream
  * (cudaStream_t) and the CUDA event recorded after the work. */
 int hp_event_device(const hp_event *ev);
@@ -328,12 +358,6 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
  * Errors: as hp_reconstruct_device; hp_set_tuning returns HP_EINVAL for a
  * setting outside the candidates' ranges (t == NULL clears the bucket).
  */
-typedef struct hp_tuning {
-    uint32_t tile_slots;
-    uint32_t blocks_per_sm;
-    uint32_t ticket_items;
-    uint32_t warp_max;
-} hp_tuning;
 hp_status hp_tuning_candidates(hp_ctx *ctx, uint32_t cap, hp_tuning *list, uint32_t *n);
 hp_status hp_get_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, hp_tuning *out);
 hp_status hp_set_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const hp_tuning *t);

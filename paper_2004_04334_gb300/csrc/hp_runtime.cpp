@@ -191,6 +191,9 @@ class Pool {
 // event's outputs.  Every change is one atomic read-modify-write of this
 // word; the change that makes the event destroyable (complete, callback run,
 // released, no consumer left) is the one that frees it, exactly once.
+// Build identifier reported in the provenance of every product.
+constexpr const char *kLibraryId = "libhp 1 (sm_103a)";
+
 constexpr uint32_t kDone = 1u, kCbSet = 2u, kCbDone = 4u, kReleaseReq = 8u;
 constexpr uint32_t kHold = 1u << 8;
 
@@ -210,6 +213,7 @@ struct hp_ctx {
     int sm_count = 0;
     uint32_t max_tile[4] = {0, 0, 0, 0}; // largest tile per resident-blocks count (init_kernels)
     char device_name[256] = {0};
+    int cc_major = 0, cc_minor = 0;
     // autotuner (hp_autotune): tuning per launch-shape bucket, optional cache file
     std::mutex tune_mu;
     std::map<std::pair<int, int>, hp::Tuning> tuned;
@@ -284,6 +288,9 @@ struct hp_event {
     hp_callback cb = nullptr;
     void *user = nullptr;
     uint64_t t_enq = 0, t_done = 0;
+    // provenance (Sec. 3): which path made the product, with which clustering settings
+    uint32_t path = 0;
+    hp::Tuning tune_used{};
     // serving requests: the batch that carries the request and its index in it
     bool request = false;
     int32_t status_local = 0;
@@ -837,6 +844,8 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     L.cc_grid = grid;
     L.tune = sh.tune;
     L.debug = take_debug(ctx);
+    ev->path = offsets ? HP_PATH_BATCH : HP_PATH_EVENT;
+    ev->tune_used = sh.tune;
 
     const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
     cudaStream_t s = ctx->streams[si];
@@ -1058,7 +1067,11 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->dev_charge = round_pow2(l.dev_bytes);
     ctx->dev_in_use.fetch_add(b->dev_charge);
     b->refs.store(E + 1);
-    for (hp_event *r : take) r->batch = b;
+    for (hp_event *r : take) {
+        r->batch = b;
+        r->path = HP_PATH_SERVING;
+        r->tune_used = l.sh.tune;
+    }
     unsigned char *hb = static_cast<unsigned char *>(b->host.ptr);
     unsigned char *hd = static_cast<unsigned char *>(b->host.dptr);
     unsigned char *db = static_cast<unsigned char *>(b->dev.ptr);
@@ -1411,8 +1424,11 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
     if (ctx->max_tile[2] < (uint32_t)hp::kSmemSlots) return bail(HP_EINVAL); // the default tile must fit
     {
         cudaDeviceProp prop;
-        if (cudaGetDeviceProperties(&prop, cfg->device) == cudaSuccess)
+        if (cudaGetDeviceProperties(&prop, cfg->device) == cudaSuccess) {
             std::snprintf(ctx->device_name, sizeof ctx->device_name, "%s", prop.name);
+            ctx->cc_major = prop.major;
+            ctx->cc_minor = prop.minor;
+        }
     }
     load_tuning(ctx);
     const size_t M = cfg->n_modules;
@@ -1534,6 +1550,21 @@ hp_status hp_release_event(hp_event *ev)
     return HP_OK;
 }
 
+hp_status hp_event_provenance(const hp_event *ev, hp_provenance *o)
+{
+    if (!ev || !o) return HP_EINVAL;
+    const hp_ctx *ctx = ev->ctx;
+    std::memset(o, 0, sizeof *o);
+    std::snprintf(o->device_name, sizeof o->device_name, "%s", ctx->device_name);
+    o->device = ctx->device;
+    o->cc_major = ctx->cc_major;
+    o->cc_minor = ctx->cc_minor;
+    o->library = kLibraryId;
+    o->path = ev->path;
+    if (ev->path != HP_PATH_HITS && ev->path != HP_PATH_TRANSFER) to_public(ev->tune_used, &o->tuning);
+    return HP_OK;
+}
+
 int hp_event_device(const hp_event *ev) { return ev ? ev->ctx->device : -1; }
 void *hp_event_stream(const hp_event *ev) { return ev ? (void *)ev->stream : nullptr; }
 void *hp_event_cuda_event(const hp_event *ev) { return ev ? (void *)ev->done : nullptr; }
@@ -1611,6 +1642,7 @@ hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
     ev->N = N;
     ev->tag = prod->tag;
     ev->hits = true;
+    ev->path = HP_PATH_HITS;
     if (ctx->hpool.alloc(hoff, &ev->host) != HP_OK) {
         delete ev;
         return HP_ENOMEM;
@@ -1726,6 +1758,7 @@ hp_status hp_enqueue_transfer(hp_event *prod, uint32_t what, hp_event **out)
     ev->N = N;
     ev->tag = prod->tag;
     ev->transfer = true;
+    ev->path = HP_PATH_TRANSFER;
     if (ctx->hpool.alloc(hoff, &ev->host) != HP_OK) {
         delete ev;
         return HP_ENOMEM;

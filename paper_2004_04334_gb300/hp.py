@@ -34,7 +34,7 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_serve_stop", "hp_serve_replay", "hp_set_geometry", "hp_enqueue_hits", "hp_fetch_hits",
            "hp_hits_device", "hp_graph_capture", "hp_graph_launch", "hp_graph_destroy", "hp_tuning_candidates",
            "hp_get_tuning", "hp_set_tuning", "hp_autotune", "hp_event_device_clusters", "hp_enqueue_transfer",
-           "hp_debug_expire_waits")
+           "hp_debug_expire_waits", "hp_event_provenance")
 
 
 class HPError(RuntimeError):
@@ -79,6 +79,15 @@ class Tuning(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class Provenance(ctypes.Structure):
+    _fields_ = [("device_name", ctypes.c_char * 64), ("device", ctypes.c_int), ("cc_major", ctypes.c_int),
+                ("cc_minor", ctypes.c_int), ("library", ctypes.c_char_p), ("path", ctypes.c_uint32),
+                ("tuning", Tuning)]
+
+
+PATHS = {1: "event", 2: "batch", 3: "serving", 4: "hits", 5: "transfer"}
 
 
 class HitsView(ctypes.Structure):
@@ -130,6 +139,7 @@ def load(path: str = LIB_PATH):
             "hp_profile_read": (I, [V, U32, P(ctypes.c_char_p), P(ctypes.c_double), P(U64), P(U32)]),
             "hp_debug_fail_allocations": (I, [V, U32]),
             "hp_debug_expire_waits": (I, [V, U32]),
+            "hp_event_provenance": (I, [V, P(Provenance)]),
             "hp_serve_start": (I, [V, P(ServeConfig)]),
             "hp_submit": (I, [V, V, V, U64, U64, V, V, P(V)]),
             "hp_serve_stop": (I, [V]),
@@ -286,6 +296,14 @@ class Event:
     @property
     def stream(self) -> int:
         return int(self._ctx._lib.hp_event_stream(self._h) or 0)
+
+    def provenance(self) -> dict:
+        """Device, library build, path and clustering settings that made this product."""
+        p = Provenance()
+        _check(self._ctx._lib.hp_event_provenance(self._h, ctypes.byref(p)), "hp_event_provenance")
+        return {"device_name": p.device_name.decode(), "device": p.device, "cc": (p.cc_major, p.cc_minor),
+                "library": p.library.decode() if p.library else "", "path": PATHS.get(p.path, str(p.path)),
+                "tuning": p.tuning.as_dict()}
 
     def fetch(self, copy: bool = True) -> Result:
         """The event's results.  copy=False returns numpy views of the

@@ -93,3 +93,16 @@ def test_null_arguments(lib):
     assert lib.hp_release_event(None) == hp.HP_EINVAL
     assert lib.hp_event_query(None) == hp.HP_EINVAL
     assert lib.hp_get_stats(None, None) == hp.HP_EINVAL
+
+
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header must compile as C on its own
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("no gcc")
+    r = subprocess.run([gcc, "-fsyntax-only", "-std=c11", "-x", "c", os.path.join(ROOT, "include", "hp.h")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
