@@ -182,7 +182,7 @@ typedef struct hp_serve_config {
     size_t device_budget_bytes;    /* device bytes in-flight batches may hold; 0 = no limit */
     uint32_t max_batch_events;     /* requests per batch; 0 = 256 */
     uint64_t max_batch_digis;      /* digis per batch; 0 = 32 Mi */
-    uint32_t max_inflight_batches; /* batches on the device at once; 0 = 2 (one copying while one computes) */
+    uint32_t max_inflight_batches; /* batches on the device at once; 0 = 3 */
     uint32_t max_pending;          /* queued requests before hp_submit says HP_EAGAIN; 0 = 65536 */
     uint32_t flags;                /* HP_WANT_LABELS; HP_INPUT_NOCOPY: hp_submit does not copy the inputs,
                                       the batch copies them by DMA, so they must stay valid (and should

@@ -1166,7 +1166,7 @@ void admitter_main(hp_ctx *ctx, Serve *sv)
     cudaSetDevice(ctx->device);
     const uint32_t max_events = sv->cfg.max_batch_events ? sv->cfg.max_batch_events : 256;
     const uint64_t max_digis = sv->cfg.max_batch_digis ? sv->cfg.max_batch_digis : (32ull << 20);
-    const uint32_t max_batches = sv->cfg.max_inflight_batches ? sv->cfg.max_inflight_batches : 2;
+    const uint32_t max_batches = sv->cfg.max_inflight_batches ? sv->cfg.max_inflight_batches : 3;
     const size_t budget = sv->cfg.device_budget_bytes;
     const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
     for (;;) {
