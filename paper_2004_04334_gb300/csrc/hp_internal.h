@@ -2,12 +2,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 struct hp_ctx;
 
 namespace hp {
+
+// NVTX range around a host-side stage (visible to Nsight tools, e.g.
+// `ncu --nvtx`; costs nothing measurable when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Error bits accumulated on the device (per event, and per launch).
 constexpr uint32_t kErrBadDigi = 1u;

@@ -1352,6 +1352,7 @@ const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel", "sc
 
 cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count, cudaEvent_t *marks)
 {
+    NvtxRange range("hp_launch_reconstruct");
     cudaError_t err = cudaMemsetAsync(L.ws.ctl, 0, L.ws.zero_bytes, stream);
     if (err != cudaSuccess) return err;
     auto mark = [&](int i) {

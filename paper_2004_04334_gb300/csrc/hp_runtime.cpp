@@ -660,6 +660,7 @@ cudaEvent_t *profile_marks(hp_ctx *ctx)
 hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_t n_single, const uint32_t *words,
                        const uint16_t *mods, uint64_t tag, uint32_t flags, hp_event **out)
 {
+    hp::NvtxRange range("hp_enqueue");
     if (!ctx || !out) return HP_EINVAL;
     if (ctx->failed.load()) return HP_ECUDA;
     if (E < 1) return HP_EINVAL;
@@ -1033,6 +1034,7 @@ BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
 
 void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
 {
+    hp::NvtxRange range("hp_serve_batch");
     const uint32_t E = (uint32_t)take.size();
     const uint64_t t_start = now_ns();
     uint64_t N = 0;
@@ -1615,6 +1617,7 @@ hp_status hp_set_geometry(hp_ctx *ctx, const float *origin, const float *rot, fl
 
 hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
 {
+    hp::NvtxRange range("hp_enqueue_hits");
     if (!prod || !out || flags != 0) return HP_EINVAL;
     if (prod->request || prod->hits || prod->transfer) return HP_EINVAL;
     hp_ctx *ctx = prod->ctx;
@@ -1729,6 +1732,7 @@ hp_status hp_event_device_clusters(hp_event *ev, hp_device_clusters *v)
 
 hp_status hp_enqueue_transfer(hp_event *prod, uint32_t what, hp_event **out)
 {
+    hp::NvtxRange range("hp_enqueue_transfer");
     if (!prod || !out) return HP_EINVAL;
     if (!prod->on_device || prod->hits || prod->transfer || prod->request) return HP_EINVAL;
     if (what == 0 || (what & ~(uint32_t)(HP_TRANSFER_CLUSTERS | HP_TRANSFER_LABELS))) return HP_EINVAL;
@@ -1942,6 +1946,7 @@ hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const ui
                       const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out,
                       uint32_t reps, uint32_t cap, double *cand_ms, hp_tuning *best, double *best_ms)
 {
+    hp::NvtxRange range("hp_autotune");
     hp_status st = check_device_args(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out);
     if (st != HP_OK) return st;
     if (reps < 1) reps = 1;

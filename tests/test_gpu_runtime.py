@@ -227,3 +227,30 @@ def test_product_metadata(tiny):
         ev.wait(30)
         assert ev.latency_ns > 0
         ev.release()
+
+
+def test_labels_cross_the_link_only_when_asked(tiny):
+    """D2H on demand (Sec. 4.3): without HP_WANT_LABELS no label bytes are copied."""
+    N = tiny.n_digis
+    with _ctx(tiny) as ctx:
+        d0 = ctx.stats()["d2h_bytes"]
+        ev = ctx.enqueue_batch(tiny.words, tiny.modules, tiny.offsets)
+        assert ev.wait(30) == hp.HP_OK and ev.fetch().label is None
+        ev.release()
+        d1 = ctx.stats()["d2h_bytes"]
+        assert d1 == d0
+        ev = ctx.enqueue_batch(tiny.words, tiny.modules, tiny.offsets, flags=hp.HP_WANT_LABELS)
+        assert ev.wait(30) == hp.HP_OK and ev.fetch().label is not None
+        ev.release()
+        assert ctx.stats()["d2h_bytes"] - d1 == 4 * N
+
+
+def test_events_in_flight_use_different_streams(tiny):
+    """One stream per event in flight (Sec. 4.1): consecutive enqueues take
+    different streams of the pool, so their copies and kernels may overlap."""
+    with _ctx(tiny, n_streams=4) as ctx:
+        evs = [ctx.enqueue_batch(tiny.words, tiny.modules, tiny.offsets) for _ in range(4)]
+        assert len({ev.stream for ev in evs}) == 4
+        for ev in evs:
+            assert ev.wait(30) == hp.HP_OK
+            ev.release()
