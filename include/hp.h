@@ -211,7 +211,8 @@ hp_status hp_destroy(hp_ctx *ctx);
  * may reuse them at once.  The call queues the host-to-device copy, the
  * kernels, the device-to-host transfer and a completion callback on one
  * stream of the pool and returns without waiting for the device.
- * flags: HP_WANT_LABELS, HP_INPUT_NOCOPY (ORed with hp_config.flags).
+ * flags: HP_WANT_LABELS, HP_INPUT_NOCOPY, HP_KEEP_ON_DEVICE (ORed with
+ * hp_config.flags).
  * Errors: HP_EINVAL (NULL pointers with n_digis > 0, n_digis >= 2^32 - 1),
  * HP_EAGAIN (budget or in-flight limit), HP_ENOMEM, HP_ECUDA.
  */
@@ -243,14 +244,19 @@ hp_status hp_event_query(hp_event *ev);
 /*
  * produce() (Sec. 2): fill *view with the event's results.  HP_ENOTREADY if
  * the event has not completed; otherwise returns the event's status (the
- * view is filled in every case once complete).  Makes no CUDA call.
+ * view is filled in every case once complete).  Works on clusters events of
+ * the host path, serving requests and transfer events (arrays a transfer
+ * did not carry are NULL); HP_EINVAL for hits events and for events kept on
+ * the device (HP_KEEP_ON_DEVICE).  Makes no CUDA call.
  */
 hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *view);
 
 /*
  * Return the event's buffers to the pool.  Before completion the release is
- * deferred until the event completes (after its callback).  The event
- * pointer and its views are invalid afterwards.  Makes no CUDA call.
+ * deferred until the event completes (after its callback), and while
+ * consumers (hits, transfers) still read its outputs, until they have run.
+ * The event pointer and its views are invalid afterwards.  Makes no CUDA
+ * call.
  */
 hp_status hp_release_event(hp_event *ev);
 
