@@ -114,3 +114,22 @@ def test_provenance_of_products(torch_cuda):
         assert pr["path"] == "serving" and pr["tuning"]["tile_slots"] > 0
         r.release()
         ctx.serve_stop()
+
+
+def test_destroy_with_unreleased_products_and_consumers(torch_cuda):
+    """hp_destroy drains and frees products whose consumers (hits, transfers)
+    were never released, in any state."""
+    w = synth.workload("full", n_events=2)
+    ctx = _ctx(w)
+    ev = ctx.enqueue_batch(w.words, w.modules, w.offsets)
+    h = ev.hits()
+    kept = ctx.enqueue_batch(w.words, w.modules, w.offsets, flags=hp.HP_KEEP_ON_DEVICE | hp.HP_WANT_LABELS)
+    t = kept.transfer(hp.HP_TRANSFER_CLUSTERS | hp.HP_TRANSFER_LABELS)
+    h2 = kept.hits()
+    assert t.wait(60) == hp.HP_OK
+    ctx.close()  # nothing released: everything is drained and freed here
+    # a fresh context on the same device works
+    with _ctx(w) as ctx2:
+        e2 = ctx2.enqueue_batch(w.words, w.modules, w.offsets)
+        assert e2.wait(60) == hp.HP_OK
+        e2.release()
