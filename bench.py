@@ -126,7 +126,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -142,16 +142,16 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:  # noqa: BLE001
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(0.15)
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.12)
         self.proc.terminate()
         try:
             self.proc.wait(5)
@@ -317,6 +317,12 @@ def run_ours(a):
         ctx.reconstruct_device(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
                                stream.cuda_stream)
 
+    # clocks sampled over the device work around the timed region (autotuning,
+    # warm-up, the timed replays, the stage-timed passes and the hits chain):
+    # the timed region alone is shorter than the sampling interval
+    clocks = ClockSampler(local)
+    clocks.start()
+
     # autotuner: pick the clustering kernel's settings for this launch shape (before any
     # other pass, so that every later launch, warm-up included, runs with them)
     if a.tuning:
@@ -347,8 +353,6 @@ def run_ours(a):
         graph.launch(stream.cuda_stream)
     barrier()
     launches0 = ctx.stats()["kernel_launches"]
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -357,7 +361,6 @@ def run_ours(a):
         graph.launch(stream.cuda_stream)
     e1.record(stream)
     barrier()
-    clk = clocks.stop()
     t_dev = e0.elapsed_time(e1) / 1000.0
     gpu_launches = ctx.stats()["kernel_launches"] - launches0
     graph.destroy()
@@ -383,6 +386,7 @@ def run_ours(a):
     shares = {k: round(v[1] / max(1e-12, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
 
     chain = _chain(a, ctx, w, out, n_clusters, dev, stream, step, barrier, world)
+    clk = clocks.stop()
 
     e2e = per_event = serving = None
     if not a.device_only:
