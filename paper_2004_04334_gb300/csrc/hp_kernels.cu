@@ -73,15 +73,23 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Exclusive scan of one value per thread over a block of T threads.
+// Exclusive scan of one value per thread over a block of T threads with a
+// single barrier: warp scans, then every warp scans the warp totals in
+// registers.  tmp must not be rewritten before the caller's next barrier.
 template <int T>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t *total)
 {
+    static_assert(T / 32 <= 32, "one warp scans the warp totals");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -91,22 +99,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
     }
     if (lane == 31) tmp[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        const uint32_t wv = lane < T / 32 ? tmp[lane] : 0u;
-        uint32_t ws = wv;
+    const uint32_t wt = lane < T / 32 ? tmp[lane] : 0u;
+    uint32_t ws = wt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, ws, o);
-            if (lane >= o) ws += y;
-        }
-        if (lane < T / 32) tmp[lane] = ws - wv;
-        if (lane == T / 32 - 1) tmp[T / 32] = ws;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, ws, o);
+        if (lane >= o) ws += y;
     }
-    __syncthreads();
-    const uint32_t r = tmp[warp] + x - v;
-    *total = tmp[T / 32];
-    __syncthreads();
-    return r;
+    *total = __shfl_sync(kFull, ws, T / 32 - 1);
+    return __shfl_sync(kFull, ws - wt, warp) + x - v;
 }
 
 // s / Q as a float offset, with s an exact integer moment: exact operands and
@@ -769,38 +770,47 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     // U's run; a run head whose U is empty checks its upper-left pixel, a run
     // tail whose U is empty its upper-right one.  Every 8-adjacency between
     // two runs passes through one of these.  The lanes of a warp walk the
-    // item in step and union in lockstep.
-    for (uint32_t k0 = tid - lane; k0 < n; k0 += kCCThreads) {
-        const uint32_t k = k0 + lane;
-        uint32_t s = 0, nb0 = kNoSlot, nb1 = kNoSlot;
-        if (k < n) {
-            const uint32_t w = __ldg(bw + k);
-            const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
-            if (r > 0 && has_bit(sbits, lin)) {
-                s = rank_of(sbits, spre, lin);
-                const uint32_t up = lin - C;
-                const bool head = c == 0 || !has_bit(sbits, lin - 1);
-                const bool tail = c + 1 == C || !has_bit(sbits, lin + 1);
-                const bool ul = c > 0 && has_bit(sbits, up - 1);
-                if (has_bit(sbits, up)) {
-                    if (head || !ul) nb0 = rank_of(sbits, spre, up);
-                } else {
-                    if (head && ul) nb0 = rank_of(sbits, spre, up - 1);
-                    if (tail && c + 1 < C && has_bit(sbits, up + 1)) nb1 = rank_of(sbits, spre, up + 1);
+    // item in step, two digis a lane (64 consecutive digis a warp), and union
+    // the pairs of both in one lockstep round.
+    for (uint32_t k0 = 2 * (tid - lane); k0 < n; k0 += 2 * kCCThreads) {
+        uint32_t s[2] = {0u, 0u}, nb0[2] = {kNoSlot, kNoSlot}, nb1[2] = {kNoSlot, kNoSlot};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t k = k0 + 32 * h + lane;
+            if (k < n) {
+                const uint32_t w = __ldg(bw + k);
+                const uint32_t r = w & 0xFFu, c = (w >> 8) & 0x1FFu, lin = r * C + c;
+                if (r > 0 && has_bit(sbits, lin)) {
+                    s[h] = rank_of(sbits, spre, lin);
+                    const uint32_t up = lin - C;
+                    const bool head = c == 0 || !has_bit(sbits, lin - 1);
+                    const bool tail = c + 1 == C || !has_bit(sbits, lin + 1);
+                    const bool ul = c > 0 && has_bit(sbits, up - 1);
+                    if (has_bit(sbits, up)) {
+                        if (head || !ul) nb0[h] = rank_of(sbits, spre, up);
+                    } else {
+                        if (head && ul) nb0[h] = rank_of(sbits, spre, up - 1);
+                        if (tail && c + 1 < C && has_bit(sbits, up + 1)) nb1[h] = rank_of(sbits, spre, up + 1);
+                    }
                 }
             }
         }
         // gather the warp's union pairs onto consecutive lanes, then union them
-        const uint32_t m0 = __ballot_sync(kFull, nb0 != kNoSlot);
-        const uint32_t m1 = __ballot_sync(kFull, nb1 != kNoSlot);
-        const uint32_t n0 = __popc(m0), total = n0 + __popc(m1);
+        const uint32_t m00 = __ballot_sync(kFull, nb0[0] != kNoSlot), m01 = __ballot_sync(kFull, nb1[0] != kNoSlot);
+        const uint32_t m10 = __ballot_sync(kFull, nb0[1] != kNoSlot), m11 = __ballot_sync(kFull, nb1[1] != kNoSlot);
+        const uint32_t e0 = __popc(m00), e1 = e0 + __popc(m01), e2 = e1 + __popc(m10), total = e2 + __popc(m11);
         for (uint32_t base = 0; base < total; base += 32) {
             const uint32_t p = base + lane;
-            const bool from0 = p < n0;
-            const uint32_t src = p < total ? __fns(from0 ? m0 : m1, 0, (int)(from0 ? p : p - n0) + 1) : 0u;
-            const uint32_t a = __shfl_sync(kFull, s, src);
-            const uint32_t b0 = __shfl_sync(kFull, nb0, src), b1 = __shfl_sync(kFull, nb1, src);
-            warp_union(t.parent, a, p < total ? (from0 ? b0 : b1) : kNoSlot);
+            const uint32_t seg = p < e0 ? 0u : p < e1 ? 1u : p < e2 ? 2u : 3u;
+            const uint32_t mask = seg == 0 ? m00 : seg == 1 ? m01 : seg == 2 ? m10 : m11;
+            const uint32_t first = seg == 0 ? 0u : seg == 1 ? e0 : seg == 2 ? e1 : e2;
+            const uint32_t src = p < total ? __fns(mask, 0, (int)(p - first) + 1) : 0u;
+            const uint32_t a0 = __shfl_sync(kFull, s[0], src), a1 = __shfl_sync(kFull, s[1], src);
+            const uint32_t b00 = __shfl_sync(kFull, nb0[0], src), b01 = __shfl_sync(kFull, nb1[0], src);
+            const uint32_t b10 = __shfl_sync(kFull, nb0[1], src), b11 = __shfl_sync(kFull, nb1[1], src);
+            const uint32_t a = seg < 2 ? a0 : a1;
+            const uint32_t bb = seg == 0 ? b00 : seg == 1 ? b01 : seg == 2 ? b10 : b11;
+            warp_union(t.parent, a, p < total ? bb : kNoSlot);
         }
     }
     __syncthreads();
@@ -877,30 +887,36 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         }
     }
 
-    // Kept roots in slot order (= id order): one ballot per 32 consecutive
-    // slots (kept into abits, free since the bitmaps were built), an
-    // exclusive scan of their popcounts (into spre, free once the labels are
-    // written), then each kept root writes its record at its ordinal.
+    // Kept roots in slot order (= id order): every warp takes a contiguous
+    // range of 32-slot chunks and ballots them (into abits, free since the
+    // bitmaps were built), one scan of the warp totals gives each warp's
+    // first ordinal, and the warp walks its chunks again in order.
     const uint32_t chunks = (S + 31) >> 5;
     constexpr uint32_t kWarps = kCCThreads / 32;
-    for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+    const uint32_t cpw = (chunks + kWarps - 1) / kWarps;
+    const uint32_t wc0 = min(chunks, warp * cpw), wc1 = min(chunks, wc0 + cpw);
+    uint32_t wrun = 0;
+    for (uint32_t ch = wc0; ch < wc1; ++ch) {
         const uint32_t s = (ch << 5) + lane;
         const bool kept = s < S && (t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) >= cthr;
         const uint32_t bal = __ballot_sync(kFull, kept);
         if (lane == 0) abits[ch] = bal;
+        wrun += __popc(bal);
     }
+    if (lane == 0) bs.scan_tmp[warp] = wrun;
     __syncthreads();
-    const uint32_t cper = (chunks + kCCThreads - 1) / kCCThreads;
-    const uint32_t c0 = min(chunks, tid * cper), c1 = min(chunks, c0 + cper);
-    uint32_t cl = 0;
-    for (uint32_t ch = c0; ch < c1; ++ch) cl += __popc(abits[ch]);
-    uint32_t K;
-    uint32_t crun = block_exclusive_scan<kCCThreads>(cl, bs.scan_tmp, &K);
-    for (uint32_t ch = c0; ch < c1; ++ch) {
-        spre[ch] = crun;
-        crun += __popc(abits[ch]);
+    uint32_t K, woff;
+    {
+        const uint32_t wt = lane < kWarps ? bs.scan_tmp[lane] : 0u;
+        uint32_t ws = wt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, ws, o);
+            if ((int)lane >= o) ws += y;
+        }
+        K = __shfl_sync(kFull, ws, kWarps - 1);
+        woff = __shfl_sync(kFull, ws - wt, warp);
     }
-    __syncthreads();
     auto stage = [&](uint32_t s, uint32_t ord) {
         const unsigned long long qn = t.qn[s];
         const int32_t Q = (int32_t)(qn >> 17);
@@ -926,16 +942,20 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         // compact the kept roots (their slots, by ordinal, into the survivor
         // bitmap's space, free now) so that every lane stages a cluster
         uint16_t *kslot = reinterpret_cast<uint16_t *>(sbits);
-        for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+        uint32_t run = woff;
+        for (uint32_t ch = wc0; ch < wc1; ++ch) {
             const uint32_t bal = abits[ch];
-            if ((bal >> lane) & 1u) kslot[spre[ch] + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((ch << 5) + lane);
+            if ((bal >> lane) & 1u) kslot[run + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((ch << 5) + lane);
+            run += __popc(bal);
         }
         __syncthreads();
         for (uint32_t o = tid; o < K; o += kCCThreads) stage(kslot[o], o);
     } else {
-        for (uint32_t ch = warp; ch < chunks; ch += kWarps) {
+        uint32_t run = woff;
+        for (uint32_t ch = wc0; ch < wc1; ++ch) {
             const uint32_t bal = abits[ch];
-            if ((bal >> lane) & 1u) stage((ch << 5) + lane, spre[ch] + __popc(bal & ((1u << lane) - 1u)));
+            if ((bal >> lane) & 1u) stage((ch << 5) + lane, run + __popc(bal & ((1u << lane) - 1u)));
+            run += __popc(bal);
         }
     }
     return K;
@@ -1156,10 +1176,12 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                         pd.b[i] = s_b[i];
                         agg += s_K[i];
                     }
-                    __threadfence();
-                    // (the test hook kDebugWithholdTicket0 keeps ticket 0's aggregate
-                    // back, so that the blocking waits on it expire)
-                    if (g != 0 || !(L.debug & kDebugWithholdTicket0)) st_release(&L.ws.chain[g], kAgg | agg);
+                    // The aggregate is all that other blocks read of this ticket (its
+                    // clusters are written out by this block), so a relaxed store
+                    // with no fence suffices.  (The test hook kDebugWithholdTicket0
+                    // keeps ticket 0's aggregate back, so that the blocking waits on
+                    // it expire.)
+                    if (g != 0 || !(L.debug & kDebugWithholdTicket0)) st_relaxed(&L.ws.chain[g], kAgg | agg);
                     ++s_tail;
                 }
                 __syncthreads();
