@@ -33,9 +33,11 @@
 // pixel of its horizontal run; runs of adjacent rows that touch (8-adjacency)
 // are joined by atomicMin linking of roots (smaller slot wins), so every root
 // is the smallest slot, i.e. the smallest linear index, of its cluster.
-// Charge and pixel count accumulate per root in one 64-bit word, the two
-// moments sum(q * row), sum(q * col) in 32 bits (an item with a cluster heavy
-// enough to overflow them is re-summed exactly in 64 bits); the ordinal of a
+// Charge, pixel count and the two moments sum(q * row), sum(q * col)
+// accumulate per root with 32-bit shared-memory atomics (the charge always
+// fits, the configuration bounds every cluster's charge; an item with a
+// cluster heavy enough to overflow the moments is re-summed exactly in 64
+// bits; 64-bit shared atomics measured slower); the ordinal of a
 // kept cluster is the rank of its root among kept roots in slot order, so the
 // per-module output is already sorted by id.
 #include <algorithm>
@@ -264,14 +266,16 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const Launch L)
     extern __shared__ uint32_t sh[];
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
+    // the chunk's module ids are loaded before the event search, so that the
+    // two latencies overlap
+    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk, k0 = c0 + (uint64_t)threadIdx.x * kPerThread;
+    uint32_t m[kPerThread], e_of[kPerThread];
+    load_modules(L, k0, min(L.N, c0 + (uint64_t)kChunk), m);
     const ChunkInfo ci = chunk_info(L, s_ev, s_off);
     const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
     const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
     const uint32_t nbins = sub ? ci.nkeys * kHistWarps : ci.nkeys;
     for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) sh[i] = 0;
-    const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
-    uint32_t m[kPerThread], e_of[kPerThread];
-    load_modules(L, k0, ci.c1, m);
     __syncthreads();
     digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
     uint32_t *bins = sub ? sh + warp * ci.nkeys : sh;
@@ -335,15 +339,18 @@ __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
     __shared__ uint32_t s_scan[kHistThreads / 32 + 1];
+    // the chunk's digis are loaded before the event search, so that the two
+    // latencies overlap
+    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk, c1 = min(L.N, c0 + (uint64_t)kChunk);
+    const uint64_t k0 = c0 + (uint64_t)threadIdx.x * kPerThread;
+    uint32_t m[kPerThread], e_of[kPerThread], w[kPerThread], rank[kPerThread];
+    load_modules(L, k0, c1, m);
+    load_words(L, k0, c1, w);
     const ChunkInfo ci = chunk_info(L, s_ev, s_off);
     const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
     const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
     const uint32_t nbins = sub ? ci.nkeys * kHistWarps : ci.nkeys;
     for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) cnt[i] = 0;
-    const uint64_t k0 = ci.c0 + (uint64_t)threadIdx.x * kPerThread;
-    uint32_t m[kPerThread], e_of[kPerThread], w[kPerThread], rank[kPerThread];
-    load_modules(L, k0, ci.c1, m);
-    load_words(L, k0, ci.c1, w);
     __syncthreads();
     digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
     uint32_t *bins = sub ? cnt + warp * ci.nkeys : cnt;
@@ -425,8 +432,9 @@ constexpr int kRing = 16;                    // tickets a block may hold before 
 // items beyond the shared-memory capacity.
 struct Tile {
     uint32_t *parent;          // union-find parent of a slot; kMark | lin for roots after marking
-    unsigned long long *qn;    // root: (Q << 17) + npix
-    int2 *m;                   // root: sum q*(row - root row), sum q*(col - root col)
+    int32_t *q;                // root: charge Q
+    uint32_t *np;              // root: pixel count
+    int2 *m;                   // root: sum q*row, sum q*col
     unsigned long long *exact; // root: the same two moments in 64 bits (heavy clusters only)
 };
 
@@ -666,11 +674,13 @@ __device__ __forceinline__ void for_digis(const uint32_t *bw, uint32_t n, F &&f)
     for (uint32_t k = threadIdx.x; k < n; k += kCCThreads) f(k, __ldg(bw + k));
 }
 
-// Centroid coordinate sum / Q from an exact, non-negative moment: integer
-// quotient plus the remainder fraction, so the float result is within a
-// few ulps whatever the magnitude.
+// Centroid coordinate sum / Q from an exact, non-negative moment: one float
+// division when both are exact in float (the correctly rounded quotient),
+// else integer quotient plus the remainder fraction, so the float result is
+// within a few ulps whatever the magnitude.
 __device__ __forceinline__ float centroid_abs(long long sum, int32_t Q)
 {
+    if (sum < 16777216LL && Q < 16777216) return (float)sum / (float)Q;
     if (sum < 0x80000000LL) {
         const uint32_t su = (uint32_t)sum, qu = (uint32_t)Q;
         const uint32_t qt = su / qu;
@@ -751,6 +761,12 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         spre[i] = run;
         run += __popc(sbits[i]);
     }
+    // the per-root accumulators of every slot, cleared in slot order
+    for (uint32_t s = tid; s < S; s += kCCThreads) {
+        t.q[s] = 0;
+        t.np[s] = 0;
+        t.m[s] = make_int2(0, 0);
+    }
     __syncthreads();
     // every surviving pixel starts in its horizontal run: parent = the run's
     // first pixel, whose slot is the pixel's slot minus its run offset
@@ -759,8 +775,6 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         if (!has_bit(sbits, lin)) return;
         const uint32_t s = rank_of(sbits, spre, lin);
         t.parent[s] = s - run_offset(sbits, lin, r * C);
-        t.qn[s] = 0;
-        t.m[s] = make_int2(0, 0);
     });
     __syncthreads();
 
@@ -832,8 +846,9 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         }
         t.parent[s] = x == s ? (kMark | lin) : x;
         const int32_t q = charge(w);
-        const unsigned long long old = atomicAdd(&t.qn[x], ((unsigned long long)q << 17) | 1ull);
-        if ((int32_t)(old >> 17) + q > kQSafe32) bs.heavy = 1;
+        const int32_t old = atomicAdd(&t.q[x], q);
+        if (old + q > kQSafe32) bs.heavy = 1;
+        atomicAdd(&t.np[x], 1u);
         atomicAdd(&t.m[x].x, q * (int32_t)r);
         atomicAdd(&t.m[x].y, q * (int32_t)c);
     });
@@ -867,7 +882,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
                 const uint32_t p = t.parent[s];
                 const uint32_t x = (p & kMark) ? s : p;
                 const uint32_t px = (p & kMark) ? p : t.parent[x];
-                lab = (int32_t)(t.qn[x] >> 17) >= cthr ? (int32_t)(px & ~kMark) : -2;
+                lab = t.q[x] >= cthr ? (int32_t)(px & ~kMark) : -2;
             }
             return lab;
         };
@@ -898,7 +913,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
     uint32_t wrun = 0;
     for (uint32_t ch = wc0; ch < wc1; ++ch) {
         const uint32_t s = (ch << 5) + lane;
-        const bool kept = s < S && (t.parent[s] & kMark) && (int32_t)(t.qn[s] >> 17) >= cthr;
+        const bool kept = s < S && (t.parent[s] & kMark) && t.q[s] >= cthr;
         const uint32_t bal = __ballot_sync(kFull, kept);
         if (lane == 0) abits[ch] = bal;
         wrun += __popc(bal);
@@ -918,8 +933,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         woff = __shfl_sync(kFull, ws - wt, warp);
     }
     auto stage = [&](uint32_t s, uint32_t ord) {
-        const unsigned long long qn = t.qn[s];
-        const int32_t Q = (int32_t)(qn >> 17);
+        const int32_t Q = t.q[s];
         long long mr, mc;
         if (heavy) {
             mr = (long long)t.exact[2 * s];
@@ -932,7 +946,7 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         StagedCluster o;
         o.id = (int32_t)(t.parent[s] & ~kMark);
         o.charge = Q;
-        o.npix = (int32_t)(qn & 0x1FFFFull);
+        o.npix = (int32_t)t.np[s];
         o.x = centroid_abs(mr, Q);
         o.y = centroid_abs(mc, Q);
         o.pad = 0;
@@ -1076,8 +1090,9 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
     const uint32_t tid = threadIdx.x;
     const uint32_t T = L.tune.tile_slots, warp_max = L.tune.warp_max;
     Tile sm;
-    sm.qn = reinterpret_cast<unsigned long long *>(dsm);
-    sm.m = reinterpret_cast<int2 *>(sm.qn + T);
+    sm.q = reinterpret_cast<int32_t *>(dsm);
+    sm.np = reinterpret_cast<uint32_t *>(sm.q + T);
+    sm.m = reinterpret_cast<int2 *>(sm.np + T);
     sm.parent = reinterpret_cast<uint32_t *>(sm.m + T);
     sm.exact = L.ws.exact + (size_t)blockIdx.x * 2 * T;
     uint32_t *abits = sm.parent + T;
@@ -1156,8 +1171,9 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                         const bool fits = L.ws.big_arena ? (uint64_t)bs.big_off + n <= L.ws.big_slots
                                                          : (uint64_t)min(n, R * C) <= L.ws.big_slots;
                         Tile gt;
-                        gt.qn = reinterpret_cast<unsigned long long *>(base);
-                        gt.exact = gt.qn + cap;
+                        gt.q = reinterpret_cast<int32_t *>(base);
+                        gt.np = reinterpret_cast<uint32_t *>(gt.q + cap);
+                        gt.exact = reinterpret_cast<unsigned long long *>(gt.np + cap);
                         gt.m = reinterpret_cast<int2 *>(gt.exact + 2 * cap);
                         gt.parent = reinterpret_cast<uint32_t *>(gt.m + cap);
                         K = fits ? block_item<true>(L, it, abits, sbits, spre, gt, bs) : 0u;

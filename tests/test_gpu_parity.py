@@ -278,3 +278,38 @@ def test_heavy_cluster_exact_moments(torch_cuda, rows, cols):
     assert ref.charge[0] > 0x7FFFFFFF // 512
     got = run_batch(ctx_for(2, gain, ped), w, m, offs)
     assert_batch_matches(got, ref, offs)
+
+
+def test_duplicates_in_block_tier_items(torch_cuda):
+    """Items of ~1,400 digis (clustered by the whole block): a duplicate of a
+    surviving pixel, of a dropped pixel, and a surviving and a dropped pixel
+    at one position each flag their event HP_EDUP; the other events are
+    unaffected."""
+    base = synth.workload("batched", n_events=4)
+    ws, ms, offs = [], [], [0]
+    for e in range(4):
+        w, m = base.event(e)
+        w, m = w.copy(), m.copy()
+        q = ((w >> 17) & 0xFF).astype(np.int64) * base.gain[m] - base.pedestal[m]
+        if e == 0:
+            i = int(np.flatnonzero(q >= 1000)[0])      # survivor twice
+            extra_w, extra_m = w[i:i + 1], m[i:i + 1]
+        elif e == 1:
+            i = int(np.flatnonzero(q < 1000)[0])       # dropped pixel twice
+            extra_w, extra_m = w[i:i + 1], m[i:i + 1]
+        elif e == 2:
+            i = int(np.flatnonzero(q >= 1000)[0])      # survivor and a dropped pixel (ADC 1) at one position
+            extra_w = (w[i:i + 1] & np.uint32(0x1FFFF)) | np.uint32(1 << 17)
+            extra_m = m[i:i + 1]
+            assert int(base.gain[extra_m[0]]) - int(base.pedestal[extra_m[0]]) < 1000
+        if e < 3:
+            w, m = np.concatenate([w, extra_w]), np.concatenate([m, extra_m])
+        ws.append(w)
+        ms.append(m)
+        offs.append(offs[-1] + len(w))
+    w, m, offs = np.concatenate(ws), np.concatenate(ms), np.asarray(offs, np.uint64)
+    ref = oracle.reconstruct_batch(w, m, offs, base.n_modules, base.gain, base.pedestal)
+    assert ref.event_status.tolist() == [hp.HP_EDUP] * 3 + [0]
+    got = run_batch(ctx_for(base.n_modules, base.gain, base.pedestal), w, m, offs)
+    assert got.event_status.tolist() == [hp.HP_EDUP] * 3 + [0]
+    assert_batch_matches(got, ref, offs)
