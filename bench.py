@@ -301,10 +301,17 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and not a.device_only:
-        ev_s, md_s, dt, cores = cpu_oracle(w)
-        cpu = {"value": ev_s, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"all {E} events ({N} digis) of the {a.workload} workload, one pass, "
-                         f"{cores} threads (one oracle call per event)", "mdigis_per_s": md_s, "seconds": dt}
+        # whole passes over the workload until about 10-15 CPU-seconds of work
+        # (0.75 s of wall time on all host threads), 20 passes at most
+        passes, t_cpu, cores = 0, 0.0, 1
+        while passes < 1 or (t_cpu < 0.75 and passes < 20):
+            _, _, dt, cores = cpu_oracle(w)
+            passes += 1
+            t_cpu += dt
+        cpu = {"value": passes * E / t_cpu, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{passes} passes over all {E} events ({N} digis a pass) of the {a.workload} workload, "
+                         f"{cores} threads (one oracle call per event)",
+               "mdigis_per_s": passes * N / t_cpu / 1e6, "seconds": t_cpu}
 
     ctx = hp.Context(M, w.gain, w.pedestal, device=local, want_labels=True)
     d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
