@@ -445,7 +445,7 @@ struct BlockShared {
     uint32_t scan_tmp[kCCThreads / 32 + 1];
 };
 
-// Find with path halving (each visited node is re-pointed to its
+// Find with path splitting (each visited node is re-pointed to its
 // grandparent).  Parent entries only ever point to a smaller slot of the same
 // tree, so a plain store that races with a link elsewhere leaves a valid
 // ancestor behind; a link that loses such a race is retried by its union.
