@@ -502,30 +502,36 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
         for ev in evs:
             ev.wait(120)
             ev.release()
-    barrier()
-    t0 = time.perf_counter()
-    inflight = []
-    for _ in range(a.steps):
-        inflight.append(ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY))
-        if len(inflight) >= depth:
-            ev = inflight.pop(0)
+    # three timed runs of K steps each (a run is tens of ms of host wall time, so
+    # one scheduling hiccup moves it); the median run is reported
+    runs = []
+    for _ in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        inflight = []
+        for _ in range(a.steps):
+            inflight.append(ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY))
+            if len(inflight) >= depth:
+                ev = inflight.pop(0)
+                ev.wait(120)
+                r = ev.fetch(copy=False)
+                nc, st = r.n_clusters, r.status
+                ev.release()
+        for ev in inflight:
             ev.wait(120)
             r = ev.fetch(copy=False)
             nc, st = r.n_clusters, r.status
             ev.release()
-    for ev in inflight:
-        ev.wait(120)
-        r = ev.fetch(copy=False)
-        nc, st = r.n_clusters, r.status
-        ev.release()
-    barrier()
-    t_e2e = time.perf_counter() - t0
-    assert st == hp.HP_OK and nc == n_clusters
-    t_e2e = max_over_ranks(t_e2e, world, dev)
+        barrier()
+        t_run = time.perf_counter() - t0
+        assert st == hp.HP_OK and nc == n_clusters
+        runs.append(max_over_ranks(t_run, world, dev))
+    t_e2e = sorted(runs)[1]
     e2e = {"value": job_value(E, a.steps, t_e2e, world), "unit": "events/s", "batches_in_flight": depth,
            "h2d_bytes_per_step": 6 * N + 8 * (E + 1),
            "d2h_bytes_per_step": 4 * N + 24 * n_clusters + 8 * (E + 1) + 4 * E,
-           "mdigis_per_s": world * N * a.steps / t_e2e / 1e6}
+           "mdigis_per_s": world * N * a.steps / t_e2e / 1e6,
+           "runs_events_per_s": [job_value(E, a.steps, t, world) for t in runs], "reported": "median of the runs"}
 
     # plain per-event path: one full-size event per launch, one stream
     pe = synth.workload("full")
