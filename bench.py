@@ -192,8 +192,12 @@ def kernel_bytes(name, n_digis, n_events, n_modules, n_clusters):
         return 2 * n_digis
     if name == "scatter_kernel":
         return 6 * n_digis
-    if name == "cc_kernel":
-        return 4 * n_digis + 24 * n_clusters + 8 * n_modules * n_events
+    if name == "cc_kernel":  # labels and calibration (its staged clusters are an intermediate)
+        return 4 * n_digis + 8 * n_modules * n_events
+    if name == "offsets_kernel":  # the per-event cluster offsets
+        return 8 * (n_events + 1)
+    if name == "copy_kernel":  # the cluster records, written once in order, and the event statuses
+        return 24 * n_clusters + 4 * n_events
     if name == "hits_kernel":
         return 24 * n_clusters + 48 * n_modules + 8 * (n_events + 1)
     return 0

@@ -54,11 +54,20 @@ __host__ __device__ inline uint32_t ticket_items(uint64_t EM, unsigned grid, uin
     return g;
 }
 
-// A cluster parked between the clustering phase and the ordered write.
-struct StagedCluster {
-    int32_t id, charge, npix;
-    float x, y;
-    int32_t pad;
+// Clusters parked between the clustering kernel and the ordered write, as
+// structure-of-arrays indexed by bucket position: item i's k-th kept cluster
+// (in id order) sits at boff[i] + k.
+struct Staging {
+    int32_t *id, *charge, *npix;
+    float *x, *y;
+    __device__ __forceinline__ void put(uint64_t at, int32_t id_, int32_t q, int32_t np_, float x_, float y_) const
+    {
+        id[at] = id_;
+        charge[at] = q;
+        npix[at] = np_;
+        x[at] = x_;
+        y[at] = y_;
+    }
 };
 
 struct Geometry {
@@ -75,23 +84,23 @@ struct Outputs {
     float *x, *y;
     uint64_t *cluster_offsets; // [E+1]
     int32_t *label;            // [N] or null
-    int32_t *event_status;     // [E] written by the finalize kernel
+    int32_t *event_status;     // [E] written by copy_kernel
 };
 
 // Scratch of one launch.  The first `zero_bytes` bytes must be zero before
 // the first kernel (one memset): control words, per-event error bits,
 // per-item counts and the chained-scan state.
 struct Workspace {
-    uint32_t *ctl;        // [16]: 0 group ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier
+    uint32_t *ctl;        // [16]: 0 item ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier, 4 offsets chunk ticket
     uint32_t *event_err;  // [E]
-    uint32_t *count;      // [E*M]
-    unsigned long long *chain; // [2 * n_groups]: ticket aggregates, then inclusive prefixes
+    uint32_t *count;      // [E*M] digis of each item; then each item's first output position (offsets_kernel)
+    unsigned long long *chain; // [2 * n_chunks]: offsets_kernel chunk totals, then inclusive prefixes
     size_t zero_bytes;
     uint32_t *boff;       // [E*M] bucket start of each item
-    uint32_t *cursor;     // [E*M] scatter cursor
+    uint32_t *cursor;     // [E*M] scatter cursor; then each item's count of kept clusters (cc_kernel)
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event
-    StagedCluster *staging; // [N]
+    Staging staging;      // [N] each array
     unsigned long long *exact; // [cc_grid * 2 * tile_slots] 64-bit moments of heavy clusters
     unsigned char *big;   // scratch of items too large for shared memory
     uint64_t big_slots;   // slots per block (slab mode) or in total (arena mode)
@@ -112,7 +121,7 @@ struct Launch {
     uint32_t debug = 0;      // test hooks (kDebug*)
 };
 
-// Test hook: the clustering kernel never publishes ticket 0's cluster count,
+// Test hook: offsets_kernel never publishes chunk 0's cluster count,
 // so the bounded waits of the ordered output expire and the launch reports
 // HP_ETIMEOUT (the wait's limit is one second).
 constexpr uint32_t kDebugWithholdTicket0 = 1u;
@@ -132,7 +141,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
 cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4]);
 // Kernels of one launch, in order; marks[i] (if given) is recorded before
 // kernel i and marks[kNumKernels] after the last one.
-constexpr int kNumKernels = 5;
+constexpr int kNumKernels = 6;
 extern const char *const kKernelNames[kNumKernels];
 // Queue the whole reconstruction of one launch on `stream` (memset + kernels).
 cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count,

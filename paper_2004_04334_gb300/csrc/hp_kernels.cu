@@ -23,7 +23,10 @@
 //                   staged per item and written in (event, module, id) order
 //                   once their ticket's prefix is known (a cooperative
 //                   frontier over the tickets' cluster counts)
-//   finalize_kernel per-event status codes
+//   offsets_kernel  each item's first output position (prefix over the items'
+//                   kept-cluster counts, chained across chunks)
+//   copy_kernel     staged clusters to their ordered output positions; per-event
+//                   status codes
 //
 // Clustering of one module (block tier): set a bit per digi in an occupancy
 // bitmap (a bit already set is a duplicate) and a bit per surviving pixel in
@@ -124,17 +127,50 @@ __device__ __forceinline__ float centroid(int32_t origin, long long s, int32_t Q
     return (float)(origin + qt) + (float)rem / (float)Q;
 }
 
-__device__ __forceinline__ ItemCtx make_item(const Launch &L, uint64_t item, uint32_t b, uint32_t n)
+// Event and module of work item `item` (one division, by the thread that
+// sets up the item's record).
+__device__ __forceinline__ void item_coords(uint64_t item, uint32_t M, uint32_t *e, uint32_t *m)
+{
+    if (item <= 0xFFFFFFFFull) {
+        const uint32_t i32 = (uint32_t)item;
+        *e = i32 / M;
+        *m = i32 - *e * M;
+    } else {
+        *e = (uint32_t)(item / M);
+        *m = (uint32_t)(item - (uint64_t)*e * M);
+    }
+}
+
+// Per-item record of a ticket, set up once in shared memory by one thread
+// (the division by the module count and the calibration loads happen there,
+// not in every thread of the block).
+struct ItemRec {
+    uint32_t e, m;
+    int32_t gain, ped;
+    uint64_t label_off; // the event's first digi
+};
+
+__device__ __forceinline__ ItemRec make_rec(const Launch &L, uint64_t item)
+{
+    ItemRec r;
+    item_coords(item, L.g.M, &r.e, &r.m);
+    r.gain = L.g.gain[r.m];
+    r.ped = L.g.ped[r.m];
+    r.label_off = L.offsets[r.e];
+    return r;
+}
+
+__device__ __forceinline__ ItemCtx make_item(const Launch &L, const ItemRec &rec, uint32_t b, uint32_t n)
 {
     ItemCtx it;
-    it.e = (uint32_t)(item / L.g.M);
-    it.m = (uint32_t)(item - (uint64_t)it.e * L.g.M);
+    it.e = rec.e;
+    it.m = rec.m;
     it.b = b;
     it.n = n;
-    it.gain = L.g.gain[it.m];
-    it.ped = L.g.ped[it.m];
-    it.label_e = L.out.label ? L.out.label + L.offsets[it.e] : nullptr;
-    it.err_e = L.ws.event_err + it.e;
+    it.gain = rec.gain;
+    it.ped = rec.ped;
+    it.label_e = L.out.label ? L.out.label + rec.label_off : nullptr;
+    it.err_e = L.ws.event_err + rec.e;
     return it;
 }
 
@@ -426,7 +462,6 @@ constexpr uint32_t kMark = 0x80000000u;
 // |dcol| < 512): they cannot overflow while Q <= INT32_MAX / 512.  Items with
 // a heavier cluster recompute the moments in 64 bits.
 constexpr int32_t kQSafe32 = 0x7FFFFFFF / 512;
-constexpr int kRing = 16;                    // tickets a block may hold before their prefix is known
 
 // Per-item arrays of the block tier: shared memory, or global scratch for
 // items beyond the shared-memory capacity.
@@ -647,14 +682,8 @@ __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (lead[k] && kept[k]) {
-            StagedCluster st;
-            st.id = lab[k];
-            st.charge = Q[k];
-            st.npix = np[k];
-            st.x = centroid(rr[k], Sr[k], Q[k]);
-            st.y = centroid(rc[k], Sc[k], Q[k]);
-            st.pad = 0;
-            L.ws.staging[it.b + ord[k]] = st;
+            L.ws.staging.put(it.b + ord[k], lab[k], Q[k], np[k], centroid(rr[k], Sr[k], Q[k]),
+                             centroid(rc[k], Sc[k], Q[k]));
         }
         if (it.label_e && have[k]) it.label_e[idx[k]] = !surv[k] ? -1 : (kept[k] ? lab[k] : -2);
     }
@@ -943,14 +972,8 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
             mr = mm.x;
             mc = mm.y;
         }
-        StagedCluster o;
-        o.id = (int32_t)(t.parent[s] & ~kMark);
-        o.charge = Q;
-        o.npix = (int32_t)t.np[s];
-        o.x = centroid_abs(mr, Q);
-        o.y = centroid_abs(mc, Q);
-        o.pad = 0;
-        L.ws.staging[it.b + ord] = o;
+        L.ws.staging.put(it.b + ord, (int32_t)(t.parent[s] & ~kMark), Q, (int32_t)t.np[s], centroid_abs(mr, Q),
+                         centroid_abs(mc, Q));
     };
     if (S <= 2 * nwords) {
         // compact the kept roots (their slots, by ordinal, into the survivor
@@ -970,6 +993,382 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
             const uint32_t bal = abits[ch];
             if ((bal >> lane) & 1u) stage((ch << 5) + lane, run + __popc(bal & ((1u << lane) - 1u)));
             run += __popc(bal);
+        }
+    }
+    return K;
+}
+
+// Zero nw words at p (16-byte stores where p is 16-byte aligned).
+__device__ __forceinline__ void clear_words(uint32_t *p, uint32_t nw)
+{
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        uint4 *v = reinterpret_cast<uint4 *>(p);
+        for (uint32_t i = threadIdx.x; i < nw / 4; i += kCCThreads) v[i] = make_uint4(0, 0, 0, 0);
+        done = nw & ~3u;
+    }
+    for (uint32_t i = done + threadIdx.x; i < nw; i += kCCThreads) p[i] = 0;
+}
+
+// Slot of the first pixel of the horizontal run holding surviving pixel lin,
+// whose row starts at linear index row0; word = sbits[lin >> 5] and base =
+// spre[lin >> 5] are passed in (already loaded by the caller).  The run
+// starts one past the nearest non-surviving pixel to the left of lin, or at
+// the row start.
+__device__ __noinline__ uint32_t run_head_slot_far(const uint32_t *sbits, const uint32_t *spre, uint32_t wi,
+                                                   uint32_t row0);
+__device__ __forceinline__ uint32_t run_head_slot(const uint32_t *sbits, const uint32_t *spre, uint32_t lin,
+                                                  uint32_t row0, uint32_t word, uint32_t base)
+{
+    uint32_t wi = lin >> 5;
+    const uint32_t b = lin & 31;
+    uint32_t lo = row0 > (wi << 5) ? row0 - (wi << 5) : 0u; // first bit of the row in this word
+    uint32_t z = ~word & ((1u << b) - 1u) & ~((1u << lo) - 1u);
+    if (z) return base + __popc(word & ((1u << (32 - __clz(z))) - 1u));
+    if ((wi << 5) + lo == row0) return base + __popc(word & ((1u << lo) - 1u));
+    return run_head_slot_far(sbits, spre, wi, row0);
+}
+
+__device__ __noinline__ uint32_t run_head_slot_far(const uint32_t *sbits, const uint32_t *spre, uint32_t wi,
+                                                   uint32_t row0)
+{
+    uint32_t word, lo, z;
+    for (;;) { // the run continues into the previous word (rare)
+        --wi;
+        word = sbits[wi];
+        lo = row0 > (wi << 5) ? row0 - (wi << 5) : 0u;
+        z = ~word & ~((1u << lo) - 1u);
+        if (z) {
+            const uint32_t hb = 32 - __clz(z);
+            return hb == 32 ? spre[wi + 1] : spre[wi] + __popc(word & ((1u << hb) - 1u));
+        }
+        if ((wi << 5) + lo == row0) return spre[wi] + __popc(word & ((1u << lo) - 1u));
+    }
+}
+
+// Lock-free union of the trees of a and b by one thread: the larger root is
+// linked under the smaller with atomicMin; a link that finds its root already
+// linked elsewhere retries from the new parent.
+__device__ __noinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t b)
+{
+    for (;;) {
+        a = uf_find_halving(parent, a);
+        b = uf_find_halving(parent, b);
+        if (a == b) return;
+        if (a < b) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        const uint32_t old = atomicMin(&parent[a], b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// Root reached from slot y (its parent not yet known to be the root).
+__device__ __noinline__ uint32_t root_walk_far(const uint32_t *parent, uint32_t y)
+{
+    const volatile uint32_t *vp = parent;
+    uint32_t p = vp[y];
+    while (p != y && !(p & kMark)) {
+        y = p;
+        p = vp[y];
+    }
+    return y;
+}
+
+// Write kept cluster s (a root of tile t) to the item's staging slot ord.
+__device__ __forceinline__ void stage_cluster(const Launch &L, const ItemCtx &it, const Tile &t, bool heavy,
+                                              uint32_t s, uint32_t ord)
+{
+    const int32_t Q = t.q[s];
+    long long mr, mc;
+    if (heavy) {
+        mr = (long long)t.exact[2 * s];
+        mc = (long long)t.exact[2 * s + 1];
+    } else {
+        const int2 mm = t.m[s];
+        mr = mm.x;
+        mc = mm.y;
+    }
+    L.ws.staging.put(it.b + ord, (int32_t)(t.parent[s] & ~kMark), Q, (int32_t)t.np[s], centroid_abs(mr, Q),
+                     centroid_abs(mc, Q));
+}
+
+// Register tier of the block: items of at most kD * kCCThreads digis (and at
+// most the shared-memory tile).  Thread t holds digis t, t + kCCThreads, ...
+// of the item in registers from the first load to the labels, with its
+// slot (then its root) beside each word, so the bucket is read once per
+// digi (words) plus once (in-event indices, for the labels).
+//
+// Union-find runs on run heads only: every surviving pixel points at the
+// first pixel of its horizontal run (found from the survivor bitmap word by
+// a leading-zero count), and only heads are linked across rows, so finds
+// never visit another run's inner pixels.  Phases, one barrier each:
+//   1 occupancy + survivor bits (duplicates and invalid words flagged)
+//   2 prefix popcount -> slots; parent[s] = s; occupancy bitmap cleared
+//   3 slot and run head of every survivor; accumulators cleared at heads;
+//     one union per stretch of contact with the row above
+//   4 root of every survivor (roots marked with their linear index);
+//     charge, size and moments accumulated per root; survivor bitmap cleared
+//   5 labels; kept roots balloted per 32-slot chunk
+//   6 kept roots compacted in slot (= id) order, then staged
+// Both bitmaps are left zeroed for the next item.
+template <int kD>
+__device__ uint32_t block_item_reg(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits,
+                                   uint32_t *spre, const Tile &t, BlockShared &bs)
+{
+    const uint32_t R = L.g.R, C = L.g.C, nwords = (R * C + 31) >> 5;
+    const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
+    const uint32_t tid = threadIdx.x, n = it.n, lane = tid & 31, warp = tid >> 5;
+    const uint32_t *bw = L.ws.bucket_w + it.b;
+    const int32_t gain = it.gain, ped = it.ped;
+
+    // 1: the thread's words, then their bits
+    uint32_t w[kD], s[kD];
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        const uint32_t j = tid + k * kCCThreads;
+        w[k] = j < n ? __ldg(bw + j) : 0u;
+    }
+    uint32_t err = 0;
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        s[k] = kNoSlot;
+        if (tid + k * kCCThreads < n) {
+            const uint32_t x = w[k], r = x & 0xFFu, c = (x >> 8) & 0x1FFu, adc = (x >> 17) & 0xFFu;
+            if (r >= R || c >= C || adc == 0 || (x >> 25) != 0) {
+                err |= kErrBadDigi;
+            } else {
+                const uint32_t lin = r * C + c, bit = 1u << (lin & 31);
+                if (atomicOr(&abits[lin >> 5], bit) & bit) err |= kErrDup;
+                if ((int32_t)adc * gain - ped >= thr) {
+                    atomicOr(&sbits[lin >> 5], bit);
+                    s[k] = 0;
+                }
+            }
+        }
+    }
+    err = __reduce_or_sync(kFull, err);
+    if (err && lane == 0) atomicOr(&bs.flag, err);
+    __syncthreads();
+    const uint32_t flag = bs.flag;
+    if (flag) {
+        if (tid == 0) atomicOr(it.err_e, flag);
+        clear_words(abits, nwords);
+        clear_words(sbits, nwords);
+        __syncthreads();
+        if (tid == 0) bs.flag = 0;
+        return 0;
+    }
+
+    // 2: exclusive prefix popcount of the survivor bitmap -> dense slots
+    const uint32_t per = (nwords + kCCThreads - 1) / kCCThreads;
+    const uint32_t w0 = min(nwords, tid * per), w1 = min(nwords, w0 + per);
+    uint32_t local = 0;
+    for (uint32_t i = w0; i < w1; ++i) local += __popc(sbits[i]);
+    uint32_t S;
+    uint32_t run = block_exclusive_scan<kCCThreads>(local, bs.scan_tmp, &S);
+    for (uint32_t i = w0; i < w1; ++i) {
+        spre[i] = run;
+        run += __popc(sbits[i]);
+    }
+    for (uint32_t i = tid; i < S; i += kCCThreads) t.parent[i] = i;
+    __syncthreads();
+
+    // 3: slots, run heads, and the unions with the row above.  For a pixel p
+    // whose upper neighbour U survives, one union per maximal stretch of such
+    // pixels (at the run head, or where the upper-left pixel does not
+    // survive) joins p's run to U's run; a run head whose U is empty checks
+    // its upper-left pixel, a run tail whose U is empty its upper-right one.
+    // Every 8-adjacency between two runs passes through one of these.
+    // union pairs (head slot | target head slot << 16) go to a per-warp list in
+    // the occupancy bitmap (free since phase 2); a full list unions in place
+    const uint32_t seg = nwords / (kCCThreads / 32);
+    uint32_t *plist = abits + warp * seg;
+    uint32_t pcount = 0;
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        if (k * kCCThreads >= n) break;
+        uint32_t h = 0, th1 = kNoSlot, th2 = kNoSlot;
+        if (s[k] != kNoSlot) {
+            const uint32_t x = w[k], r = x & 0xFFu, c = (x >> 8) & 0x1FFu, lin = r * C + c;
+            const uint32_t wi = lin >> 5, b = lin & 31;
+            const uint32_t word = sbits[wi], base = spre[wi];
+            const uint32_t slot = base + __popc(word & ((1u << b) - 1u));
+            h = run_head_slot(sbits, spre, lin, r * C, word, base);
+            s[k] = slot;
+            if (h != slot) {
+                t.parent[slot] = h;
+            } else {
+                t.q[slot] = 0;
+                t.np[slot] = 0;
+                t.m[slot] = make_int2(0, 0);
+            }
+            if (r > 0) {
+                const uint32_t up = lin - C, wu = up >> 5, bu = up & 31;
+                const uint32_t uword = sbits[wu];
+                const bool U = (uword >> bu) & 1u;
+                const bool UL = c > 0 && (bu > 0 ? ((uword >> (bu - 1)) & 1u) : (sbits[wu - 1] >> 31));
+                const bool UR = c + 1 < C && (bu < 31 ? ((uword >> (bu + 1)) & 1u) : (sbits[wu + 1] & 1u));
+                const bool head = h == slot;
+                const bool tail = c + 1 == C || !(b < 31 ? ((word >> (b + 1)) & 1u) : (sbits[wi + 1] & 1u));
+                uint32_t t1 = kNoSlot, t2 = kNoSlot;
+                if (U) {
+                    if (head || !UL) t1 = up;
+                } else {
+                    if (head && UL) t1 = up - 1;
+                    if (tail && UR) t2 = up + 1;
+                }
+                const uint32_t row0u = (r - 1) * C;
+                if (t1 != kNoSlot) {
+                    const uint32_t tw = t1 >> 5;
+                    th1 = run_head_slot(sbits, spre, t1, row0u, sbits[tw], spre[tw]);
+                }
+                if (t2 != kNoSlot) {
+                    const uint32_t tw = t2 >> 5;
+                    th2 = run_head_slot(sbits, spre, t2, row0u, sbits[tw], spre[tw]);
+                }
+            }
+        }
+        const uint32_t m1 = __ballot_sync(kFull, th1 != kNoSlot), m2 = __ballot_sync(kFull, th2 != kNoSlot);
+        const uint32_t p1 = pcount + __popc(m1 & lt), p2 = pcount + __popc(m1) + __popc(m2 & lt);
+        if (th1 != kNoSlot) {
+            if (p1 < seg) plist[p1] = h | (th1 << 16);
+            else uf_union(t.parent, h, th1);
+        }
+        if (th2 != kNoSlot) {
+            if (p2 < seg) plist[p2] = h | (th2 << 16);
+            else uf_union(t.parent, h, th2);
+        }
+        pcount += __popc(m1) + __popc(m2);
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < min(pcount, seg); i += 32) {
+        const uint32_t pr = plist[i];
+        uf_union(t.parent, pr & 0xFFFFu, pr >> 16);
+    }
+    __syncthreads();
+
+    // 4: roots and per-root sums.  Each pixel walks to its root (the smallest
+    // slot); a root's own pixel marks it with kMark | its linear index (the
+    // cluster id), the others point straight at it.  Moments accumulate in
+    // 32 bits; a cluster heavier than kQSafe32 sends the item through the
+    // exact 64-bit pass.
+    clear_words(sbits, nwords);
+    clear_words(abits, nwords);
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        if (s[k] == kNoSlot) continue;
+        const uint32_t slot = s[k];
+        const volatile uint32_t *vp = t.parent;
+        uint32_t y = slot, p = vp[slot];
+        if (p != y && !(p & kMark)) {
+            y = p;
+            p = vp[y];
+            if (p != y && !(p & kMark)) y = root_walk_far(t.parent, p);
+        }
+        const uint32_t x = w[k], r = x & 0xFFu, c = (x >> 8) & 0x1FFu;
+        t.parent[slot] = y == slot ? (kMark | (r * C + c)) : y;
+        s[k] = y;
+        const int32_t q = (int32_t)((x >> 17) & 0xFFu) * gain - ped;
+        const int32_t old = atomicAdd(&t.q[y], q);
+        if (old + q > kQSafe32) bs.heavy = 1;
+        atomicAdd(&t.np[y], 1u);
+        atomicAdd(&t.m[y].x, q * (int32_t)r);
+        atomicAdd(&t.m[y].y, q * (int32_t)c);
+    }
+    __syncthreads();
+    const bool heavy = bs.heavy != 0;
+    if (heavy) {
+        for (uint32_t i = tid; i < S; i += kCCThreads) {
+            t.exact[2 * i] = 0;
+            t.exact[2 * i + 1] = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            if (s[k] == kNoSlot) continue;
+            const uint32_t x = w[k], y = s[k];
+            const long long q = (long long)((int32_t)((x >> 17) & 0xFFu) * gain - ped);
+            atomicAdd(&t.exact[2 * y], (unsigned long long)(q * (long long)(x & 0xFFu)));
+            atomicAdd(&t.exact[2 * y + 1], (unsigned long long)(q * (long long)((x >> 8) & 0x1FFu)));
+        }
+        __syncthreads();
+    }
+
+    // 5: labels, and the kept roots of every 32-slot chunk (a warp ballots a
+    // contiguous range of chunks into spre, free since phase 3)
+    if (it.label_e) {
+        const uint32_t *bi = L.ws.bucket_i + it.b;
+        uint32_t iv[kD];
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            const uint32_t j = tid + k * kCCThreads;
+            iv[k] = j < n ? __ldg(bi + j) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            if (tid + k * kCCThreads >= n) continue;
+            int32_t lab = -1;
+            if (s[k] != kNoSlot) {
+                const uint32_t y = s[k];
+                lab = t.q[y] >= cthr ? (int32_t)(t.parent[y] & ~kMark) : -2;
+            }
+            it.label_e[iv[k]] = lab;
+        }
+    }
+    constexpr uint32_t kWarps = kCCThreads / 32;
+    const uint32_t chunks = (S + 31) >> 5;
+    const uint32_t cpw = (chunks + kWarps - 1) / kWarps;
+    const uint32_t wc0 = min(chunks, warp * cpw), wc1 = min(chunks, wc0 + cpw);
+    uint32_t *ball = spre;
+    uint32_t wrun = 0;
+    for (uint32_t ch = wc0; ch < wc1; ++ch) {
+        const uint32_t sl = (ch << 5) + lane;
+        const bool kept = sl < S && (t.parent[sl] & kMark) && t.q[sl] >= cthr;
+        const uint32_t bal = __ballot_sync(kFull, kept);
+        if (lane == 0) ball[ch] = bal;
+        wrun += __popc(bal);
+    }
+    if (lane == 0) bs.scan_tmp[warp] = wrun;
+    __syncthreads();
+
+    // 6: ordinals of the kept roots, compaction, staging
+    uint32_t K, woff;
+    {
+        const uint32_t wt = lane < kWarps ? bs.scan_tmp[lane] : 0u;
+        uint32_t ws = wt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, ws, o);
+            if ((int)lane >= o) ws += y;
+        }
+        K = __shfl_sync(kFull, ws, kWarps - 1);
+        woff = __shfl_sync(kFull, ws - wt, warp);
+    }
+    if (tid == 0) bs.heavy = 0;
+    const uint32_t kslot_off = (chunks + 1) & ~1u; // words of ballots, rounded to keep kslot 4-byte aligned
+    if (K <= 2 * (nwords - min(nwords, kslot_off))) {
+        // compact the kept roots (their slots, by ordinal, after the ballot
+        // words) so that every lane stages a cluster
+        uint16_t *kslot = reinterpret_cast<uint16_t *>(spre + kslot_off);
+        uint32_t o = woff;
+        for (uint32_t ch = wc0; ch < wc1; ++ch) {
+            const uint32_t bal = ball[ch];
+            if ((bal >> lane) & 1u) kslot[o + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((ch << 5) + lane);
+            o += __popc(bal);
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < K; i += kCCThreads) stage_cluster(L, it, t, heavy, kslot[i], i);
+    } else {
+        uint32_t o = woff;
+        for (uint32_t ch = wc0; ch < wc1; ++ch) {
+            const uint32_t bal = ball[ch];
+            if ((bal >> lane) & 1u) stage_cluster(L, it, t, heavy, (ch << 5) + lane, o + __popc(bal & ((1u << lane) - 1u)));
+            o += __popc(bal);
         }
     }
     return K;
@@ -1069,21 +1468,14 @@ __device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uin
     }
 }
 
-struct Pending {
-    uint32_t g;
-    uint32_t K[kGroup];
-    uint32_t b[kGroup];
-};
-
 template <int kMinBlocks>
 __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch L)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ BlockShared bs;
-    __shared__ uint32_t s_n[kGroup], s_b[kGroup], s_K[kGroup], s_pref[kGroup + 1];
-    __shared__ Pending ring[kRing];
-    __shared__ uint32_t s_ticket, s_head, s_tail, s_ok;
-    __shared__ unsigned long long s_prefix;
+    __shared__ uint32_t s_n[kGroup], s_b[kGroup];
+    __shared__ ItemRec s_rec[kGroup];
+    __shared__ uint32_t s_ticket;
 
     const uint32_t R = L.g.R, C = L.g.C, M = L.g.M;
     const uint32_t nwords = (R * C + 31) >> 5;
@@ -1102,28 +1494,35 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
     const uint64_t EM = (uint64_t)L.E * M;
     const uint32_t G = ticket_items(EM, gridDim.x, L.tune.ticket_max);
     const uint64_t ngroups = (EM + G - 1) / G;
-    const unsigned long long kAgg = 1ull << 62;
+    // items of the register tier: kD digis a thread
+    constexpr int kD = kMinBlocks >= 3 ? 5 : 8;
     if (tid == 0) {
-        s_head = 0;
-        s_tail = 0;
+        bs.flag = 0;
+        bs.heavy = 0;
     }
-    bool tickets_left = true;
-
+    // block-tier items start from zeroed bitmaps and leave them zeroed
+    clear_words(abits, nwords);
+    clear_words(sbits, nwords);
+    // each item's count of kept clusters goes to kcount[item]; the ordered
+    // output is written by offsets_kernel and copy_kernel
+    uint32_t *kcount = L.ws.cursor;
     for (;;) {
-        if (tickets_left) {
+        {
             if (tid == 0) s_ticket = atomicAdd(&L.ws.ctl[0], 1u);
             __syncthreads();
             const uint64_t g = s_ticket;
-            if (g >= ngroups) {
-                tickets_left = false;
-            } else {
+            if (g >= ngroups) break;
+            {
                 const uint64_t item0 = g * G;
                 if (tid < (uint32_t)kGroup) {
                     const uint64_t item = item0 + tid;
                     const bool ok = tid < G && item < EM;
                     s_n[tid] = ok ? L.ws.count[item] : 0u;
                     s_b[tid] = ok ? L.ws.boff[item] : 0u;
-                    s_K[tid] = 0;
+                    if (ok) {
+                        s_rec[tid] = make_rec(L, item);
+                        if (s_n[tid] == 0) kcount[item] = 0;
+                    }
                 }
                 __syncthreads();
                 {   // pull the ticket's buckets (words and digi indices, contiguous
@@ -1133,10 +1532,11 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                     for (uint32_t i = 0; i < G; ++i)
                         if (s_n[i]) last = i;
                     const uint64_t b0 = s_b[0], b1 = (uint64_t)s_b[last] + s_n[last];
-                    const uint64_t lines = b1 > b0 ? ((b1 - b0) * 4 + 127) / 128 : 0;
-                    for (uint64_t li = tid; li < 2 * lines; li += kCCThreads) {
-                        const uint32_t *base = li < lines ? L.ws.bucket_w : L.ws.bucket_i;
-                        const uint64_t off = b0 * 4 + (li % lines) * 128; // < b1 * 4: inside the array
+                    const uint32_t lines = b1 > b0 ? (uint32_t)(((b1 - b0) * 4 + 127) / 128) : 0u;
+                    for (uint32_t li = tid; li < 2 * lines; li += kCCThreads) {
+                        const bool second = li >= lines;
+                        const uint32_t *base = second ? L.ws.bucket_i : L.ws.bucket_w;
+                        const uint64_t off = b0 * 4 + (uint64_t)(second ? li - lines : li) * 128; // inside the array
                         if (off < b1 * 4)
                             asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(base) + off));
                     }
@@ -1145,18 +1545,20 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                     const uint32_t wi = tid >> 5;
                     const uint32_t n = s_n[wi];
                     if (n > 0 && n <= warp_max) {
-                        const ItemCtx it = make_item(L, item0 + wi, s_b[wi], n);
+                        const ItemCtx it = make_item(L, s_rec[wi], s_b[wi], n);
                         const uint32_t K = n <= 32 ? warp_item<1>(L, it) : warp_item<2>(L, it);
-                        if ((tid & 31) == 0) s_K[wi] = K;
+                        if ((tid & 31) == 0) kcount[item0 + wi] = K;
                     }
                 }
                 __syncthreads();
                 for (int i = 0; i < kGroup; ++i) { // block tier: larger items one at a time
                     const uint32_t n = s_n[i];
                     if (n <= warp_max) continue;
-                    const ItemCtx it = make_item(L, item0 + i, s_b[i], n);
+                    const ItemCtx it = make_item(L, s_rec[i], s_b[i], n);
                     uint32_t K;
-                    if (n <= T) {
+                    if (n <= (uint32_t)kD * kCCThreads && n <= T) {
+                        K = block_item_reg<kD>(L, it, abits, sbits, spre, sm, bs);
+                    } else if (n <= T) {
                         K = block_item<false>(L, it, abits, sbits, spre, sm, bs);
                     } else {
                         if (tid == 0) {
@@ -1179,98 +1581,115 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                         K = fits ? block_item<true>(L, it, abits, sbits, spre, gt, bs) : 0u;
                         if (!fits && tid == 0) atomicOr(&L.ws.ctl[1], kErrCapacity);
                     }
-                    if (tid == 0) s_K[i] = K;
+                    if (n > (uint32_t)kD * kCCThreads || n > T) {
+                        // the general tier leaves its bitmaps (and scratch in them) behind
+                        __syncthreads();
+                        clear_words(abits, nwords);
+                        clear_words(sbits, nwords);
+                        if (tid == 0) {
+                            bs.flag = 0;
+                            bs.heavy = 0;
+                        }
+                    }
+                    if (tid == 0) kcount[item0 + i] = K;
                     __syncthreads();
                 }
-                // park the ticket and publish its aggregate (no waiting here)
-                if (tid == 0) {
-                    Pending &pd = ring[s_tail % kRing];
-                    unsigned long long agg = 0;
-                    pd.g = (uint32_t)g;
-                    for (int i = 0; i < kGroup; ++i) {
-                        pd.K[i] = s_K[i];
-                        pd.b[i] = s_b[i];
-                        agg += s_K[i];
-                    }
-                    // The aggregate is all that other blocks read of this ticket (its
-                    // clusters are written out by this block), so a relaxed store
-                    // with no fence suffices.  (The test hook kDebugWithholdTicket0
-                    // keeps ticket 0's aggregate back, so that the blocking waits on
-                    // it expire.)
-                    if (g != 0 || !(L.debug & kDebugWithholdTicket0)) st_relaxed(&L.ws.chain[g], kAgg | agg);
-                    ++s_tail;
-                }
-                __syncthreads();
             }
         }
-
-        // write out parked tickets whose prefix is known, oldest first (once
-        // half the ring is parked, or at the end)
-        const bool resolve_now = !tickets_left || s_tail - s_head >= (uint32_t)kRing / 2;
-        while (resolve_now && s_head != s_tail) {
-            const bool blocking = !tickets_left || (s_tail - s_head) >= (uint32_t)kRing;
-            const Pending &pd = ring[s_head % kRing];
-            if (tid < 32) {
-                unsigned long long agg = 0;
-                for (int i = 0; i < kGroup; ++i) agg += pd.K[i];
-                unsigned long long excl = 0;
-                const bool ok =
-                    chain_resolve(L.ws.chain, &L.ws.ctl[3], ngroups, pd.g, agg, blocking, &excl, &L.ws.ctl[1]);
-                if (tid == 0) {
-                    s_ok = ok ? 1u : 0u;
-                    s_prefix = excl;
-                    uint32_t p = 0;
-                    for (int i = 0; i < kGroup; ++i) {
-                        s_pref[i] = p;
-                        p += pd.K[i];
-                    }
-                    s_pref[kGroup] = p;
-                }
-            }
-            __syncthreads();
-            if (!s_ok) break;
-            const unsigned long long P = s_prefix;
-            const uint32_t tot = s_pref[kGroup];
-            const uint64_t item0 = (uint64_t)pd.g * G;
-            for (uint32_t o = tid; o < tot; o += kCCThreads) {
-                int i = 0;
-                while (i + 1 < kGroup && s_pref[i + 1] <= o) ++i;
-                const StagedCluster sc = L.ws.staging[pd.b[i] + (o - s_pref[i])];
-                const unsigned long long d = P + o;
-                if (d < L.out.capacity) {
-                    L.out.module[d] = (uint32_t)((item0 + i) % M);
-                    L.out.id[d] = sc.id;
-                    L.out.charge[d] = sc.charge;
-                    L.out.npix[d] = sc.npix;
-                    L.out.x[d] = sc.x;
-                    L.out.y[d] = sc.y;
-                }
-            }
-            if (tid == 0 && P + tot > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
-            if (tid < G) {
-                const uint64_t item = item0 + tid;
-                if (item < EM && item % M == 0) L.out.cluster_offsets[item / M] = P + s_pref[tid];
-            }
-            if (tid == 0 && pd.g == ngroups - 1) L.out.cluster_offsets[L.E] = P + tot;
-            __syncthreads();
-            if (tid == 0) ++s_head;
-            __syncthreads();
-        }
-        if (!tickets_left && s_head == s_tail) break;
     }
 }
 
-__global__ void finalize_kernel(const Launch L)
+
+// Ordered output, in two kernels.
+//
+// offsets_kernel: block c takes chunk c of kOffItems consecutive items (in
+// the order blocks start, so the chunks below it are running or done), scans
+// the items' kept-cluster counts (cursor[], from cc_kernel), publishes the
+// chunk's total in chain[c] and resolves its exclusive prefix with the
+// cooperative frontier (a bounded wait; few, large chunks keep the frontier
+// short); it writes every item's first output position to count[] (free
+// since cc_kernel read it), the cluster offsets of the events that start in
+// the chunk, and the capacity check.
+constexpr int kOffThreads = 1024;
+constexpr uint32_t kOffItems = kOffThreads;
+
+__global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
 {
-    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= L.E) return;
-    const uint32_t bits = L.ws.event_err[e] | L.ws.ctl[1];
-    int32_t st = 0;                          // HP_OK
-    if (bits & kErrTimeout) st = 8;          // HP_ETIMEOUT
-    else if (bits & kErrCapacity) st = 6;    // HP_ECAPACITY
-    else if (bits & kErrBadDigi) st = 4;     // HP_EBADDIGI
-    else if (bits & kErrDup) st = 5;         // HP_EDUP
-    L.out.event_status[e] = st;
+    __shared__ uint32_t s_tmp[kOffThreads / 32 + 1];
+    __shared__ uint32_t s_chunk;
+    __shared__ unsigned long long s_prefix;
+    const uint32_t tid = threadIdx.x, M = L.g.M;
+    const uint64_t EM = (uint64_t)L.E * M;
+    const uint64_t nchunks = (EM + kOffItems - 1) / kOffItems;
+    if (tid == 0) s_chunk = atomicAdd(&L.ws.ctl[4], 1u);
+    __syncthreads();
+    const uint64_t c = s_chunk;
+    if (c >= nchunks) return;
+    const uint64_t item = c * kOffItems + tid;
+    const bool in = item < EM;
+    const uint32_t k = in ? L.ws.cursor[item] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan<kOffThreads>(k, s_tmp, &total);
+    if (tid < 32) {
+        // The chunk's total is all that other blocks read of it, so a relaxed
+        // store suffices.  (The test hook kDebugWithholdTicket0 keeps chunk
+        // 0's total back, so that the waits on it expire.)
+        const unsigned long long kAgg = 1ull << 62;
+        if (tid == 0 && (c != 0 || !(L.debug & kDebugWithholdTicket0))) st_relaxed(&L.ws.chain[c], kAgg | total);
+        __syncwarp();
+        unsigned long long P = 0;
+        chain_resolve(L.ws.chain, &L.ws.ctl[3], nchunks, c, total, true, &P, &L.ws.ctl[1]);
+        if (tid == 0) s_prefix = P;
+    }
+    __syncthreads();
+    const unsigned long long P = s_prefix;
+    if (in) {
+        L.ws.count[item] = (uint32_t)(P + ex);
+        uint32_t e, m;
+        item_coords(item, M, &e, &m);
+        if (m == 0) L.out.cluster_offsets[e] = P + ex;
+    }
+    if (tid == 0 && c == nchunks - 1) L.out.cluster_offsets[L.E] = P + total;
+    if (tid == 0 && P + total > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
+}
+
+// copy_kernel: one warp per item copies its staged clusters (SoA, at the
+// item's bucket start) to their output positions; the first E threads write
+// the per-event status codes from the error bits.
+constexpr int kCopyThreads = 256;
+
+__global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
+{
+    const uint32_t lane = threadIdx.x & 31, M = L.g.M;
+    const uint64_t EM = (uint64_t)L.E * M;
+    const uint64_t gt = (uint64_t)blockIdx.x * kCopyThreads + threadIdx.x;
+    if (gt < L.E) {
+        const uint32_t bits = L.ws.event_err[gt] | L.ws.ctl[1];
+        int32_t st = 0;                          // HP_OK
+        if (bits & kErrTimeout) st = 8;          // HP_ETIMEOUT
+        else if (bits & kErrCapacity) st = 6;    // HP_ECAPACITY
+        else if (bits & kErrBadDigi) st = 4;     // HP_EBADDIGI
+        else if (bits & kErrDup) st = 5;         // HP_EDUP
+        L.out.event_status[gt] = st;
+    }
+    const Staging sg = L.ws.staging;
+    const uint64_t warps = (uint64_t)gridDim.x * (kCopyThreads / 32);
+    for (uint64_t item = gt >> 5; item < EM; item += warps) {
+        const uint32_t K = L.ws.cursor[item], d0 = L.ws.count[item], b = L.ws.boff[item];
+        uint32_t e, m;
+        item_coords(item, M, &e, &m);
+        for (uint32_t o = lane; o < K; o += 32) {
+            const uint64_t d = (uint64_t)d0 + o, a = (uint64_t)b + o;
+            if (d < L.out.capacity) {
+                L.out.module[d] = m;
+                L.out.id[d] = sg.id[a];
+                L.out.charge[d] = sg.charge[a];
+                L.out.npix[d] = sg.npix[a];
+                L.out.x[d] = sg.x[a];
+                L.out.y[d] = sg.y[a];
+            }
+        }
+    }
 }
 
 // Serving batches: block (x, e) copies a slice of request e's digis.
@@ -1311,20 +1730,23 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
         return base ? static_cast<unsigned char *>(base) + o : nullptr;
     };
     const uint64_t EM = (uint64_t)E * M;
-    const uint32_t G = ticket_items(EM, (unsigned)(cc_grid > 0 ? cc_grid : 1), tune.ticket_max);
-    const uint64_t ngroups = (EM + G - 1) / G;
+    const uint64_t nchunks = (EM + kOffItems - 1) / kOffItems;
     Workspace w{};
     w.ctl = reinterpret_cast<uint32_t *>(take(64));
     w.event_err = reinterpret_cast<uint32_t *>(take(4ull * E));
     w.count = reinterpret_cast<uint32_t *>(take(4ull * EM));
-    w.chain = reinterpret_cast<unsigned long long *>(take(16ull * ngroups)); // aggregates, then inclusive prefixes
+    w.chain = reinterpret_cast<unsigned long long *>(take(16ull * nchunks)); // aggregates, then inclusive prefixes
     off = (off + 255) & ~(size_t)255;
     w.zero_bytes = off;
     w.boff = reinterpret_cast<uint32_t *>(take(4ull * EM));
     w.cursor = reinterpret_cast<uint32_t *>(take(4ull * EM));
     w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
-    w.staging = reinterpret_cast<StagedCluster *>(take(sizeof(StagedCluster) * N));
+    w.staging.id = reinterpret_cast<int32_t *>(take(4ull * N));
+    w.staging.charge = reinterpret_cast<int32_t *>(take(4ull * N));
+    w.staging.npix = reinterpret_cast<int32_t *>(take(4ull * N));
+    w.staging.x = reinterpret_cast<float *>(take(4ull * N));
+    w.staging.y = reinterpret_cast<float *>(take(4ull * N));
     w.exact = reinterpret_cast<unsigned long long *>(take(16ull * tune.tile_slots * (cc_grid > 0 ? cc_grid : 1)));
     const uint64_t slab_slots = std::min<uint64_t>((uint64_t)R * C, N);
     const uint64_t slab_total = slab_slots * (uint64_t)(cc_grid > 0 ? cc_grid : 1);
@@ -1385,8 +1807,8 @@ cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4
     return fit_tile(cc_kernel<3>, device, 3, R, C, kSmemSlots, &max_tile[3]);
 }
 
-const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel", "scatter_kernel", "cc_kernel",
-                                                "finalize_kernel"};
+const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel",    "scatter_kernel",
+                                                "cc_kernel",   "offsets_kernel", "copy_kernel"};
 
 cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count, cudaEvent_t *marks)
 {
@@ -1421,9 +1843,18 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
         cc_kernel<2><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
     ++nk;
     mark(4);
-    finalize_kernel<<<(L.E + 255) / 256, 256, 0, stream>>>(L);
+    const uint64_t EM = (uint64_t)L.E * L.g.M;
+    offsets_kernel<<<(unsigned)((EM + kOffItems - 1) / kOffItems), kOffThreads, 0, stream>>>(L);
     ++nk;
     mark(5);
+    {   // a warp per item, at most 8192 blocks (the items loop), and a thread per event status
+        const uint64_t by_items = (EM + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
+        const uint64_t by_events = ((uint64_t)L.E + kCopyThreads - 1) / kCopyThreads;
+        const uint64_t blocks = std::max<uint64_t>(by_events, std::min<uint64_t>(by_items, 8192));
+        copy_kernel<<<(unsigned)blocks, kCopyThreads, 0, stream>>>(L);
+    }
+    ++nk;
+    mark(6);
     if (kernel_count) *kernel_count += nk;
     if (err != cudaSuccess) return err;
     return cudaGetLastError();

@@ -41,6 +41,6 @@ def test_device_run_line():
     rf = d["roofline"]
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(rf)
     assert 0 < rf["frac"] < 2 and rf["unit"] == "GB/s"
-    assert d["gpu_launches"] == 3 * 5
+    assert d["gpu_launches"] == 3 * 6
     assert d["value"] > 0 and d["n_gpus"] == 1 and d["scaling"] == "weak"
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
