@@ -91,7 +91,8 @@ struct Outputs {
 // the first kernel (one memset): control words, per-event error bits,
 // per-item counts and the chained-scan state.
 struct Workspace {
-    uint32_t *ctl;        // [16]: 0 item ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier, 4 offsets chunk ticket
+    uint32_t *ctl;        // [16]: 0 item ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier,
+                          //       4 offsets chunk ticket, 5 pieces of large items
     uint32_t *event_err;  // [E]
     uint32_t *count;      // [E*M] digis of each item; then each item's first output position (offsets_kernel)
     unsigned long long *chain; // [2 * n_chunks]: offsets_kernel chunk totals, then inclusive prefixes
@@ -101,6 +102,7 @@ struct Workspace {
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event
     Staging staging;      // [N] each array
+    uint2 *pieces;        // [N / 512 + 1] (item, piece) of the large items, copied a block per piece
     unsigned long long *exact; // [cc_grid * 2 * tile_slots] 64-bit moments of heavy clusters
     unsigned char *big;   // scratch of items too large for shared memory
     uint64_t big_slots;   // slots per block (slab mode) or in total (arena mode)
@@ -117,6 +119,7 @@ struct Launch {
     Outputs out;
     Workspace ws;
     int cc_grid;             // blocks of the clustering kernel
+    int copy_grid = 1216;    // most blocks of the output copy (8 an SM of a 152-SM GPU)
     Tuning tune;
     uint32_t debug = 0;      // test hooks (kDebug*)
 };

@@ -1612,6 +1612,8 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
 // the chunk, and the capacity check.
 constexpr int kOffThreads = 1024;
 constexpr uint32_t kOffItems = kOffThreads;
+constexpr unsigned long long kCopySpan = 1024; // clusters of a large item a copy_kernel block takes at a time
+constexpr uint32_t kBigItem = 512;             // items with more kept clusters are copied by blocks, not warps
 
 __global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
 {
@@ -1644,19 +1646,42 @@ __global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
     __syncthreads();
     const unsigned long long P = s_prefix;
     if (in) {
-        L.ws.count[item] = (uint32_t)(P + ex);
+        const unsigned long long o = P + ex;
+        L.ws.count[item] = (uint32_t)o;
         uint32_t e, m;
         item_coords(item, M, &e, &m);
-        if (m == 0) L.out.cluster_offsets[e] = P + ex;
+        if (m == 0) L.out.cluster_offsets[e] = o;
+        // a large item is copied in pieces of kCopySpan clusters by whole blocks
+        if (k > kBigItem) {
+            const uint32_t pieces = (k + (uint32_t)kCopySpan - 1) / (uint32_t)kCopySpan;
+            const uint32_t at = atomicAdd(&L.ws.ctl[5], pieces);
+            for (uint32_t pc = 0; pc < pieces; ++pc) L.ws.pieces[at + pc] = make_uint2((uint32_t)item, pc);
+        }
     }
     if (tid == 0 && c == nchunks - 1) L.out.cluster_offsets[L.E] = P + total;
     if (tid == 0 && P + total > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
 }
 
 // copy_kernel: one warp per item copies its staged clusters (SoA, at the
-// item's bucket start) to their output positions; the first E threads write
-// the per-event status codes from the error bits.
+// item's bucket start) to their output positions, four clusters a lane in
+// flight; items with more than kBigItem clusters are skipped there and
+// copied instead in pieces of kCopySpan clusters, a block per piece (the
+// piece list comes from offsets_kernel), so that no warp carries a hot
+// module alone.  The first E threads write the per-event status codes from
+// the error bits.
 constexpr int kCopyThreads = 256;
+
+__device__ __forceinline__ void copy_one(const Launch &L, const Staging &sg, uint64_t d, uint64_t a, uint32_t m)
+{
+    const int32_t id = sg.id[a], q = sg.charge[a], np = sg.npix[a];
+    const float x = sg.x[a], y = sg.y[a];
+    L.out.module[d] = m;
+    L.out.id[d] = id;
+    L.out.charge[d] = q;
+    L.out.npix[d] = np;
+    L.out.x[d] = x;
+    L.out.y[d] = y;
+}
 
 __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
 {
@@ -1673,22 +1698,34 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
         L.out.event_status[gt] = st;
     }
     const Staging sg = L.ws.staging;
+    const unsigned long long cap = L.out.capacity;
     const uint64_t warps = (uint64_t)gridDim.x * (kCopyThreads / 32);
     for (uint64_t item = gt >> 5; item < EM; item += warps) {
-        const uint32_t K = L.ws.cursor[item], d0 = L.ws.count[item], b = L.ws.boff[item];
+        const uint32_t K = L.ws.cursor[item];
+        if (K == 0 || K > kBigItem) continue;
+        const uint64_t d0 = L.ws.count[item], b = L.ws.boff[item];
         uint32_t e, m;
         item_coords(item, M, &e, &m);
-        for (uint32_t o = lane; o < K; o += 32) {
-            const uint64_t d = (uint64_t)d0 + o, a = (uint64_t)b + o;
-            if (d < L.out.capacity) {
-                L.out.module[d] = m;
-                L.out.id[d] = sg.id[a];
-                L.out.charge[d] = sg.charge[a];
-                L.out.npix[d] = sg.npix[a];
-                L.out.x[d] = sg.x[a];
-                L.out.y[d] = sg.y[a];
-            }
+        uint32_t o = lane;
+        for (; o + 96 < K; o += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (d0 + o + 32 * u < cap) copy_one(L, sg, d0 + o + 32 * u, b + o + 32 * u, m);
         }
+        for (; o < K; o += 32)
+            if (d0 + o < cap) copy_one(L, sg, d0 + o, b + o, m);
+    }
+    const uint32_t npieces = L.ws.ctl[5];
+    for (uint32_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
+        const uint2 w = L.ws.pieces[pc];
+        const uint64_t item = w.x;
+        const uint32_t K = L.ws.cursor[item];
+        const uint64_t d0 = L.ws.count[item], b = L.ws.boff[item];
+        uint32_t e, m;
+        item_coords(item, M, &e, &m);
+        const uint32_t lo = w.y * (uint32_t)kCopySpan, hi = min(K, lo + (uint32_t)kCopySpan);
+        for (uint32_t o = lo + threadIdx.x; o < hi; o += kCopyThreads)
+            if (d0 + o < cap) copy_one(L, sg, d0 + o, b + o, m);
     }
 }
 
@@ -1742,6 +1779,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     w.cursor = reinterpret_cast<uint32_t *>(take(4ull * EM));
     w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
+    w.pieces = reinterpret_cast<uint2 *>(take(8ull * (N / kBigItem + 1)));
     w.staging.id = reinterpret_cast<int32_t *>(take(4ull * N));
     w.staging.charge = reinterpret_cast<int32_t *>(take(4ull * N));
     w.staging.npix = reinterpret_cast<int32_t *>(take(4ull * N));
@@ -1847,10 +1885,11 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     offsets_kernel<<<(unsigned)((EM + kOffItems - 1) / kOffItems), kOffThreads, 0, stream>>>(L);
     ++nk;
     mark(5);
-    {   // a warp per item, at most 8192 blocks (the items loop), and a thread per event status
+    {   // a warp per item (at most copy_grid blocks, looping), and a thread per event status
         const uint64_t by_items = (EM + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
         const uint64_t by_events = ((uint64_t)L.E + kCopyThreads - 1) / kCopyThreads;
-        const uint64_t blocks = std::max<uint64_t>(by_events, std::min<uint64_t>(by_items, 8192));
+        const uint64_t blocks =
+            std::max<uint64_t>(1, std::max<uint64_t>(by_events, std::min<uint64_t>(by_items, (uint64_t)L.copy_grid)));
         copy_kernel<<<(unsigned)blocks, kCopyThreads, 0, stream>>>(L);
     }
     ++nk;

@@ -93,6 +93,7 @@ extern "C" hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_event
     L.out.label = out->label;
     hp::carve_workspace(base, n_events, g.M, n_digis, g.R, g.C, grid, tune, &L.ws);
     L.cc_grid = grid;
+    L.copy_grid = 4 * grid;
     L.tune = tune;
     uint64_t nk = 0;
     if (hp::launch_reconstruct(L, static_cast<cudaStream_t>(stream), &nk, nullptr) != cudaSuccess) {

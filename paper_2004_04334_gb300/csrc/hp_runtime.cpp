@@ -843,6 +843,7 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     if (!keep) ev->dv.label = nullptr; // the device labels go back to the pool at completion
     hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, sh.tune, &L.ws);
     L.cc_grid = grid;
+    L.copy_grid = ctx->sm_count * 8;
     L.tune = sh.tune;
     L.debug = take_debug(ctx);
     ev->path = offsets ? HP_PATH_BATCH : HP_PATH_EVENT;
@@ -1123,6 +1124,7 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     hp::carve_workspace(db + l.d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.sh.grid, l.sh.tune,
                         &L.ws);
     L.cc_grid = l.sh.grid;
+    L.copy_grid = ctx->sm_count * 8;
     L.tune = l.sh.tune;
 
     const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
@@ -1356,6 +1358,7 @@ cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const 
     hp::carve_workspace(base, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows, ctx->cfg.cols, sh.grid, sh.tune,
                         &L.ws);
     L.cc_grid = sh.grid;
+    L.copy_grid = ctx->sm_count * 8;
     L.tune = sh.tune;
     L.debug = debug;
     return hp::launch_reconstruct(L, s, nk, marks);
