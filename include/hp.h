@@ -320,11 +320,14 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
  * GPU where the library is used, for the life of the process.
  * Limits: n_digis <= 131072 and n_events * n_modules <= 16384 per call, else
  * HP_ECAPACITY (nothing is launched).  The first call on a device looks the
- * array up on that device (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array and each call
+ * array up on that device (cudaGetSymbolAddress) and keeps its address for
+ * the life of the process; make that first call before any stream capture,
+ * and do not call the entry point after a cudaDeviceReset.  All calls share the one array and each call
  * overwrites what the previous one left in it: calls whose work overlaps on
  * the GPU (different streams, or another thread) race and corrupt each
  * other; serialise them, e.g. on one stream.
+ * Argument checks are those of hp_reconstruct_device; a CUDA error marks the
+ * context failed (HP_ECUDA for every later call), as there.
  * Errors: HP_EINVAL, HP_ECAPACITY, HP_ECUDA.
  */
 hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,

@@ -24,6 +24,7 @@ constexpr uint32_t kErrBadDigi = 1u;
 constexpr uint32_t kErrDup = 2u;
 constexpr uint32_t kErrCapacity = 4u;
 constexpr uint32_t kErrTimeout = 8u;
+constexpr uint32_t kErrBadOffsets = 16u; // event offsets not 0 = o[0] <= o[1] <= ... <= o[E] = N (launch-wide)
 
 // Tuning constants of the kernels.
 constexpr int kChunk = 4096;         // digis per histogram / scatter block
@@ -94,11 +95,15 @@ struct Workspace {
     uint32_t *ctl;        // [16]: 0 item ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier,
                           //       4 offsets chunk ticket, 5 pieces of large items
     uint32_t *event_err;  // [E]
-    uint32_t *count;      // [E*M] digis of each item; then each item's first output position (offsets_kernel)
+    uint32_t *count;      // [E*M] digis of each item (reserved part, then the total: scan_kernel);
+                          //       then each item's first output position (offsets_kernel)
+    uint32_t *count2;     // [E*M] digis counted one by one (histogram ranges with too many keys)
     unsigned long long *chain; // [2 * n_chunks]: offsets_kernel chunk totals, then inclusive prefixes
     size_t zero_bytes;
     uint32_t *boff;       // [E*M] bucket start of each item
-    uint32_t *cursor;     // [E*M] scatter cursor; then each item's count of kept clusters (cc_kernel)
+    uint32_t *blk_off;    // [bucket_grid * kHistCap] each histogram block's offset inside each key's bucket
+    uint32_t *cursor;     // [E*M] scatter cursor of the one-by-one part; then each item's count of kept
+                          //       clusters (cc_kernel)
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event
     Staging staging;      // [N] each array
@@ -120,6 +125,7 @@ struct Launch {
     Workspace ws;
     int cc_grid;             // blocks of the clustering kernel
     int copy_grid = 1216;    // most blocks of the output copy (8 an SM of a 152-SM GPU)
+    int sm_count = 152;      // SMs of the device (grids of the persistent histogram and scatter)
     Tuning tune;
     uint32_t debug = 0;      // test hooks (kDebug*)
 };
@@ -129,6 +135,15 @@ struct Launch {
 // HP_ETIMEOUT (the wait's limit is one second).
 constexpr uint32_t kDebugWithholdTicket0 = 1u;
 
+// Blocks of the persistent histogram and scatter kernels (the same
+// contiguous digi ranges in both): two an SM, at least one kChunk a block.
+__host__ __device__ inline unsigned bucket_grid(uint64_t N, int sm_count)
+{
+    const uint64_t chunks = (N + kChunk - 1) / kChunk;
+    const uint64_t cap = 2ull * (uint64_t)(sm_count > 0 ? sm_count : 1);
+    return (unsigned)(chunks < 1 ? 1 : (chunks < cap ? chunks : cap));
+}
+
 // Bytes of one global-tier slot: (Q, npix), two 64-bit and two 32-bit moments,
 // parent, padded to 8-byte multiples so every slot range stays 8-byte aligned.
 constexpr size_t kBigSlotBytes = 8 + 16 + 8 + 4 + 4;
@@ -136,7 +151,7 @@ constexpr size_t kBigSlotBytes = 8 + 16 + 8 + 4 + 4;
 size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots);
 // Lay out the workspace for (E, M, N) in `base` (nullptr: only compute size).
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
-                       const Tuning &tune, Workspace *ws);
+                       const Tuning &tune, Workspace *ws, int sm_count);
 // Configure kernel attributes once per device.  max_tile[b] receives the
 // largest tile (slots) with which b clustering blocks stay resident per SM
 // (0 if b blocks cannot be resident), for b = 1, 2 and 3 (at most
@@ -200,8 +215,15 @@ cudaError_t launch_copy_out(const Outputs &src, const Outputs &dst, uint32_t E, 
                             cudaStream_t stream);
 
 // Launch parameters of a context (implemented by the runtime): geometry with
-// device calibration pointers, device ordinal, clustering grid size, and
-// whether the context has failed.
-bool context_launch_params(hp_ctx *ctx, Geometry *g, int *device, int *cc_grid);
+// device calibration pointers, device ordinal, clustering grid size and SM
+// count; false if the context has failed.
+bool context_launch_params(hp_ctx *ctx, Geometry *g, int *device, int *cc_grid, int *sm_count);
+// Argument checks shared by the device-resident entry points: 0 (HP_OK) or
+// the hp_status to return.
+int check_device_call(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                      const uint32_t *d_words, const uint16_t *d_module_ids, const struct hp_device_clusters *out);
+// Mark the context failed after a CUDA error (every later call reports
+// HP_ECUDA); returns HP_ECUDA.
+int context_fail(hp_ctx *ctx);
 
 } // namespace hp

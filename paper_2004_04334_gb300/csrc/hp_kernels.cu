@@ -206,6 +206,49 @@ __device__ __forceinline__ void load_words(const Launch &L, uint64_t k0, uint64_
     }
 }
 
+// Asynchronous 16-byte copies global -> shared (cp.async), committed as one
+// group and waited for by the issuing thread only.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Prefetch of the thread's next kPerThread digis (starting at k0, all before
+// c1 and 16-byte aligned) into its own slots of pf_m / pf_w; false (nothing
+// issued) for a partial or unaligned group, which is then loaded directly.
+__device__ __forceinline__ bool prefetch_digis(const Launch &L, uint64_t k0, uint64_t c1, uint16_t *pf_m, uint32_t *pf_w)
+{
+    if (k0 + kPerThread > c1 || (reinterpret_cast<uintptr_t>(L.modules) & 15) ||
+        (pf_w && (reinterpret_cast<uintptr_t>(L.words) & 15)))
+        return false;
+    const uint32_t t = threadIdx.x * kPerThread;
+    cp_async16(pf_m + t, L.modules + k0);
+    if (pf_w) {
+        cp_async16(pf_w + t, L.words + k0);
+        cp_async16(pf_w + t + 4, L.words + k0 + 4);
+    }
+    cp_async_commit();
+    return true;
+}
+
+__device__ __forceinline__ void take_prefetched(const uint16_t *pf_m, const uint32_t *pf_w, uint32_t m[kPerThread],
+                                                uint32_t w[kPerThread])
+{
+    cp_async_wait_all();
+    const uint32_t t = threadIdx.x * kPerThread;
+    const uint4 a = *reinterpret_cast<const uint4 *>(pf_m + t);
+    m[0] = a.x & 0xFFFFu, m[1] = a.x >> 16, m[2] = a.y & 0xFFFFu, m[3] = a.y >> 16;
+    m[4] = a.z & 0xFFFFu, m[5] = a.z >> 16, m[6] = a.w & 0xFFFFu, m[7] = a.w >> 16;
+    if (pf_w) {
+        const uint4 b = *reinterpret_cast<const uint4 *>(pf_w + t);
+        const uint4 c = *reinterpret_cast<const uint4 *>(pf_w + t + 4);
+        w[0] = b.x, w[1] = b.y, w[2] = b.z, w[3] = b.w, w[4] = c.x, w[5] = c.y, w[6] = c.z, w[7] = c.w;
+    }
+}
+
 // Event of each of the thread's digis: a binary search over the block's
 // event offsets (in shared memory when they fit), then a forward walk.
 constexpr uint32_t kChunkEvents = 512; // event offsets a block keeps in shared memory
@@ -266,11 +309,24 @@ struct ChunkInfo {
     bool use_sh;
 };
 
-__device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint32_t *s_ev, uint64_t *s_off)
+// Digis [c0, c1) of block b of nb: contiguous ranges cut at multiples of
+// kPerThread digis (so every thread's group of digis is 16-byte aligned).
+__device__ __forceinline__ void block_range(uint64_t N, uint32_t b, uint32_t nb, uint64_t *c0, uint64_t *c1)
+{
+    const uint64_t ng = (N + kPerThread - 1) / kPerThread;
+    *c0 = min(N, (uint64_t)b * ng / nb * kPerThread);
+    *c1 = min(N, (uint64_t)(b + 1) * ng / nb * kPerThread);
+}
+
+// Events and (event, module) keys of the digis [c0, c1) (c0 < c1): the first
+// and last event by a warp search, the events' offsets in shared memory when
+// they fit, and whether the keys fit a shared-memory histogram.
+__device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint64_t c0, uint64_t c1, uint32_t *s_ev,
+                                                uint64_t *s_off)
 {
     ChunkInfo ci;
-    ci.c0 = (uint64_t)blockIdx.x * kChunk;
-    ci.c1 = min(L.N, ci.c0 + (uint64_t)kChunk);
+    ci.c0 = c0;
+    ci.c1 = c1;
     if (threadIdx.x < 32) {
         const uint32_t ef = find_event_warp(L.offsets, 0, L.E - 1, ci.c0);
         const uint32_t el = find_event_warp(L.offsets, ef, L.E - 1, ci.c1 - 1);
@@ -297,72 +353,121 @@ __device__ __forceinline__ ChunkInfo chunk_info(const Launch &L, uint32_t *s_ev,
 constexpr uint32_t kHistWarps = kHistThreads / 32;
 constexpr uint32_t kSubKeys = kHistCap / kHistWarps; // keys per warp sub-histogram
 
-__global__ void __launch_bounds__(kHistThreads) hist_kernel(const Launch L)
+// Histogram, persistent: block b counts the digis of its contiguous range
+// (one event search a block), 8 module ids a thread per step with the next
+// step's ids loaded ahead (cp.async), into a shared histogram over the
+// range's keys, flushed once with one global atomic per non-empty key; the
+// atomic's return value (the block's offset inside the key's bucket) is
+// kept in blk_off for the scatter kernel.
+__global__ void __launch_bounds__(kHistThreads, 3) hist_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
-    // the chunk's module ids are loaded before the event search, so that the
+    __shared__ __align__(16) uint16_t pf_m[kChunk];
+    // the event offsets must run 0 = o[0] <= o[1] <= ... <= o[E] = N (the
+    // device entry points take them from the caller); each block checks a
+    // slice, and a violation makes every later kernel skip its writes and
+    // every event report HP_EINVAL
+    {
+        const uint64_t e0 = (uint64_t)blockIdx.x * L.E / gridDim.x, e1 = (uint64_t)(blockIdx.x + 1) * L.E / gridDim.x;
+        bool bad = false;
+        for (uint64_t e = e0 + threadIdx.x; e < e1; e += kHistThreads) bad |= L.offsets[e] > L.offsets[e + 1];
+        if (threadIdx.x == 0 && blockIdx.x == 0) bad |= L.offsets[0] != 0 || L.offsets[L.E] != L.N;
+        if (bad) atomicOr(&L.ws.ctl[1], kErrBadOffsets);
+    }
+    uint64_t c0, c1;
+    block_range(L.N, blockIdx.x, gridDim.x, &c0, &c1);
+    if (c0 >= c1) return;
+    // the first module ids are loaded before the event search, so that the
     // two latencies overlap
-    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk, k0 = c0 + (uint64_t)threadIdx.x * kPerThread;
+    uint64_t k0 = c0 + (uint64_t)threadIdx.x * kPerThread;
     uint32_t m[kPerThread], e_of[kPerThread];
-    load_modules(L, k0, min(L.N, c0 + (uint64_t)kChunk), m);
-    const ChunkInfo ci = chunk_info(L, s_ev, s_off);
+    load_modules(L, k0, c1, m);
+    const ChunkInfo ci = chunk_info(L, c0, c1, s_ev, s_off);
     const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
     const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
     const uint32_t nbins = sub ? ci.nkeys * kHistWarps : ci.nkeys;
     for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) sh[i] = 0;
     __syncthreads();
-    digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
     uint32_t *bins = sub ? sh + warp * ci.nkeys : sh;
+    for (; k0 < c1; k0 += kChunk) {
+        const bool pf = prefetch_digis(L, k0 + kChunk, c1, pf_m, nullptr);
+        digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        const bool present = k0 + j < ci.c1;
-        const bool ok = present && m[j] < M;
-        if (present && !ok) atomicOr(&L.ws.event_err[e_of[j]], kErrBadDigi);
-        if (!ok) continue;
-        const uint64_t key = (uint64_t)e_of[j] * M + m[j];
-        if (ci.use_sh)
-            atomicAdd(&bins[key - ci.keybase], 1u);
-        else
-            atomicAdd(&L.ws.count[key], 1u);
+        for (int j = 0; j < kPerThread; ++j) {
+            const bool present = k0 + j < c1;
+            const bool ok = present && m[j] < M;
+            if (present && !ok) atomicOr(&L.ws.event_err[e_of[j]], kErrBadDigi);
+            if (!ok) continue;
+            const uint64_t key = (uint64_t)e_of[j] * M + m[j];
+            if (ci.use_sh)
+                atomicAdd(&bins[key - ci.keybase], 1u);
+            else
+                atomicAdd(&L.ws.count2[key], 1u);
+        }
+        if (pf)
+            take_prefetched(pf_m, nullptr, m, nullptr);
+        else if (k0 + kChunk < c1)
+            load_modules(L, k0 + kChunk, c1, m);
     }
     __syncthreads();
+    // the flush's atomic returns this block's offset inside each key's bucket
+    // (the scatter kernel, over the same ranges, places its digis from there)
+    uint32_t *boffs = L.ws.blk_off + (size_t)blockIdx.x * kHistCap;
     for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
         uint32_t v = 0;
         if (sub)
             for (uint32_t w = 0; w < kHistWarps; ++w) v += sh[w * ci.nkeys + i];
         else
             v = sh[i];
-        if (v) atomicAdd(&L.ws.count[ci.keybase + i], v);
+        boffs[i] = v ? atomicAdd(&L.ws.count[ci.keybase + i], v) : 0u;
     }
 }
 
 // ---------------------------------------------------------------- scan
 
+// Per item, count[] holds the digis of histogram blocks that flushed a
+// shared histogram (their runs are reserved, by offset, in blk_off) and
+// count2[] those counted one by one (ranges with too many keys); the scan
+// sets boff = the item's bucket start, cursor = the start of its
+// one-by-one part (after every reserved run) and count = the item's total.
 __global__ void __launch_bounds__(256) scan_kernel(const Launch L)
 {
     __shared__ uint32_t tmp[256 / 32 + 1];
+    if (L.ws.ctl[1] & kErrBadOffsets) return;
     const uint32_t e = blockIdx.x, M = L.g.M;
     const uint64_t kb = (uint64_t)e * M;
     const uint32_t per = (M + 255) / 256;
     const uint32_t m0 = min(M, threadIdx.x * per), m1 = min(M, m0 + per);
     uint32_t local = 0;
-    for (uint32_t m = m0; m < m1; ++m) local += L.ws.count[kb + m];
+    for (uint32_t m = m0; m < m1; ++m) local += L.ws.count[kb + m] + L.ws.count2[kb + m];
     uint32_t total;
     uint32_t run = block_exclusive_scan<256>(local, tmp, &total) + (uint32_t)L.offsets[e];
     for (uint32_t m = m0; m < m1; ++m) {
+        const uint32_t c1 = L.ws.count[kb + m], n = c1 + L.ws.count2[kb + m];
         L.ws.boff[kb + m] = run;
-        L.ws.cursor[kb + m] = run;
-        run += L.ws.count[kb + m];
+        L.ws.cursor[kb + m] = run + c1;
+        L.ws.count[kb + m] = n;
+        run += n;
     }
 }
 
 // Shared memory of the scatter kernel (bytes).
-constexpr size_t kScatterSmem = kHistCap * 4 + kChunk * (4 + 4 + 2) + (2 * kSubKeys + 1) * 4;
+constexpr size_t kScatterSmem = kHistCap * 4 + kChunk * (4 + 4 + 2) + (2 * kSubKeys + 2) * 4 + 16 + kChunk * (2 + 4);
 static_assert(kChunk * (4 + 4 + 2) >= kHistCap * 4, "the staging area also holds the single-histogram bases");
 
-__global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
+// Scatter, persistent, over the histogram kernel's ranges: block b walks its
+// range in steps of kChunk digis (one event search a block; the next step's
+// words and module ids are loaded while the current step is written out,
+// cp.async).  Each key's bucket positions for the block start at the bucket
+// start plus the block's offset from the histogram, so no step needs a
+// global atomic.  Each step ranks its digis per key in shared memory; with
+// few keys it sorts them by key in shared memory and writes each key's run
+// with consecutive threads, else each digi goes straight to its place.  (A
+// range with more keys than a shared histogram holds falls back to global
+// atomics, in both kernels.)
+__global__ void __launch_bounds__(kHistThreads, 2) scatter_kernel(const Launch L)
 {
     extern __shared__ __align__(16) uint32_t sh[];
     uint32_t *cnt = sh;             // counts: per warp sub-histograms, or one histogram
@@ -371,86 +476,114 @@ __global__ void __launch_bounds__(kHistThreads) scatter_kernel(const Launch L)
     uint32_t *stage_i = stage_w + kChunk;                                   // and in-event indices
     uint16_t *stage_k = reinterpret_cast<uint16_t *>(stage_i + kChunk);     // and local keys
     uint32_t *lk = reinterpret_cast<uint32_t *>(stage_k + kChunk);          // block-local start of each key
-    uint32_t *gb = lk + kSubKeys + 1;                                       // bucket position of each key's range
+    uint32_t *gb = lk + kSubKeys + 1;                                       // bucket position of each key's run
     __shared__ uint32_t s_ev[2];
     __shared__ uint64_t s_off[kChunkEvents + 1];
     __shared__ uint32_t s_scan[kHistThreads / 32 + 1];
-    // the chunk's digis are loaded before the event search, so that the two
+    // next step's module ids and words (16-byte aligned for cp.async)
+    uint16_t *pf_m = reinterpret_cast<uint16_t *>((reinterpret_cast<uintptr_t>(gb + kSubKeys + 1) + 15) & ~(uintptr_t)15);
+    uint32_t *pf_w = reinterpret_cast<uint32_t *>(pf_m + kChunk);
+    if (L.ws.ctl[1] & kErrBadOffsets) return;
+    uint64_t c0, c1;
+    block_range(L.N, blockIdx.x, gridDim.x, &c0, &c1);
+    if (c0 >= c1) return;
+    // the first digis are loaded before the event search, so that the two
     // latencies overlap
-    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk, c1 = min(L.N, c0 + (uint64_t)kChunk);
-    const uint64_t k0 = c0 + (uint64_t)threadIdx.x * kPerThread;
+    uint64_t k0 = c0 + (uint64_t)threadIdx.x * kPerThread;
     uint32_t m[kPerThread], e_of[kPerThread], w[kPerThread], rank[kPerThread];
     load_modules(L, k0, c1, m);
     load_words(L, k0, c1, w);
-    const ChunkInfo ci = chunk_info(L, s_ev, s_off);
+    const ChunkInfo ci = chunk_info(L, c0, c1, s_ev, s_off);
     const uint32_t M = L.g.M, warp = threadIdx.x >> 5;
     const bool sub = ci.use_sh && ci.nkeys <= kSubKeys;
     const uint32_t nbins = sub ? ci.nkeys * kHistWarps : ci.nkeys;
-    for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) cnt[i] = 0;
-    __syncthreads();
-    digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
+    const bool off_sh = ci.el - ci.ef + 1 < kChunkEvents;
+    auto event_start = [&](uint32_t e) -> uint64_t { return off_sh ? s_off[e - ci.ef] : L.offsets[e]; };
     uint32_t *bins = sub ? cnt + warp * ci.nkeys : cnt;
-#pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        const bool ok = k0 + j < ci.c1 && m[j] < M;
-        if (!ok) {
-            m[j] = 0xFFFFFFFFu;
-            continue;
-        }
-        const uint64_t key = (uint64_t)e_of[j] * M + m[j];
-        rank[j] = ci.use_sh ? atomicAdd(&bins[key - ci.keybase], 1u) : atomicAdd(&L.ws.cursor[key], 1u);
+    // each key's next bucket position for this block: the bucket start, plus
+    // the block's offset inside the bucket (from the histogram's flush),
+    // advanced step by step
+    uint32_t *kcur = sub ? gb : bas;
+    if (ci.use_sh) {
+        const uint32_t *boffs = L.ws.blk_off + (size_t)blockIdx.x * kHistCap;
+        for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) kcur[i] = L.ws.boff[ci.keybase + i] + boffs[i];
     }
-    __syncthreads();
-    if (sub) {
-        // Few keys: sort the block's digis by key in shared memory, then write
-        // each key's run to its bucket with consecutive threads.  Per key:
-        // per-warp counts become offsets within the key, the key's block
-        // start comes from a scan over keys, and one atomic reserves its range.
-        uint32_t tot = 0;
-        if (threadIdx.x < ci.nkeys) {
-            for (uint32_t wi = 0; wi < kHistWarps; ++wi) {
-                const uint32_t c = cnt[wi * ci.nkeys + threadIdx.x];
-                cnt[wi * ci.nkeys + threadIdx.x] = tot;
-                tot += c;
-            }
-        }
-        uint32_t total;
-        const uint32_t start = block_exclusive_scan<kHistThreads>(tot, s_scan, &total);
-        if (threadIdx.x < ci.nkeys) {
-            lk[threadIdx.x] = start;
-            gb[threadIdx.x] = tot ? atomicAdd(&L.ws.cursor[ci.keybase + threadIdx.x], tot) : 0u;
-        }
+    for (uint64_t s0 = c0;; s0 += kChunk, k0 += kChunk) {
+        for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) cnt[i] = 0;
         __syncthreads();
+        const bool more = s0 + kChunk < c1; // another step follows
+        const bool pf = more && prefetch_digis(L, k0 + kChunk, c1, pf_m, pf_w);
+        digi_events(L, s_off, ci.ef, ci.el, k0, e_of);
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
-            if (m[j] == 0xFFFFFFFFu) continue;
-            const uint32_t key = (uint32_t)((uint64_t)e_of[j] * M + m[j] - ci.keybase);
-            const uint32_t p = lk[key] + cnt[warp * ci.nkeys + key] + rank[j];
-            stage_w[p] = w[j];
-            stage_i[p] = (uint32_t)(k0 + j - L.offsets[e_of[j]]);
-            stage_k[p] = (uint16_t)key;
+            const bool ok = k0 + j < ci.c1 && m[j] < M;
+            if (!ok) {
+                m[j] = 0xFFFFFFFFu;
+                continue;
+            }
+            const uint64_t key = (uint64_t)e_of[j] * M + m[j];
+            rank[j] = ci.use_sh ? atomicAdd(&bins[key - ci.keybase], 1u) : atomicAdd(&L.ws.cursor[key], 1u);
         }
         __syncthreads();
-        for (uint32_t p = threadIdx.x; p < total; p += kHistThreads) {
-            const uint32_t key = stage_k[p];
-            const uint32_t g = gb[key] + (p - lk[key]);
-            L.ws.bucket_w[g] = stage_w[p];
-            L.ws.bucket_i[g] = stage_i[p];
-        }
-        return;
-    }
-    for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
-        const uint32_t v = cnt[i];
-        if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
-    }
-    __syncthreads();
+        if (sub) {
+            // Per key: per-warp counts become offsets within the key, the
+            // key's block start comes from a scan over keys, and one atomic
+            // reserves its run in the bucket.
+            uint32_t tot = 0;
+            if (threadIdx.x < ci.nkeys) {
+                for (uint32_t wi = 0; wi < kHistWarps; ++wi) {
+                    const uint32_t c = cnt[wi * ci.nkeys + threadIdx.x];
+                    cnt[wi * ci.nkeys + threadIdx.x] = tot;
+                    tot += c;
+                }
+            }
+            uint32_t total;
+            const uint32_t start = block_exclusive_scan<kHistThreads>(tot, s_scan, &total);
+            uint32_t kg = 0;
+            if (threadIdx.x < ci.nkeys) {
+                lk[threadIdx.x] = start;
+                kg = gb[threadIdx.x];
+            }
+            __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        if (m[j] == 0xFFFFFFFFu) continue;
-        const uint64_t key = (uint64_t)e_of[j] * M + m[j];
-        const uint32_t p = ci.use_sh ? bas[key - ci.keybase] + rank[j] : rank[j];
-        L.ws.bucket_w[p] = w[j];
-        L.ws.bucket_i[p] = (uint32_t)(k0 + j - L.offsets[e_of[j]]);
+            for (int j = 0; j < kPerThread; ++j) {
+                if (m[j] == 0xFFFFFFFFu) continue;
+                const uint32_t key = (uint32_t)((uint64_t)e_of[j] * M + m[j] - ci.keybase);
+                const uint32_t p = lk[key] + cnt[warp * ci.nkeys + key] + rank[j];
+                stage_w[p] = w[j];
+                stage_i[p] = (uint32_t)(k0 + j - event_start(e_of[j]));
+                stage_k[p] = (uint16_t)key;
+            }
+            __syncthreads();
+            for (uint32_t p = threadIdx.x; p < total; p += kHistThreads) {
+                const uint32_t key = stage_k[p];
+                const uint32_t g = gb[key] + (p - lk[key]);
+                L.ws.bucket_w[g] = stage_w[p];
+                L.ws.bucket_i[g] = stage_i[p];
+            }
+            __syncthreads();
+            if (threadIdx.x < ci.nkeys) gb[threadIdx.x] = kg + tot; // the key's cursor after this step
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPerThread; ++j) {
+                if (m[j] == 0xFFFFFFFFu) continue;
+                const uint64_t key = (uint64_t)e_of[j] * M + m[j];
+                const uint32_t p = ci.use_sh ? bas[key - ci.keybase] + rank[j] : rank[j];
+                L.ws.bucket_w[p] = w[j];
+                L.ws.bucket_i[p] = (uint32_t)(k0 + j - event_start(e_of[j]));
+            }
+            __syncthreads();
+            if (ci.use_sh)
+                for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) bas[i] += cnt[i];
+        }
+        __syncthreads();
+        if (!more) break;
+        if (pf) {
+            take_prefetched(pf_m, pf_w, m, w);
+        } else {
+            load_modules(L, k0 + kChunk, c1, m);
+            load_words(L, k0 + kChunk, c1, w);
+        }
     }
 }
 
@@ -1503,6 +1636,7 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
     // block-tier items start from zeroed bitmaps and leave them zeroed
     clear_words(abits, nwords);
     clear_words(sbits, nwords);
+    if (L.ws.ctl[1] & kErrBadOffsets) return;
     // each item's count of kept clusters goes to kcount[item]; the ordered
     // output is written by offsets_kernel and copy_kernel
     uint32_t *kcount = L.ws.cursor;
@@ -1623,6 +1757,7 @@ __global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
     const uint32_t tid = threadIdx.x, M = L.g.M;
     const uint64_t EM = (uint64_t)L.E * M;
     const uint64_t nchunks = (EM + kOffItems - 1) / kOffItems;
+    if (L.ws.ctl[1] & kErrBadOffsets) return;
     if (tid == 0) s_chunk = atomicAdd(&L.ws.ctl[4], 1u);
     __syncthreads();
     const uint64_t c = s_chunk;
@@ -1688,15 +1823,19 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
     const uint32_t lane = threadIdx.x & 31, M = L.g.M;
     const uint64_t EM = (uint64_t)L.E * M;
     const uint64_t gt = (uint64_t)blockIdx.x * kCopyThreads + threadIdx.x;
+    const bool bad_offsets = (L.ws.ctl[1] & kErrBadOffsets) != 0;
+    if (bad_offsets && gt <= L.E) L.out.cluster_offsets[gt] = 0; // no clusters
     if (gt < L.E) {
         const uint32_t bits = L.ws.event_err[gt] | L.ws.ctl[1];
         int32_t st = 0;                          // HP_OK
-        if (bits & kErrTimeout) st = 8;          // HP_ETIMEOUT
+        if (bits & kErrBadOffsets) st = 3;       // HP_EINVAL
+        else if (bits & kErrTimeout) st = 8;     // HP_ETIMEOUT
         else if (bits & kErrCapacity) st = 6;    // HP_ECAPACITY
         else if (bits & kErrBadDigi) st = 4;     // HP_EBADDIGI
         else if (bits & kErrDup) st = 5;         // HP_EDUP
         L.out.event_status[gt] = st;
     }
+    if (bad_offsets) return;
     const Staging sg = L.ws.staging;
     const unsigned long long cap = L.out.capacity;
     const uint64_t warps = (uint64_t)gridDim.x * (kCopyThreads / 32);
@@ -1757,7 +1896,7 @@ size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots)
 }
 
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
-                       const Tuning &tune, Workspace *ws)
+                       const Tuning &tune, Workspace *ws, int sm_count)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) -> unsigned char * {
@@ -1772,10 +1911,12 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     w.ctl = reinterpret_cast<uint32_t *>(take(64));
     w.event_err = reinterpret_cast<uint32_t *>(take(4ull * E));
     w.count = reinterpret_cast<uint32_t *>(take(4ull * EM));
+    w.count2 = reinterpret_cast<uint32_t *>(take(4ull * EM));
     w.chain = reinterpret_cast<unsigned long long *>(take(16ull * nchunks)); // aggregates, then inclusive prefixes
     off = (off + 255) & ~(size_t)255;
     w.zero_bytes = off;
     w.boff = reinterpret_cast<uint32_t *>(take(4ull * EM));
+    w.blk_off = reinterpret_cast<uint32_t *>(take(4ull * kHistCap * bucket_grid(N, sm_count)));
     w.cursor = reinterpret_cast<uint32_t *>(take(4ull * EM));
     w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
@@ -1858,9 +1999,11 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     };
     uint64_t nk = 0;
     const uint64_t nchunks = (L.N + kChunk - 1) / kChunk;
+    // persistent histogram and scatter over the same contiguous ranges
+    const unsigned hist_grid = bucket_grid(L.N, L.sm_count), scat_grid = hist_grid; // the same ranges
     mark(0);
     if (L.N > 0) {
-        hist_kernel<<<(unsigned)nchunks, kHistThreads, kHistCap * sizeof(uint32_t), stream>>>(L);
+        hist_kernel<<<hist_grid, kHistThreads, kHistCap * sizeof(uint32_t), stream>>>(L);
         ++nk;
     }
     mark(1);
@@ -1868,7 +2011,7 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     ++nk;
     mark(2);
     if (L.N > 0) {
-        scatter_kernel<<<(unsigned)nchunks, kHistThreads, kScatterSmem, stream>>>(L);
+        scatter_kernel<<<scat_grid, kHistThreads, kScatterSmem, stream>>>(L);
         ++nk;
     }
     mark(3);
@@ -1885,9 +2028,9 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     offsets_kernel<<<(unsigned)((EM + kOffItems - 1) / kOffItems), kOffThreads, 0, stream>>>(L);
     ++nk;
     mark(5);
-    {   // a warp per item (at most copy_grid blocks, looping), and a thread per event status
+    {   // a warp per item (at most copy_grid blocks, looping), and a thread per event status and offset
         const uint64_t by_items = (EM + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
-        const uint64_t by_events = ((uint64_t)L.E + kCopyThreads - 1) / kCopyThreads;
+        const uint64_t by_events = ((uint64_t)L.E + kCopyThreads) / kCopyThreads; // E + 1 offsets
         const uint64_t blocks =
             std::max<uint64_t>(1, std::max<uint64_t>(by_events, std::min<uint64_t>(by_items, (uint64_t)L.copy_grid)));
         copy_kernel<<<(unsigned)blocks, kCopyThreads, 0, stream>>>(L);

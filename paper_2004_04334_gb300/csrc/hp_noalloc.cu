@@ -27,8 +27,10 @@ std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on `device` (current), looked up once per
-// device.  In host code g_scratch names a host-side stand-in, never the
-// device memory itself.
+// device (and kept for the process: after a cudaDeviceReset the module is
+// reloaded elsewhere, so the entry point must not be used after a reset).
+// In host code g_scratch names a host-side stand-in, never the device memory
+// itself.
 cudaError_t scratch_address(int device, void **out)
 {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -49,15 +51,13 @@ extern "C" hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_event
                                                    const uint16_t *d_module_ids, const hp_device_clusters *out,
                                                    void *stream)
 {
-    if (!ctx || !out || !d_offsets || n_events < 1) return HP_EINVAL;
-    if (n_digis > 0 && (!d_words || !d_module_ids)) return HP_EINVAL;
-    if (((uintptr_t)d_words & 3) || ((uintptr_t)d_module_ids & 1) || ((uintptr_t)d_offsets & 7)) return HP_EINVAL;
-    if (!out->module || !out->id || !out->charge || !out->npix || !out->x || !out->y || !out->cluster_offsets ||
-        !out->event_status)
-        return HP_EINVAL;
+    // the same argument checks as hp_reconstruct_device (a failed context
+    // reports HP_ECUDA)
+    const int chk = hp::check_device_call(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out);
+    if (chk != HP_OK) return (hp_status)chk;
     hp::Geometry g;
-    int device = 0, grid = 0;
-    if (!hp::context_launch_params(ctx, &g, &device, &grid)) return HP_ECUDA;
+    int device = 0, grid = 0, sms = 0;
+    if (!hp::context_launch_params(ctx, &g, &device, &grid, &sms)) return HP_ECUDA;
     if (device < 0 || device >= kMaxDevices) return HP_EINVAL;
     const uint64_t items = (uint64_t)n_events * g.M;
     if (n_digis > kMaxDigis || items > kMaxItems) return HP_ECAPACITY;
@@ -66,13 +66,13 @@ extern "C" hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_event
     if (grid > kMaxGrid) grid = kMaxGrid;
     if (grid < 1) grid = 1;
     const hp::Tuning tune; // the default tuning: the scratch limits are sized for it
-    if (hp::carve_workspace(nullptr, n_events, g.M, n_digis, g.R, g.C, grid, tune, nullptr) > kScratchBytes)
+    if (hp::carve_workspace(nullptr, n_events, g.M, n_digis, g.R, g.C, grid, tune, nullptr, sms) > kScratchBytes)
         return HP_ECAPACITY;
-    if (cudaSetDevice(device) != cudaSuccess) return HP_ECUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return (hp_status)hp::context_fail(ctx);
     void *base = nullptr;
     if (scratch_address(device, &base) != cudaSuccess) {
         cudaGetLastError();
-        return HP_ECUDA;
+        return (hp_status)hp::context_fail(ctx);
     }
     hp::Launch L;
     L.g = g;
@@ -91,14 +91,15 @@ extern "C" hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_event
     L.out.cluster_offsets = out->cluster_offsets;
     L.out.event_status = out->event_status;
     L.out.label = out->label;
-    hp::carve_workspace(base, n_events, g.M, n_digis, g.R, g.C, grid, tune, &L.ws);
+    hp::carve_workspace(base, n_events, g.M, n_digis, g.R, g.C, grid, tune, &L.ws, sms);
     L.cc_grid = grid;
     L.copy_grid = 4 * grid;
+    L.sm_count = sms;
     L.tune = tune;
     uint64_t nk = 0;
     if (hp::launch_reconstruct(L, static_cast<cudaStream_t>(stream), &nk, nullptr) != cudaSuccess) {
         cudaGetLastError();
-        return HP_ECUDA;
+        return (hp_status)hp::context_fail(ctx); // as hp_reconstruct_device: the context is failed
     }
     return HP_OK;
 }

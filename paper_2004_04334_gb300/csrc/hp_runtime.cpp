@@ -684,7 +684,7 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     const Shape sh = shape_for(ctx, E, N);
     const int grid = sh.grid;
     const size_t ws_bytes = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols,
-                                                grid, sh.tune, nullptr);
+                                                grid, sh.tune, nullptr, ctx->sm_count);
     size_t doff = 0;
     const size_t d_words = doff;
     doff = align_up(doff + 4 * N, 256);
@@ -841,9 +841,10 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     L.out.label = labels ? reinterpret_cast<int32_t *>(keep ? ob + o_label : db + d_label) : nullptr;
     ev->dv = L.out;
     if (!keep) ev->dv.label = nullptr; // the device labels go back to the pool at completion
-    hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, sh.tune, &L.ws);
+    hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, sh.tune, &L.ws, ctx->sm_count);
     L.cc_grid = grid;
     L.copy_grid = ctx->sm_count * 8;
+    L.sm_count = ctx->sm_count;
     L.tune = sh.tune;
     L.debug = take_debug(ctx);
     ev->path = offsets ? HP_PATH_BATCH : HP_PATH_EVENT;
@@ -1002,7 +1003,7 @@ BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
     BatchLayout l;
     l.sh = shape_for(ctx, E, N);
     const size_t ws = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols,
-                                          l.sh.grid, l.sh.tune, nullptr);
+                                          l.sh.grid, l.sh.tune, nullptr, ctx->sm_count);
     size_t d = 0;
     l.d_words = d;
     d = align_up(d + 4 * N, 256);
@@ -1122,9 +1123,10 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     L.out.event_status = reinterpret_cast<int32_t *>(hd + l.h_status);
     L.out.label = labels ? reinterpret_cast<int32_t *>(db + l.d_label) : nullptr;
     hp::carve_workspace(db + l.d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.sh.grid, l.sh.tune,
-                        &L.ws);
+                        &L.ws, ctx->sm_count);
     L.cc_grid = l.sh.grid;
     L.copy_grid = ctx->sm_count * 8;
+    L.sm_count = ctx->sm_count;
     L.tune = l.sh.tune;
 
     const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
@@ -1356,9 +1358,10 @@ cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const 
     L.out.event_status = out->event_status;
     L.out.label = out->label;
     hp::carve_workspace(base, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows, ctx->cfg.cols, sh.grid, sh.tune,
-                        &L.ws);
+                        &L.ws, ctx->sm_count);
     L.cc_grid = sh.grid;
     L.copy_grid = ctx->sm_count * 8;
+    L.sm_count = ctx->sm_count;
     L.tune = sh.tune;
     L.debug = debug;
     return hp::launch_reconstruct(L, s, nk, marks);
@@ -1375,14 +1378,24 @@ void destroy_graph(hp_graph *g)
 
 } // namespace
 
-bool hp::context_launch_params(hp_ctx *ctx, hp::Geometry *g, int *device, int *cc_grid)
+bool hp::context_launch_params(hp_ctx *ctx, hp::Geometry *g, int *device, int *cc_grid, int *sm_count)
 {
     if (!ctx || ctx->failed.load()) return false;
     *g = geometry(ctx);
     *device = ctx->device;
     *cc_grid = ctx->sm_count * (int)hp::Tuning().blocks_per_sm;
+    *sm_count = ctx->sm_count;
     return true;
 }
+
+int hp::check_device_call(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
+                          const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out)
+{
+    return check_device_args(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out);
+}
+
+int hp::context_fail(hp_ctx *ctx) { return fail(ctx); }
+
 
 extern "C" {
 
@@ -1878,7 +1891,7 @@ hp_status hp_reconstruct_device(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis
     }
     const Shape sh = shape_for(ctx, n_events, n_digis);
     const size_t need = hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
-                                            ctx->cfg.cols, sh.grid, sh.tune, nullptr);
+                                            ctx->cfg.cols, sh.grid, sh.tune, nullptr, ctx->sm_count);
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> g(ctx->ws_mu);
@@ -1960,7 +1973,7 @@ hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const ui
     for (const hp::Tuning &t : cands) {
         const Shape sh = shape_with(ctx, n_events, t);
         need = std::max(need, hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
-                                                  ctx->cfg.cols, sh.grid, sh.tune, nullptr));
+                                                  ctx->cfg.cols, sh.grid, sh.tune, nullptr, ctx->sm_count));
     }
     void *ws = nullptr;
     if (cudaMalloc(&ws, need) != cudaSuccess) {
@@ -2029,7 +2042,7 @@ hp_status hp_graph_capture(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, con
     g->ctx = ctx;
     const Shape sh = shape_for(ctx, n_events, n_digis);
     const size_t need = hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
-                                            ctx->cfg.cols, sh.grid, sh.tune, nullptr);
+                                            ctx->cfg.cols, sh.grid, sh.tune, nullptr, ctx->sm_count);
     if (cudaMalloc(&g->ws, need) != cudaSuccess) {
         cudaGetLastError();
         delete g;
