@@ -1,4 +1,7 @@
 """Comparison helpers for GPU-vs-oracle parity tests."""
+import concurrent.futures as cf
+import os
+
 import numpy as np
 
 # Centroids: FP32 on the GPU vs the FP64 oracle, within 1e-4 pixel.
@@ -37,3 +40,30 @@ def assert_batch_matches(got, ref, offsets, check_labels=True):
             s, t = int(offsets[e]), int(offsets[e + 1])
             lg, lr = got.label[s:t], ref.label[s:t]
         assert_event_matches(got, ref, e, labels_got=lg, labels_ref=lr)
+
+
+def oracle_events(w, events=None, **kw):
+    """The oracle's result for each event of workload w (one oracle call per
+    event, on the host's cores; the oracle releases the GIL)."""
+    from oracle import oracle
+
+    events = list(range(w.n_events)) if events is None else list(events)
+
+    def one(e):
+        words, mods = w.event(e)
+        return oracle.reconstruct_event(words, mods, w.n_modules, w.gain, w.pedestal, **kw)
+
+    with cf.ThreadPoolExecutor(min(len(events), os.cpu_count() or 1) or 1) as ex:
+        return list(ex.map(one, events))
+
+
+def assert_events_match(got, refs, offsets, events=None):
+    """Compare every event e of a GPU batch result with refs[j], the oracle's
+    result for that event alone (j-th of `events`, default all)."""
+    events = range(got.n_events) if events is None else events
+    for j, e in enumerate(events):
+        s, t = int(offsets[e]), int(offsets[e + 1])
+        ref = refs[j]
+        lg = got.label[s:t] if got.label is not None and int(ref.event_status[0]) == 0 else None
+        lr = ref.label if lg is not None else None
+        assert_event_matches(got, ref, e, 0, lg, lr)

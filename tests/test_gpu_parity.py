@@ -9,7 +9,8 @@ import pytest
 from oracle import oracle
 from paper_2004_04334_gb300 import hp, synth
 from tests import shapes
-from tests.gpu_util import CENTROID_TOL, assert_batch_matches, assert_event_matches
+from tests.gpu_util import CENTROID_TOL, assert_batch_matches, assert_event_matches, assert_events_match, \
+    oracle_events
 
 pytestmark = pytest.mark.gpu
 
@@ -223,12 +224,7 @@ def test_device_path_full_batched_workload(torch_cuda):
     assert_batch_matches(got, ref, w.offsets)
 
 
-def test_device_path_occupancy_sampled(torch_cuda):
-    """All 64 high-occupancy events in one device launch; 6 sampled events
-    checked in full against the oracle, all events against invariants."""
-    torch = torch_cuda
-    w = synth.workload("occupancy")
-    ctx = ctx_for(w.n_modules, w.gain, w.pedestal)
+def _device_run(torch, ctx, w):
     dev = torch.device("cuda:0")
     d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
     d_mods = torch.from_numpy(w.modules.view(np.int16)).to(dev)
@@ -237,24 +233,94 @@ def test_device_path_occupancy_sampled(torch_cuda):
     ctx.reconstruct_device(w.n_events, w.n_digis, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
                            torch.cuda.current_stream(dev).cuda_stream)
     torch.cuda.synchronize()
-    got = out.to_result(w.n_digis)
+    return out.to_result(w.n_digis)
+
+
+def test_device_path_occupancy_every_event(torch_cuda):
+    """All 64 high-occupancy events (~229M digis, hot modules at 20%
+    occupancy) in one device launch with the autotuned settings, every event
+    element by element against the oracle (run event by event on the host's
+    cores)."""
+    torch = torch_cuda
+    w = synth.workload("occupancy")
+    ctx = ctx_for(w.n_modules, w.gain, w.pedestal)
+    dev = torch.device("cuda:0")
+    d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
+    d_mods = torch.from_numpy(w.modules.view(np.int16)).to(dev)
+    d_offs = torch.from_numpy(w.offsets.view(np.int64)).to(dev)
+    out = hp.DeviceOutputs(w.n_events, w.n_digis, dev)
+    ctx.autotune(w.n_events, w.n_digis, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out, reps=1)
+    got = _device_run(torch, ctx, w)
     assert np.all(got.event_status == 0)
-    sample = [0, 9, 21, 33, 47, 63]
-    sub = w.subset(sample)
-    ref = oracle.reconstruct_workload(sub)
-    for j, e in enumerate(sample):
-        s, t = int(w.offsets[e]), int(w.offsets[e + 1])
-        u, v = int(sub.offsets[j]), int(sub.offsets[j + 1])
-        assert_event_matches(got, ref, e, j, got.label[s:t], ref.label[u:v])
-    # every event: kept charge equals the charge of labelled pixels (any size)
-    q = ((w.words.astype(np.int64) >> 17) & 0xFF) * w.gain[w.modules].astype(np.int64) - \
-        w.pedestal[w.modules].astype(np.int64)
-    for e in range(w.n_events):
-        s, t = int(w.offsets[e]), int(w.offsets[e + 1])
-        a, b = int(got.cluster_offsets[e]), int(got.cluster_offsets[e + 1])
-        lab = got.label[s:t]
-        assert int(got.charge[a:b].astype(np.int64).sum()) == int(q[s:t][lab >= 0].sum())
-        assert int(got.npix[a:b].sum()) == int((lab >= 0).sum())
+    assert_events_match(got, oracle_events(w), w.offsets)
+
+
+def test_many_small_events_on_large_geometry(torch_cuda):
+    """Events of 1856 modules with ~100 digis each, so that one histogram
+    range spans more (event, module) keys than a shared histogram holds (the
+    one-by-one counting path), between ranges of large events that reserve
+    their runs in bulk; device and host paths."""
+    torch = torch_cuda
+    big = synth.workload("full", n_events=3)
+    ws, ms, offs = [], [], [0]
+    for e in range(3):
+        words, mods = big.event(e)
+        ws.append(words)
+        ms.append(mods)
+        offs.append(offs[-1] + len(words))
+        if e < 2:
+            for k in range(40):
+                sub_w, sub_m = big.event((e + 1) % 3)
+                sel = np.random.default_rng(100 * e + k).choice(len(sub_w), 100, replace=False)
+                ws.append(sub_w[sel])
+                ms.append(sub_m[sel])
+                offs.append(offs[-1] + 100)
+    words, mods, offs = np.concatenate(ws), np.concatenate(ms), np.asarray(offs, np.uint64)
+    ref = oracle.reconstruct_batch(words, mods, offs, big.n_modules, big.gain, big.pedestal)
+    ctx = ctx_for(big.n_modules, big.gain, big.pedestal)
+    got = run_batch(ctx, words, mods, offs)
+    assert_batch_matches(got, ref, offs)
+    dev = torch.device("cuda:0")
+    out = hp.DeviceOutputs(len(offs) - 1, len(words), dev)
+    d_offs = torch.from_numpy(offs.view(np.int64)).to(dev)  # held until the pass has run
+    d_words = torch.from_numpy(words.view(np.int32)).to(dev)
+    d_mods = torch.from_numpy(mods.view(np.int16)).to(dev)
+    ctx.reconstruct_device(len(offs) - 1, len(words), d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
+                           torch.cuda.current_stream(dev).cuda_stream)
+    torch.cuda.synchronize()
+    assert_batch_matches(out.to_result(len(words)), ref, offs)
+
+
+@pytest.mark.parametrize("kind", ["short_last", "decreasing", "nonzero_first"])
+def test_malformed_offsets_report_einval(torch_cuda, kind):
+    """Device entry with event offsets that do not run 0 <= ... <= N (all
+    within the digi arrays, so nothing is read out of bounds): every event
+    reports HP_EINVAL with no clusters, and the next call with good offsets
+    is exact."""
+    torch = torch_cuda
+    w = synth.workload("tiny", n_events=4)
+    ctx = ctx_for(w.n_modules, w.gain, w.pedestal)
+    offs = w.offsets.copy()
+    if kind == "short_last":
+        offs[-1] -= 5
+    elif kind == "decreasing":
+        offs[2] = offs[1] - 1
+    else:
+        offs[0] = 1
+    dev = torch.device("cuda:0")
+    d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
+    d_mods = torch.from_numpy(w.modules.view(np.int16)).to(dev)
+    out = hp.DeviceOutputs(w.n_events, w.n_digis, dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    d_offs = torch.from_numpy(offs.view(np.int64)).to(dev)  # held until the pass has run
+    ctx.reconstruct_device(w.n_events, w.n_digis, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
+                           stream)
+    torch.cuda.synchronize()
+    bad = out.to_result(w.n_digis)
+    assert bad.event_status.tolist() == [hp.HP_EINVAL] * w.n_events
+    assert int(bad.cluster_offsets[-1]) == 0
+    got = _device_run(torch, ctx, w)
+    assert_batch_matches(got, oracle.reconstruct_workload(w), w.offsets)
 
 
 @pytest.mark.parametrize("rows,cols", [(40, 100), (50, 120)])

@@ -10,7 +10,7 @@ import pytest
 
 from oracle import oracle
 from paper_2004_04334_gb300 import hp, synth
-from tests.gpu_util import assert_batch_matches
+from tests.gpu_util import assert_batch_matches, oracle_events
 
 pytestmark = pytest.mark.gpu
 
@@ -71,11 +71,11 @@ def test_mix_equals_alone(pool):
         r, a = results[i], alone[e]
         for f in ("module", "id", "charge", "npix", "x", "y", "label"):
             assert np.array_equal(getattr(r, f), getattr(a, f)), (i, f)
-    # and the alone results are the oracle's
-    for e in (0, 5, 11):
-        words, mods = w.event(e)
-        ref = oracle.reconstruct_event(words, mods, w.n_modules, w.gain, w.pedestal)
-        assert_batch_matches(alone[e], ref, np.array([0, len(words)], np.uint64))
+    # and the alone results (so the mixed ones too) are the oracle's, for
+    # every event of the pool
+    refs = oracle_events(w)
+    for e in range(w.n_events):
+        assert_batch_matches(alone[e], refs[e], np.array([0, int(w.offsets[e + 1] - w.offsets[e])], np.uint64))
 
 
 def test_budget_admits_one_batch_at_a_time(pool):
