@@ -97,12 +97,12 @@ struct Workspace {
     uint32_t *event_err;  // [E]
     uint32_t *count;      // [E*M] digis of each item (reserved part, then the total: scan_kernel);
                           //       then each item's first output position (offsets_kernel)
-    uint32_t *count2;     // [E*M] digis counted one by one (histogram ranges with too many keys)
+    uint32_t *count2;     // [E*M] digis of histogram ranges with many keys (placed step by step)
     unsigned long long *chain; // [2 * n_chunks]: offsets_kernel chunk totals, then inclusive prefixes
     size_t zero_bytes;
     uint32_t *boff;       // [E*M] bucket start of each item
     uint32_t *blk_off;    // [bucket_grid * kHistCap] each histogram block's offset inside each key's bucket
-    uint32_t *cursor;     // [E*M] scatter cursor of the one-by-one part; then each item's count of kept
+    uint32_t *cursor;     // [E*M] scatter cursor of the step-by-step part; then each item's count of kept
                           //       clusters (cc_kernel)
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event

@@ -412,26 +412,30 @@ __global__ void __launch_bounds__(kHistThreads, 3) hist_kernel(const Launch L)
             load_modules(L, k0 + kChunk, c1, m);
     }
     __syncthreads();
-    // the flush's atomic returns this block's offset inside each key's bucket
-    // (the scatter kernel, over the same ranges, places its digis from there)
+    // With few keys (long runs per key) the flush's atomic returns this
+    // block's offset inside each key's bucket, and the scatter kernel (over
+    // the same ranges) places its digis from there; with many keys the
+    // counts go to count2 and the scatter hands out positions step by step,
+    // so that blocks running at the same time fill neighbouring positions.
     uint32_t *boffs = L.ws.blk_off + (size_t)blockIdx.x * kHistCap;
     for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
-        uint32_t v = 0;
-        if (sub)
+        if (sub) {
+            uint32_t v = 0;
             for (uint32_t w = 0; w < kHistWarps; ++w) v += sh[w * ci.nkeys + i];
-        else
-            v = sh[i];
-        boffs[i] = v ? atomicAdd(&L.ws.count[ci.keybase + i], v) : 0u;
+            boffs[i] = v ? atomicAdd(&L.ws.count[ci.keybase + i], v) : 0u;
+        } else if (sh[i]) {
+            atomicAdd(&L.ws.count2[ci.keybase + i], sh[i]);
+        }
     }
 }
 
 // ---------------------------------------------------------------- scan
 
-// Per item, count[] holds the digis of histogram blocks that flushed a
-// shared histogram (their runs are reserved, by offset, in blk_off) and
-// count2[] those counted one by one (ranges with too many keys); the scan
-// sets boff = the item's bucket start, cursor = the start of its
-// one-by-one part (after every reserved run) and count = the item's total.
+// Per item, count[] holds the digis of histogram blocks with few keys
+// (their runs are reserved, by offset, in blk_off) and count2[] those of
+// blocks with many keys (placed step by step by the scatter); the scan sets
+// boff = the item's bucket start, cursor = the start of the step-by-step
+// part (after every reserved run) and count = the item's total.
 __global__ void __launch_bounds__(256) scan_kernel(const Launch L)
 {
     __shared__ uint32_t tmp[256 / 32 + 1];
@@ -460,13 +464,13 @@ static_assert(kChunk * (4 + 4 + 2) >= kHistCap * 4, "the staging area also holds
 // Scatter, persistent, over the histogram kernel's ranges: block b walks its
 // range in steps of kChunk digis (one event search a block; the next step's
 // words and module ids are loaded while the current step is written out,
-// cp.async).  Each key's bucket positions for the block start at the bucket
-// start plus the block's offset from the histogram, so no step needs a
-// global atomic.  Each step ranks its digis per key in shared memory; with
-// few keys it sorts them by key in shared memory and writes each key's run
-// with consecutive threads, else each digi goes straight to its place.  (A
-// range with more keys than a shared histogram holds falls back to global
-// atomics, in both kernels.)
+// cp.async).  Each step ranks its digis per key in shared memory.  With few
+// keys it sorts them by key in shared memory and writes each key's run with
+// consecutive threads, from the block's offset inside the bucket (reserved
+// by the histogram's flush), so no step needs a global atomic.  With many
+// keys one global atomic per key and step hands out the positions (after
+// the reserved runs), and each digi goes straight to its place; a range
+// with more keys than a shared histogram holds takes one atomic per digi.
 __global__ void __launch_bounds__(kHistThreads, 2) scatter_kernel(const Launch L)
 {
     extern __shared__ __align__(16) uint32_t sh[];
@@ -503,10 +507,9 @@ __global__ void __launch_bounds__(kHistThreads, 2) scatter_kernel(const Launch L
     // each key's next bucket position for this block: the bucket start, plus
     // the block's offset inside the bucket (from the histogram's flush),
     // advanced step by step
-    uint32_t *kcur = sub ? gb : bas;
-    if (ci.use_sh) {
+    if (sub) {
         const uint32_t *boffs = L.ws.blk_off + (size_t)blockIdx.x * kHistCap;
-        for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) kcur[i] = L.ws.boff[ci.keybase + i] + boffs[i];
+        for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) gb[i] = L.ws.boff[ci.keybase + i] + boffs[i];
     }
     for (uint64_t s0 = c0;; s0 += kChunk, k0 += kChunk) {
         for (uint32_t i = threadIdx.x; i < nbins; i += kHistThreads) cnt[i] = 0;
@@ -564,6 +567,11 @@ __global__ void __launch_bounds__(kHistThreads, 2) scatter_kernel(const Launch L
             __syncthreads();
             if (threadIdx.x < ci.nkeys) gb[threadIdx.x] = kg + tot; // the key's cursor after this step
         } else {
+            for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) {
+                const uint32_t v = cnt[i];
+                if (v) bas[i] = atomicAdd(&L.ws.cursor[ci.keybase + i], v);
+            }
+            __syncthreads();
 #pragma unroll
             for (int j = 0; j < kPerThread; ++j) {
                 if (m[j] == 0xFFFFFFFFu) continue;
@@ -572,9 +580,6 @@ __global__ void __launch_bounds__(kHistThreads, 2) scatter_kernel(const Launch L
                 L.ws.bucket_w[p] = w[j];
                 L.ws.bucket_i[p] = (uint32_t)(k0 + j - event_start(e_of[j]));
             }
-            __syncthreads();
-            if (ci.use_sh)
-                for (uint32_t i = threadIdx.x; i < ci.nkeys; i += kHistThreads) bas[i] += cnt[i];
         }
         __syncthreads();
         if (!more) break;
