@@ -76,6 +76,10 @@ typedef enum hp_status {
 #define HP_KEEP_ON_DEVICE 0x4u /* enqueue: keep the clusters (and labels) in device
                                   memory until release; nothing but per-event status
                                   and offsets goes to the host (see hp_enqueue_transfer) */
+#define HP_LABELS_U16 0x8u /* labels in the compact form (implies HP_WANT_LABELS):
+                              hp_clusters.label16 and .item_first instead of .label,
+                              2 bytes a digi instead of 4 over the host link; not with
+                              HP_KEEP_ON_DEVICE (HP_EINVAL) */
 
 /* what of hp_enqueue_transfer */
 #define HP_TRANSFER_CLUSTERS 0x1u
@@ -129,7 +133,15 @@ typedef struct hp_clusters {
     const float *x;                  /* charge-weighted mean row */
     const float *y;                  /* charge-weighted mean column */
     const int32_t *label;            /* [n_digis] cluster id, -1 (pixel below threshold),
-                                        -2 (cluster below threshold); NULL without HP_WANT_LABELS */
+                                        -2 (cluster below threshold); NULL without HP_WANT_LABELS
+                                        and with HP_LABELS_U16 */
+    /* HP_LABELS_U16 (else NULL).  Digi i of event e on module m belongs to
+     * cluster cluster_offsets[e] + item_first[e * n_modules + m] + label16[i]
+     * when label16[i] < 0xFFFE; 0xFFFF marks a pixel below threshold, 0xFFFE
+     * a cluster below threshold (the -1 and -2 of .label).  A module holds at
+     * most ceil(rows/2) * ceil(cols/2) <= 32768 clusters, so the rank fits. */
+    const uint16_t *label16;         /* [n_digis] rank of the digi's cluster among its module's */
+    const uint32_t *item_first;      /* [n_events * n_modules] first cluster of (e, m), from e's first */
 } hp_clusters;
 
 /*
@@ -184,9 +196,11 @@ typedef struct hp_serve_config {
     uint64_t max_batch_digis;      /* digis per batch; 0 = 32 Mi */
     uint32_t max_inflight_batches; /* batches on the device at once; 0 = 3 */
     uint32_t max_pending;          /* queued requests before hp_submit says HP_EAGAIN; 0 = 65536 */
-    uint32_t flags;                /* HP_WANT_LABELS; HP_INPUT_NOCOPY: hp_submit does not copy the inputs,
-                                      the batch copies them by DMA, so they must stay valid (and should
-                                      be pinned) until the request completes */
+    uint32_t flags;                /* HP_WANT_LABELS or HP_LABELS_U16; HP_INPUT_NOCOPY: hp_submit does not
+                                      copy the inputs, the batch's gather kernel reads them in place
+                                      (pinned memory, or any host memory on hosts whose device reads
+                                      pageable memory), else one DMA each; they must stay valid until
+                                      the request completes */
 } hp_serve_config;
 
 const char *hp_status_string(hp_status st);
@@ -350,8 +364,11 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
  * Labels and clusters are the same for every setting; only speed differs.
  * Settings are kept per shape bucket (log2 of n_events * n_modules, log2 of
  * the mean digis per item) and used by every later launch in the bucket
- * (host, device, graph and serving paths); a bucket without an entry uses
- * the defaults (4096 slots, 2 blocks, 16 items, 64 digis).
+ * (host, device, graph and serving paths).  A bucket without an entry takes
+ * the entry of the nearest tuned bucket (distance |d items_log2| +
+ * 4 |d digis_per_item_log2|, at most 8), else the defaults: 4096 slots, 2
+ * blocks, 16 items, 64 digis, or, for a mean of 1024 digis per item or
+ * more, the single-block tile with 4 items a ticket and 32 digis.
  *
  * hp_autotune times every candidate (hp_tuning_candidates) on the given
  * device-resident inputs, `reps` passes each after one warm-up, on a private
@@ -501,7 +518,11 @@ hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, cons
  * hp_on_complete callback), status, latency and one-event view
  * (hp_fetch_clusters); release each with hp_release_event.  hp_serve_stop
  * launches what is still queued and waits for every batch (blocking;
- * hp_destroy does it too).
+ * hp_destroy does it too).  hp_serve_start reserves, in the context's
+ * caching pools, one block of the largest batch the loop can form per
+ * in-flight batch (within the device budget), so that the loop itself never
+ * calls cudaMalloc or cudaHostAlloc (this is setup: it blocks, and holds
+ * that memory until hp_destroy).
  * Errors: HP_EINVAL (not serving / already serving / bad arguments),
  * HP_EAGAIN, HP_ENOMEM, HP_ECUDA.
  */
@@ -542,6 +563,32 @@ hp_status hp_get_stats(hp_ctx *ctx, hp_stats *out);
  * names[i] are static strings.  *n_kernels receives the number of kernels
  * (at most cap are written).
  */
+/*
+ * Serving trace (tracing of the loop of hp_serve_start).  After
+ * hp_serve_trace_enable(ctx, cap) the next cap batches record, when their
+ * completion host function ends: the submit time of their oldest request,
+ * when the admitter took them, when their launch had been queued, and when
+ * their completion host function started and ended (ns, one monotonic
+ * clock, the one of hp_event_latency_ns), with their event and digi counts.
+ * hp_serve_trace_read copies up to cap records (oldest first) and reports
+ * how many there are; cap 0 in hp_serve_trace_enable stops and clears.  No
+ * CUDA call.  Errors: HP_EINVAL.
+ */
+typedef struct hp_serve_trace_record {
+    uint64_t t_first_submit, t_admit, t_launched, t_done_start, t_done_end;
+    uint64_t n_digis;
+    uint32_t n_events, stream;
+    uint64_t t_pooled;  /* the batch's blocks taken from the pools */
+    uint64_t t_inputs;  /* its input copies queued */
+    uint64_t t_kernels; /* its kernels queued */
+    /* device times (CUDA events on the batch's stream, ns from the first
+     * traced batch's start; -1 if not taken): the batch's start, its inputs
+     * copied, its kernels done, its outputs copied */
+    int64_t gpu_start, gpu_inputs, gpu_kernels, gpu_outputs;
+} hp_serve_trace_record;
+hp_status hp_serve_trace_enable(hp_ctx *ctx, uint64_t cap);
+hp_status hp_serve_trace_read(hp_ctx *ctx, hp_serve_trace_record *out, uint64_t cap, uint64_t *n);
+
 hp_status hp_profile_enable(hp_ctx *ctx, uint32_t max_launches);
 hp_status hp_profile_read(hp_ctx *ctx, uint32_t cap, const char **names, double *total_ms, uint64_t *launches,
                           uint32_t *n_kernels);

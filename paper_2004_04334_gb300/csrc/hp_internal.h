@@ -78,6 +78,13 @@ struct Geometry {
     const int32_t *ped;  // device [M]
 };
 
+// The six per-cluster output columns.
+struct ClusterCols {
+    uint32_t *module;
+    int32_t *id, *charge, *npix;
+    float *x, *y;
+};
+
 struct Outputs {
     uint64_t capacity;
     uint32_t *module;
@@ -86,14 +93,31 @@ struct Outputs {
     uint64_t *cluster_offsets; // [E+1]
     int32_t *label;            // [N] or null
     int32_t *event_status;     // [E] written by copy_kernel
+    // compact labels, instead of `label` (cc_kernel): each digi's cluster as
+    // its rank among the kept clusters of its (event, module) item, 0xFFFF
+    // below the pixel threshold, 0xFFFE in a cluster below the cluster
+    // threshold; and (copy_kernel) each item's first cluster counted from its
+    // event's first
+    uint16_t *label16 = nullptr;    // [N] or null
+    uint32_t *item_first = nullptr; // [E*M] (with label16)
+    // Outputs in mapped host memory: positions below head_n go to these
+    // device columns instead (16-byte aligned), which the launch then copies
+    // to the host columns by DMA, so that the copy engine, not the SMs,
+    // carries them over the host link; the positions from head_n on (the
+    // launch cannot know the cluster count in advance) go straight to host.
+    ClusterCols head{};
+    uint32_t head_n = 0;
 };
+
+// Output positions a copy_kernel warp writes per step (four a lane).
+constexpr uint32_t kOutChunk = 128;
 
 // Scratch of one launch.  The first `zero_bytes` bytes must be zero before
 // the first kernel (one memset): control words, per-event error bits,
 // per-item counts and the chained-scan state.
 struct Workspace {
     uint32_t *ctl;        // [16]: 0 item ticket, 1 launch error bits, 2 arena bump, 3 prefix frontier,
-                          //       4 offsets chunk ticket, 5 pieces of large items
+                          //       4 offsets chunk ticket, 6 clusters of the launch (offsets_kernel)
     uint32_t *event_err;  // [E]
     uint32_t *count;      // [E*M] digis of each item (reserved part, then the total: scan_kernel);
                           //       then each item's first output position (offsets_kernel)
@@ -107,7 +131,7 @@ struct Workspace {
     uint32_t *bucket_w;   // [N]
     uint32_t *bucket_i;   // [N] index of the digi within its event
     Staging staging;      // [N] each array
-    uint2 *pieces;        // [N / 512 + 1] (item, piece) of the large items, copied a block per piece
+    uint32_t *chunk_item; // [N / kOutChunk + 2] item holding the first position of each output chunk
     unsigned long long *exact; // [cc_grid * 2 * tile_slots] 64-bit moments of heavy clusters
     unsigned char *big;   // scratch of items too large for shared memory
     uint64_t big_slots;   // slots per block (slab mode) or in total (arena mode)

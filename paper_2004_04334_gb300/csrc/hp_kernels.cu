@@ -60,9 +60,15 @@ constexpr unsigned long long kWaitNs = 1000000000ull; // and at most one second 
 struct ItemCtx {
     uint32_t e, m, b, n;
     int32_t gain, ped;
-    int32_t *label_e;  // label of the event's first digi, or null
-    uint32_t *err_e;   // the event's error bits
+    int32_t *label_e;    // label of the event's first digi, or null
+    uint16_t *label16_e; // compact label of the event's first digi, or null (then label_e is null)
+    uint32_t *err_e;     // the event's error bits
 };
+
+// Compact labels: the rank of the digi's cluster among the kept clusters of
+// its item (= its staging ordinal), or these two markers.
+constexpr uint16_t kLab16Below = 0xFFFFu;   // pixel below threshold (label -1)
+constexpr uint16_t kLab16Dropped = 0xFFFEu; // cluster below threshold (label -2)
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
 {
@@ -170,6 +176,7 @@ __device__ __forceinline__ ItemCtx make_item(const Launch &L, const ItemRec &rec
     it.gain = rec.gain;
     it.ped = rec.ped;
     it.label_e = L.out.label ? L.out.label + rec.label_off : nullptr;
+    it.label16_e = L.out.label16 ? L.out.label16 + rec.label_off : nullptr;
     it.err_e = L.ws.event_err + rec.e;
     return it;
 }
@@ -814,7 +821,7 @@ __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
         if ((kl >> j) & 1u) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                if (lj < lin[k]) ++ord[k];
+                if (lj < lab[k]) ++ord[k]; // the rank of the digi's cluster (lab = lin for its lead)
         }
     }
 #pragma unroll
@@ -824,6 +831,8 @@ __device__ uint32_t warp_item(const Launch &L, const ItemCtx &it)
                              centroid(rc[k], Sc[k], Q[k]));
         }
         if (it.label_e && have[k]) it.label_e[idx[k]] = !surv[k] ? -1 : (kept[k] ? lab[k] : -2);
+        if (it.label16_e && have[k])
+            it.label16_e[idx[k]] = !surv[k] ? kLab16Below : (kept[k] ? (uint16_t)ord[k] : kLab16Dropped);
     }
     if constexpr (K == 1)
         return __popc(kl);
@@ -1112,8 +1121,11 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
         }
         L.ws.staging.put(it.b + ord, (int32_t)(t.parent[s] & ~kMark), Q, (int32_t)t.np[s], centroid_abs(mr, Q),
                          centroid_abs(mc, Q));
+        if (it.label16_e) t.np[s] = ord; // read back by the compact labels
     };
-    if (S <= 2 * nwords) {
+    // (the compact labels look digis up in the survivor bitmap afterwards, so
+    // with them the kept roots are not compacted into its space)
+    if (S <= 2 * nwords && !it.label16_e) {
         // compact the kept roots (their slots, by ordinal, into the survivor
         // bitmap's space, free now) so that every lane stages a cluster
         uint16_t *kslot = reinterpret_cast<uint16_t *>(sbits);
@@ -1131,6 +1143,33 @@ __device__ uint32_t block_item(const Launch &L, const ItemCtx &it, uint32_t *abi
             const uint32_t bal = abits[ch];
             if ((bal >> lane) & 1u) stage((ch << 5) + lane, run + __popc(bal & ((1u << lane) - 1u)));
             run += __popc(bal);
+        }
+    }
+    if (it.label16_e) { // compact labels: the ordinal of the digi's root, kept in t.np by the staging
+        __syncthreads();
+#pragma unroll 1
+        for (uint32_t k0 = tid; k0 < n; k0 += 4 * kCCThreads) {
+            uint32_t wv[4], iv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = k0 + u * kCCThreads;
+                const bool in = k < n;
+                wv[u] = in ? __ldg(bw + k) : 0u;
+                iv[u] = in ? __ldg(bi + k) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u * kCCThreads >= n) continue;
+                const uint32_t lin = lin_of(wv[u]);
+                uint16_t v = kLab16Below;
+                if (has_bit(sbits, lin)) {
+                    const uint32_t sl = rank_of(sbits, spre, lin);
+                    const uint32_t p = t.parent[sl];
+                    const uint32_t x = (p & kMark) ? sl : p;
+                    v = t.q[x] >= cthr ? (uint16_t)t.np[x] : kLab16Dropped;
+                }
+                it.label16_e[iv[u]] = v;
+            }
         }
     }
     return K;
@@ -1232,6 +1271,7 @@ __device__ __forceinline__ void stage_cluster(const Launch &L, const ItemCtx &it
     }
     L.ws.staging.put(it.b + ord, (int32_t)(t.parent[s] & ~kMark), Q, (int32_t)t.np[s], centroid_abs(mr, Q),
                      centroid_abs(mc, Q));
+    if (it.label16_e) t.np[s] = ord; // read back by the compact labels
 }
 
 // Register tier of the block: items of at most kD * kCCThreads digis (and at
@@ -1509,6 +1549,19 @@ __device__ uint32_t block_item_reg(const Launch &L, const ItemCtx &it, uint32_t 
             o += __popc(bal);
         }
     }
+    // 7: compact labels, once every kept root's ordinal is in t.np
+    if (it.label16_e) {
+        __syncthreads();
+        const uint32_t *bi = L.ws.bucket_i + it.b;
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            const uint32_t j = tid + k * kCCThreads;
+            if (j >= n) continue;
+            uint16_t v = kLab16Below;
+            if (s[k] != kNoSlot) v = t.q[s[k]] >= cthr ? (uint16_t)t.np[s[k]] : kLab16Dropped;
+            it.label16_e[__ldg(bi + j)] = v;
+        }
+    }
     return K;
 }
 
@@ -1751,8 +1804,6 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
 // the chunk, and the capacity check.
 constexpr int kOffThreads = 1024;
 constexpr uint32_t kOffItems = kOffThreads;
-constexpr unsigned long long kCopySpan = 1024; // clusters of a large item a copy_kernel block takes at a time
-constexpr uint32_t kBigItem = 512;             // items with more kept clusters are copied by blocks, not warps
 
 __global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
 {
@@ -1791,42 +1842,32 @@ __global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
         uint32_t e, m;
         item_coords(item, M, &e, &m);
         if (m == 0) L.out.cluster_offsets[e] = o;
-        // a large item is copied in pieces of kCopySpan clusters by whole blocks
-        if (k > kBigItem) {
-            const uint32_t pieces = (k + (uint32_t)kCopySpan - 1) / (uint32_t)kCopySpan;
-            const uint32_t at = atomicAdd(&L.ws.ctl[5], pieces);
-            for (uint32_t pc = 0; pc < pieces; ++pc) L.ws.pieces[at + pc] = make_uint2((uint32_t)item, pc);
-        }
+        // the output chunks whose first position falls in this item's range
+        if (k > 0)
+            for (unsigned long long q = (o + kOutChunk - 1) / kOutChunk; q * kOutChunk < o + k; ++q)
+                L.ws.chunk_item[q] = (uint32_t)item;
     }
-    if (tid == 0 && c == nchunks - 1) L.out.cluster_offsets[L.E] = P + total;
+    if (tid == 0 && c == nchunks - 1) {
+        L.out.cluster_offsets[L.E] = P + total;
+        L.ws.ctl[6] = (uint32_t)(P + total);
+    }
     if (tid == 0 && P + total > L.out.capacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
 }
 
-// copy_kernel: one warp per item copies its staged clusters (SoA, at the
-// item's bucket start) to their output positions, four clusters a lane in
-// flight; items with more than kBigItem clusters are skipped there and
-// copied instead in pieces of kCopySpan clusters, a block per piece (the
-// piece list comes from offsets_kernel), so that no warp carries a hot
-// module alone.  The first E threads write the per-event status codes from
-// the error bits.
+// copy_kernel: the staged clusters (SoA, at each item's bucket start) to
+// their ordered output positions, driven by the output: a warp takes a chunk
+// of kOutChunk consecutive positions, four a lane, finds the item of its
+// first position by a binary search between the items that hold the first
+// positions of this chunk and the next (chunk_item[], from offsets_kernel),
+// and walks on from there.  Every warp store is then a whole, aligned 512-byte
+// run of one output array, which matters most when the outputs are mapped
+// host memory written over the chip-to-chip link (partial lines cost there).
+// The first E threads write the per-event status codes from the error bits.
 constexpr int kCopyThreads = 256;
-
-__device__ __forceinline__ void copy_one(const Launch &L, const Staging &sg, uint64_t d, uint64_t a, uint32_t m)
-{
-    const int32_t id = sg.id[a], q = sg.charge[a], np = sg.npix[a];
-    const float x = sg.x[a], y = sg.y[a];
-    L.out.module[d] = m;
-    L.out.id[d] = id;
-    L.out.charge[d] = q;
-    L.out.npix[d] = np;
-    L.out.x[d] = x;
-    L.out.y[d] = y;
-}
 
 __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
 {
     const uint32_t lane = threadIdx.x & 31, M = L.g.M;
-    const uint64_t EM = (uint64_t)L.E * M;
     const uint64_t gt = (uint64_t)blockIdx.x * kCopyThreads + threadIdx.x;
     const bool bad_offsets = (L.ws.ctl[1] & kErrBadOffsets) != 0;
     if (bad_offsets && gt <= L.E) L.out.cluster_offsets[gt] = 0; // no clusters
@@ -1842,44 +1883,123 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
     }
     if (bad_offsets) return;
     const Staging sg = L.ws.staging;
-    const unsigned long long cap = L.out.capacity;
+    const uint32_t total = L.ws.ctl[6];
+    const uint32_t T = (uint32_t)min((unsigned long long)total, (unsigned long long)L.out.capacity);
+    const uint32_t nchunks = (uint32_t)(((uint64_t)total + kOutChunk - 1) / kOutChunk);
+    const uint32_t last_item = (uint32_t)((uint64_t)L.E * M - 1);
+    const bool vec = ((reinterpret_cast<uintptr_t>(L.out.module) | reinterpret_cast<uintptr_t>(L.out.id) |
+                       reinterpret_cast<uintptr_t>(L.out.charge) | reinterpret_cast<uintptr_t>(L.out.npix) |
+                       reinterpret_cast<uintptr_t>(L.out.x) | reinterpret_cast<uintptr_t>(L.out.y)) & 15) == 0;
     const uint64_t warps = (uint64_t)gridDim.x * (kCopyThreads / 32);
-    for (uint64_t item = gt >> 5; item < EM; item += warps) {
-        const uint32_t K = L.ws.cursor[item];
-        if (K == 0 || K > kBigItem) continue;
-        const uint64_t d0 = L.ws.count[item], b = L.ws.boff[item];
-        uint32_t e, m;
-        item_coords(item, M, &e, &m);
-        uint32_t o = lane;
-        for (; o + 96 < K; o += 128) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (d0 + o + 32 * u < cap) copy_one(L, sg, d0 + o + 32 * u, b + o + 32 * u, m);
+    for (uint64_t ch = gt >> 5; ch < nchunks; ch += warps) {
+        const uint32_t p0 = (uint32_t)ch * kOutChunk + 4 * lane;
+        if (p0 >= T) continue;
+        // the item of p0: the last one in [lo, hi] whose range starts at or
+        // before p0 (empty items share their start with the next item)
+        uint32_t lo = L.ws.chunk_item[ch];
+        uint32_t hi = ch + 1 < nchunks ? L.ws.chunk_item[ch + 1] : last_item;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (L.ws.count[mid] <= p0) lo = mid;
+            else hi = mid - 1;
         }
-        for (; o < K; o += 32)
-            if (d0 + o < cap) copy_one(L, sg, d0 + o, b + o, m);
+        uint32_t it = lo, start = L.ws.count[it], K = L.ws.cursor[it];
+        const uint32_t nv = min(4u, T - p0);
+        uint32_t mo[4];
+        int32_t id[4], q[4], np[4];
+        float x[4], y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            mo[j] = 0;
+            id[j] = q[j] = np[j] = 0;
+            x[j] = y[j] = 0.f;
+            if ((uint32_t)j >= nv) continue;
+            const uint32_t p = p0 + j;
+            while (p - start >= K) { // on to the item holding p (count[it + 1] = start + K)
+                ++it;
+                start = L.ws.count[it];
+                K = L.ws.cursor[it];
+            }
+            const uint64_t a = (uint64_t)L.ws.boff[it] + (p - start);
+            uint32_t e, m;
+            item_coords(it, M, &e, &m);
+            mo[j] = m;
+            id[j] = sg.id[a];
+            q[j] = sg.charge[a];
+            np[j] = sg.npix[a];
+            x[j] = sg.x[a];
+            y[j] = sg.y[a];
+        }
+        const ClusterCols host = {L.out.module, L.out.id, L.out.charge, L.out.npix, L.out.x, L.out.y};
+        const bool in_head = p0 + nv <= L.out.head_n, past_head = p0 >= L.out.head_n;
+        if (nv == 4 && (in_head || (past_head && vec))) {
+            const ClusterCols &d = in_head ? L.out.head : host;
+            *reinterpret_cast<uint4 *>(d.module + p0) = make_uint4(mo[0], mo[1], mo[2], mo[3]);
+            *reinterpret_cast<int4 *>(d.id + p0) = make_int4(id[0], id[1], id[2], id[3]);
+            *reinterpret_cast<int4 *>(d.charge + p0) = make_int4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<int4 *>(d.npix + p0) = make_int4(np[0], np[1], np[2], np[3]);
+            *reinterpret_cast<float4 *>(d.x + p0) = make_float4(x[0], x[1], x[2], x[3]);
+            *reinterpret_cast<float4 *>(d.y + p0) = make_float4(y[0], y[1], y[2], y[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((uint32_t)j >= nv) continue;
+                const ClusterCols &d = p0 + j < L.out.head_n ? L.out.head : host;
+                d.module[p0 + j] = mo[j];
+                d.id[p0 + j] = id[j];
+                d.charge[p0 + j] = q[j];
+                d.npix[p0 + j] = np[j];
+                d.x[p0 + j] = x[j];
+                d.y[p0 + j] = y[j];
+            }
+        }
     }
-    const uint32_t npieces = L.ws.ctl[5];
-    for (uint32_t pc = blockIdx.x; pc < npieces; pc += gridDim.x) {
-        const uint2 w = L.ws.pieces[pc];
-        const uint64_t item = w.x;
-        const uint32_t K = L.ws.cursor[item];
-        const uint64_t d0 = L.ws.count[item], b = L.ws.boff[item];
-        uint32_t e, m;
-        item_coords(item, M, &e, &m);
-        const uint32_t lo = w.y * (uint32_t)kCopySpan, hi = min(K, lo + (uint32_t)kCopySpan);
-        for (uint32_t o = lo + threadIdx.x; o < hi; o += kCopyThreads)
-            if (d0 + o < cap) copy_one(L, sg, d0 + o, b + o, m);
+    // with compact labels: every item's first cluster counted from its event's first
+    if (L.out.item_first) {
+        const uint64_t EM = (uint64_t)L.E * M;
+        for (uint64_t item = gt; item < EM; item += (uint64_t)gridDim.x * kCopyThreads)
+            L.out.item_first[item] = L.ws.count[item] - L.ws.count[item - item % M];
     }
 }
 
 // Serving batches: block (x, e) copies a slice of request e's digis.
+// Four digis a thread, read with one 16-byte (words) and one 8-byte
+// (module ids) load where the source allows it: the sources are host memory
+// read over the chip-to-chip link, where wide loads carry more per request.
 __global__ void __launch_bounds__(256) gather_kernel(const GatherEntry *table, uint32_t *words, uint16_t *modules)
 {
     const GatherEntry g = table[blockIdx.y];
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (uint64_t)gridDim.x * blockDim.x) {
-        words[g.off + i] = g.words[i];
-        modules[g.off + i] = g.modules[i];
+    const bool wv = (reinterpret_cast<uintptr_t>(g.words) & 15) == 0;
+    const bool mv = (reinterpret_cast<uintptr_t>(g.modules) & 7) == 0;
+    const uint64_t n4 = g.n / 4, stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t *dw = words + g.off;
+    uint16_t *dm = modules + g.off;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        uint32_t w[4];
+        uint16_t m[4];
+        if (wv) {
+            const uint4 v = reinterpret_cast<const uint4 *>(g.words)[q];
+            w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = g.words[4 * q + j];
+        }
+        if (mv) {
+            const ushort4 v = reinterpret_cast<const ushort4 *>(g.modules)[q];
+            m[0] = v.x, m[1] = v.y, m[2] = v.z, m[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) m[j] = g.modules[4 * q + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            dw[4 * q + j] = w[j];
+            dm[4 * q + j] = m[j];
+        }
+    }
+    for (uint64_t i = 4 * n4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += stride) {
+        dw[i] = g.words[i];
+        dm[i] = g.modules[i];
     }
 }
 
@@ -1925,7 +2045,7 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
     w.cursor = reinterpret_cast<uint32_t *>(take(4ull * EM));
     w.bucket_w = reinterpret_cast<uint32_t *>(take(4ull * N));
     w.bucket_i = reinterpret_cast<uint32_t *>(take(4ull * N));
-    w.pieces = reinterpret_cast<uint2 *>(take(8ull * (N / kBigItem + 1)));
+    w.chunk_item = reinterpret_cast<uint32_t *>(take(4ull * (N / kOutChunk + 2)));
     w.staging.id = reinterpret_cast<int32_t *>(take(4ull * N));
     w.staging.charge = reinterpret_cast<int32_t *>(take(4ull * N));
     w.staging.npix = reinterpret_cast<int32_t *>(take(4ull * N));
@@ -2033,8 +2153,8 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     offsets_kernel<<<(unsigned)((EM + kOffItems - 1) / kOffItems), kOffThreads, 0, stream>>>(L);
     ++nk;
     mark(5);
-    {   // a warp per item (at most copy_grid blocks, looping), and a thread per event status and offset
-        const uint64_t by_items = (EM + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
+    {   // a warp per output chunk (at most copy_grid blocks, looping), and a thread per event status and offset
+        const uint64_t by_items = (L.N / kOutChunk + 1 + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
         const uint64_t by_events = ((uint64_t)L.E + kCopyThreads) / kCopyThreads; // E + 1 offsets
         const uint64_t blocks =
             std::max<uint64_t>(1, std::max<uint64_t>(by_events, std::min<uint64_t>(by_items, (uint64_t)L.copy_grid)));

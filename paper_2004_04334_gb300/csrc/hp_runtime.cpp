@@ -17,6 +17,7 @@
 // autotuner of the clustering kernel's launch parameters, and the
 // continuous-batching serving loop with its native load driver.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -48,11 +49,15 @@ uint64_t now_ns()
 // Bin sizes: four bins per power of two, 4 KiB minimum (at most 25% slack).
 // Serving sizes vary from batch to batch and request to request: rounding
 // them up to a power of two keeps the number of distinct pool bins small, and
-// serving allocations may take any cached block up to kServeRatio times their
-// size, so a steady stream reuses cached blocks instead of allocating
-// (cudaMalloc synchronises the device; cudaHostAlloc takes milliseconds),
-// at the cost of memory.
+// request staging may take any cached block up to kServeRatio times its
+// size, and a batch any cached block at all (the smallest that fits; the
+// blocks reserved at hp_serve_start, one of the largest batch per batch in
+// flight, always leave one), so a steady stream reuses cached blocks instead
+// of allocating: cudaMalloc synchronises the device and cudaHostAlloc takes
+// milliseconds, and one such call on the admitter thread stalled every
+// request behind it for tens of milliseconds.
 constexpr size_t kServeRatio = 256;
+constexpr size_t kAnyRatio = 0; // Pool::alloc: any cached block that fits
 size_t round_pow2(size_t bytes)
 {
     size_t p = 4096;
@@ -83,7 +88,7 @@ class Pool {
     explicit Pool(bool host) : host_(host) {}
 
     // max_ratio: the largest cached block (relative to the request) that may
-    // serve it; a large ratio trades memory for fewer backend calls.
+    // serve it, 0 for any; a large ratio trades memory for fewer backend calls.
     hp_status alloc(size_t bytes, Block *out, size_t max_ratio = 2)
     {
         const size_t b = round_bin(bytes);
@@ -94,7 +99,7 @@ class Pool {
                 return HP_ENOMEM;
             }
             auto it = free_.lower_bound(b); // best fit among cached blocks of up to max_ratio times the size
-            if (it != free_.end() && it->first <= max_ratio * b) {
+            if (it != free_.end() && (max_ratio == 0 || it->first / max_ratio <= b)) {
                 *out = it->second;
                 free_.erase(it);
                 ++hits_;
@@ -226,6 +231,10 @@ struct hp_ctx {
     std::atomic<uint64_t> inflight{0}, dev_in_use{0};
     std::atomic<int> failed{0};
     std::atomic<uint64_t> enqueued{0}, completed{0}, h2d{0}, d2h{0}, kernels{0}, ws_mallocs{0};
+    // clusters per digi of recent launches (x 65536): sizes the part of the
+    // cluster outputs that goes to the host by DMA (see head_count)
+    std::atomic<uint32_t> clus_ratio{6554};
+    bool pageable_access = false; // the device reads pageable host memory (cudaDevAttrPageableMemoryAccess)
     std::mutex live_mu;
     std::set<hp_event *> live;
     std::mutex cev_mu;
@@ -245,6 +254,12 @@ struct hp_ctx {
     Serve *serve = nullptr;
     std::atomic<uint64_t> serve_batches{0}, serve_requests{0};
     std::atomic<uint64_t> serve_submit_ns{0}, serve_launch_ns{0}, serve_complete_ns{0}, serve_max_batch{0};
+    // serving trace (hp_serve_trace_enable / hp_serve_trace_read)
+    std::mutex trace_mu;
+    std::vector<hp_serve_trace_record> trace;
+    std::vector<std::array<cudaEvent_t, 4>> trace_ev; // device marks of each record (or null)
+    std::vector<cudaEvent_t> trace_spare;             // marks of batches past the cap, destroyed later
+    uint64_t trace_cap = 0;
     // hits: module placement (every version stays until hp_destroy, so queued
     // work keeps the one it was queued with) and the consumer streams
     std::mutex geom_mu;
@@ -283,6 +298,8 @@ struct hp_event {
     uint32_t *h_module = nullptr;
     int32_t *h_id = nullptr, *h_charge = nullptr, *h_npix = nullptr, *h_label = nullptr;
     float *h_x = nullptr, *h_y = nullptr;
+    uint16_t *h_label16 = nullptr; // compact labels (HP_LABELS_U16)
+    uint32_t *h_ifirst = nullptr;
     std::atomic<uint32_t> state{0};
     hp_status status = HP_OK;
     hp_callback cb = nullptr;
@@ -380,11 +397,45 @@ void complete_event(hp_event *ev)
     }
 }
 
+// Destroy the serving trace's device marks (not from a host function).
+void clear_trace_marks(hp_ctx *ctx)
+{
+    for (auto &a : ctx->trace_ev)
+        for (cudaEvent_t e : a)
+            if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->trace_spare) cudaEventDestroy(e);
+    ctx->trace_ev.clear();
+    ctx->trace_spare.clear();
+    cudaGetLastError();
+}
+
+// Cluster outputs bound for mapped host memory: how many leading positions
+// go through device columns and one DMA each (Outputs::head) instead of
+// being stored over the host link by the copy kernel.  15/16 of the clusters
+// expected from the recent clusters-per-digi ratio, at most a quarter of the
+// digis, in whole copy chunks; the rest of a launch that has more clusters
+// still goes straight to the host.
+uint32_t head_count(const hp_ctx *ctx, uint64_t N)
+{
+    const uint64_t expect = (N * ctx->clus_ratio.load(std::memory_order_relaxed)) >> 16;
+    const uint64_t h = std::min<uint64_t>(N / 4, expect - expect / 16);
+    return (uint32_t)(h & ~(uint64_t)(hp::kOutChunk - 1));
+}
+
+void note_clusters(hp_ctx *ctx, uint64_t clusters, uint64_t N)
+{
+    if (N < 4096) return;
+    const uint32_t now = (uint32_t)std::min<uint64_t>(65536, (std::min(clusters, N) << 16) / N);
+    const uint32_t old = ctx->clus_ratio.load(std::memory_order_relaxed);
+    ctx->clus_ratio.store((3 * old + now) / 4, std::memory_order_relaxed);
+}
+
 // Runs on the CUDA host-function thread once the event's stream work is done.
 void CUDART_CB trampoline(void *p)
 {
     hp_event *ev = static_cast<hp_event *>(p);
     hp_ctx *ctx = ev->ctx;
+    if (!ev->on_device) note_clusters(ctx, ev->h_coff[ev->E], ev->N);
     hp_status st = HP_OK;
     for (uint32_t e = 0; e < ev->E; ++e)
         if (ev->h_status[e] != 0) {
@@ -494,13 +545,43 @@ Shape shape_with(const hp_ctx *ctx, uint32_t E, const hp::Tuning &t)
     return sh;
 }
 
-Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N)
+// Settings of a bucket the autotuner has not seen: those of the nearest
+// tuned bucket (the mean item size weighs four times the item count, since
+// it decides which tier the items take), else a size default: items of a
+// thousand digis or more on average get the single-block tile, so that the
+// large ones among them stay in shared memory instead of global scratch.
+hp::Tuning untuned_default(const hp_ctx *ctx, std::pair<int, int> b)
 {
     hp::Tuning t;
     if (ctx->tune_mode != 0) {
+        int best = 1 << 30;
+        for (const auto &kv : ctx->tuned) {
+            const int d = std::abs(kv.first.first - b.first) + 4 * std::abs(kv.first.second - b.second);
+            if (d < best) {
+                best = d;
+                t = kv.second;
+            }
+        }
+        if (best <= 4 * 2) return t;
+        t = hp::Tuning{};
+    }
+    if (b.second >= 10 && ctx->max_tile[1] >= hp::kSmemSlots) {
+        t.tile_slots = ctx->max_tile[1];
+        t.blocks_per_sm = 1;
+        t.ticket_max = 4;
+        t.warp_max = 32;
+    }
+    return t;
+}
+
+Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N)
+{
+    const std::pair<int, int> b = tune_bucket(ctx, E, N);
+    hp::Tuning t;
+    {
         std::lock_guard<std::mutex> g(ctx->tune_mu);
-        auto it = ctx->tuned.find(tune_bucket(ctx, E, N));
-        if (it != ctx->tuned.end()) t = it->second;
+        auto it = ctx->tune_mode != 0 ? ctx->tuned.find(b) : ctx->tuned.end();
+        t = it != ctx->tuned.end() ? it->second : untuned_default(ctx, b);
     }
     return shape_with(ctx, E, t);
 }
@@ -626,6 +707,21 @@ bool pinned_host(const void *p)
     return a.type == cudaMemoryTypeHost;
 }
 
+// The address by which the device reads p: device, managed and pinned
+// (mapped) host memory, and any host memory where the device reads pageable
+// memory (hardware-coherent hosts); null where it cannot.
+const void *device_view(const hp_ctx *ctx, const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost)
+        return a.devicePointer;
+    return ctx->pageable_access ? p : nullptr;
+}
+
 bool device_pointer(const void *p)
 {
     cudaPointerAttributes a;
@@ -634,6 +730,17 @@ bool device_pointer(const void *p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Most blocks of the output copy.  Into device memory: eight an SM.  Into
+// mapped host memory the chip-to-chip link bounds it, and half an SM's worth
+// of blocks already fill the link with whole-line stores (about 190 GB/s
+// from 16 blocks of 512 threads on a GB300), so the copy leaves the other
+// SMs to the next launch's kernels instead of holding all of them while its
+// stores drain.
+int copy_grid(const hp_ctx *ctx, bool host_outputs)
+{
+    return host_outputs ? std::max(16, ctx->sm_count / 2) : ctx->sm_count * 8;
 }
 
 // Timing marks for the next launch, or null when stage timers are off.
@@ -676,9 +783,11 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     const uint64_t EM = (uint64_t)E * ctx->cfg.n_modules;
     if (EM > (1ull << 31)) return HP_EINVAL;
     flags |= ctx->cfg.flags;
-    const bool labels = (flags & HP_WANT_LABELS) != 0;
+    const bool compact = (flags & HP_LABELS_U16) != 0;
+    const bool labels = compact || (flags & HP_WANT_LABELS) != 0;
     const bool nocopy = (flags & HP_INPUT_NOCOPY) != 0;
     const bool keep = (flags & HP_KEEP_ON_DEVICE) != 0;
+    if (compact && keep) return HP_EINVAL;
 
     // device block: inputs, labels, workspace
     const Shape sh = shape_for(ctx, E, N);
@@ -693,7 +802,17 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     const size_t d_offs = doff;
     doff = align_up(doff + 8 * (E + 1), 256);
     const size_t d_label = doff;
-    if (labels) doff = align_up(doff + 4 * N, 256);
+    if (labels && !compact) doff = align_up(doff + 4 * N, 256);
+    const size_t d_label16 = doff; // compact labels and item offsets, staged for one copy each
+    if (compact) doff = align_up(doff + 2 * N, 256);
+    const size_t d_ifirst = doff;
+    if (compact) doff = align_up(doff + 4 * EM, 256);
+    const uint32_t head = keep ? 0u : head_count(ctx, N);
+    size_t d_head[6];
+    for (int i = 0; i < 6; ++i) {
+        d_head[i] = doff;
+        doff = align_up(doff + 4 * (size_t)head, 256);
+    }
     const size_t d_ws = doff;
     doff += ws_bytes;
     // outputs kept in device memory (HP_KEEP_ON_DEVICE): their own block, held until release
@@ -731,7 +850,9 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
         if (!keep) hoff = align_up(hoff + 4 * N, 256);
     }
     const size_t h_label = hoff;
-    if (labels && !keep) hoff = align_up(hoff + 4 * N, 256);
+    if (labels && !keep) hoff = align_up(hoff + (compact ? 2 : 4) * N, 256);
+    const size_t h_ifirst = hoff;
+    if (compact) hoff = align_up(hoff + 4 * EM, 256);
 
     // admission: in-flight limit and device budget (non-blocking: HP_EAGAIN)
     const uint64_t maxin = ctx->cfg.max_inflight ? ctx->cfg.max_inflight : 256;
@@ -815,7 +936,9 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
         ev->h_npix = reinterpret_cast<int32_t *>(hb + h_arr[3]);
         ev->h_x = reinterpret_cast<float *>(hb + h_arr[4]);
         ev->h_y = reinterpret_cast<float *>(hb + h_arr[5]);
-        ev->h_label = labels ? reinterpret_cast<int32_t *>(hb + h_label) : nullptr;
+        ev->h_label = labels && !compact ? reinterpret_cast<int32_t *>(hb + h_label) : nullptr;
+        ev->h_label16 = compact ? reinterpret_cast<uint16_t *>(hb + h_label) : nullptr;
+        ev->h_ifirst = compact ? reinterpret_cast<uint32_t *>(hb + h_ifirst) : nullptr;
     }
     ev->on_device = keep;
 
@@ -838,12 +961,23 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     L.out.y = reinterpret_cast<float *>(ob + (keep ? o_arr[5] : h_arr[5]));
     L.out.cluster_offsets = reinterpret_cast<uint64_t *>(ob + (keep ? o_coff : h_coff));
     L.out.event_status = reinterpret_cast<int32_t *>(ob + (keep ? o_status : h_status));
-    L.out.label = labels ? reinterpret_cast<int32_t *>(keep ? ob + o_label : db + d_label) : nullptr;
+    L.out.label = labels && !compact ? reinterpret_cast<int32_t *>(keep ? ob + o_label : db + d_label) : nullptr;
+    if (compact) {
+        L.out.label16 = reinterpret_cast<uint16_t *>(db + d_label16);
+        L.out.item_first = reinterpret_cast<uint32_t *>(db + d_ifirst);
+    }
+    L.out.head = {reinterpret_cast<uint32_t *>(db + d_head[0]), reinterpret_cast<int32_t *>(db + d_head[1]),
+                  reinterpret_cast<int32_t *>(db + d_head[2]), reinterpret_cast<int32_t *>(db + d_head[3]),
+                  reinterpret_cast<float *>(db + d_head[4]), reinterpret_cast<float *>(db + d_head[5])};
+    L.out.head_n = head;
     ev->dv = L.out;
+    ev->dv.head_n = 0;
     if (!keep) ev->dv.label = nullptr; // the device labels go back to the pool at completion
+    ev->dv.label16 = nullptr;
+    ev->dv.item_first = nullptr;
     hp::carve_workspace(db + d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, grid, sh.tune, &L.ws, ctx->sm_count);
     L.cc_grid = grid;
-    L.copy_grid = ctx->sm_count * 8;
+    L.copy_grid = copy_grid(ctx, !keep);
     L.sm_count = ctx->sm_count;
     L.tune = sh.tune;
     L.debug = take_debug(ctx);
@@ -867,9 +1001,22 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     }
     uint64_t nk = 0;
     if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
-    if (err == cudaSuccess && labels && N && !keep) {
-        err = cudaMemcpyAsync(ev->h_label, db + d_label, 4 * N, cudaMemcpyDeviceToHost, s);
-        ctx->d2h.fetch_add(4 * N);
+    if (err == cudaSuccess && head) { // the leading clusters, by DMA (see head_count)
+        void *dst[6] = {ev->h_module, ev->h_id, ev->h_charge, ev->h_npix, ev->h_x, ev->h_y};
+        for (int i = 0; i < 6 && err == cudaSuccess; ++i)
+            err = cudaMemcpyAsync(dst[i], db + d_head[i], 4 * (size_t)head, cudaMemcpyDeviceToHost, s);
+        ctx->d2h.fetch_add(24ull * head);
+    }
+    if (err == cudaSuccess && labels && !keep) {
+        if (compact) {
+            if (N) err = cudaMemcpyAsync(ev->h_label16, db + d_label16, 2 * N, cudaMemcpyDeviceToHost, s);
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(ev->h_ifirst, db + d_ifirst, 4 * EM, cudaMemcpyDeviceToHost, s);
+            ctx->d2h.fetch_add(2 * N + 4 * EM);
+        } else if (N) {
+            err = cudaMemcpyAsync(ev->h_label, db + d_label, 4 * N, cudaMemcpyDeviceToHost, s);
+            ctx->d2h.fetch_add(4 * N);
+        }
     }
     if (err == cudaSuccess && keep) { // per-event status and offsets only: the completion needs them
         err = cudaMemcpyAsync(ev->h_coff, L.out.cluster_offsets, 8 * (size_t)(E + 1), cudaMemcpyDeviceToHost, s);
@@ -902,10 +1049,15 @@ struct Batch {
     uint32_t E = 0;
     uint64_t N = 0;
     bool labels = false;
+    uint32_t si = 0; // its stream (index into the pool)
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr}; // serving trace: device marks
     std::vector<hp_event *> reqs;
     std::atomic<uint32_t> refs{0}; // one per request, plus one while in flight
+    hp_serve_trace_record rec{};   // serving trace record of this batch
     uint64_t *h_offs = nullptr, *h_coff = nullptr;
     int32_t *h_status = nullptr, *h_id = nullptr, *h_charge = nullptr, *h_npix = nullptr, *h_label = nullptr;
+    uint16_t *h_label16 = nullptr; // compact labels (HP_LABELS_U16)
+    uint32_t *h_ifirst = nullptr;
     uint32_t *h_module = nullptr;
     float *h_x = nullptr, *h_y = nullptr;
 };
@@ -919,6 +1071,7 @@ struct Serve {
     std::condition_variable cv;
     std::deque<hp_event *> pending;
     uint32_t inflight_batches = 0;
+    std::vector<uint32_t> stream_load; // batches in flight on each stream of the pool
     bool stop = false;
     std::thread admitter;
 };
@@ -960,6 +1113,7 @@ void CUDART_CB batch_done(void *p)
         uint64_t t;
         ~Timer() { c->serve_complete_ns.fetch_add(now_ns() - t); }
     } timer{ctx, now};
+    note_clusters(ctx, b->h_coff[b->E], b->N);
     for (uint32_t e = 0; e < b->E; ++e) {
         hp_event *r = b->reqs[e];
         const uint64_t c0 = b->h_coff[e], c1 = b->h_coff[e + 1];
@@ -974,7 +1128,9 @@ void CUDART_CB batch_done(void *p)
         r->h_npix = b->h_npix + c0;
         r->h_x = b->h_x + c0;
         r->h_y = b->h_y + c0;
-        r->h_label = b->labels ? b->h_label + b->h_offs[e] : nullptr;
+        r->h_label = b->h_label ? b->h_label + b->h_offs[e] : nullptr;
+        r->h_label16 = b->h_label16 ? b->h_label16 + b->h_offs[e] : nullptr;
+        r->h_ifirst = b->h_ifirst ? b->h_ifirst + (uint64_t)e * ctx->cfg.n_modules : nullptr;
         r->t_done = now;
         ctx->hpool.free(r->staging);
         r->staging = Block();
@@ -986,20 +1142,42 @@ void CUDART_CB batch_done(void *p)
     {
         std::lock_guard<std::mutex> g(b->sv->mu);
         b->sv->inflight_batches--;
+        b->sv->stream_load[b->si]--;
         b->sv->cv.notify_all();
     }
     for (uint32_t e = 0; e < b->E; ++e) complete_event(b->reqs[e]);
+    {
+        std::lock_guard<std::mutex> g(ctx->trace_mu);
+        if (ctx->trace.size() < ctx->trace_cap) {
+            b->rec.t_done_start = now;
+            b->rec.t_done_end = now_ns();
+            ctx->trace.push_back(b->rec);
+            ctx->trace_ev.push_back({b->tev[0], b->tev[1], b->tev[2], b->tev[3]});
+        } else {
+            for (cudaEvent_t e : b->tev)
+                if (e) ctx->trace_spare.push_back(e);
+        }
+    }
     release_batch_ref(b);
 }
 
 struct BatchLayout {
-    size_t d_words, d_mods, d_offs, d_label, d_ws, dev_bytes;
-    size_t h_offs, h_coff, h_status, h_arr[6], h_label, h_table, host_bytes;
+    size_t d_words, d_mods, d_offs, d_label, d_label16, d_ifirst, d_head[6], d_ws, dev_bytes;
+    uint32_t head;
+    size_t h_offs, h_coff, h_status, h_arr[6], h_label, h_ifirst, h_table, host_bytes;
     Shape sh;
 };
 
-BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
+// Labels a batch returns: 0 none, 1 int32 (HP_WANT_LABELS), 2 compact (HP_LABELS_U16).
+int label_mode(uint32_t flags)
 {
+    return (flags & HP_LABELS_U16) ? 2 : (flags & HP_WANT_LABELS) ? 1 : 0;
+}
+
+BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, int lmode, uint32_t head)
+{
+    const bool labels = lmode != 0, compact = lmode == 2;
+    const uint64_t EM = (uint64_t)E * ctx->cfg.n_modules;
     BatchLayout l;
     l.sh = shape_for(ctx, E, N);
     const size_t ws = hp::carve_workspace(nullptr, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols,
@@ -1012,7 +1190,16 @@ BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
     l.d_offs = d;
     d = align_up(d + 8 * (size_t)(E + 1), 256);
     l.d_label = d;
-    if (labels) d = align_up(d + 4 * N, 256);
+    if (labels && !compact) d = align_up(d + 4 * N, 256);
+    l.d_label16 = d;
+    if (compact) d = align_up(d + 2 * N, 256);
+    l.d_ifirst = d;
+    if (compact) d = align_up(d + 4 * EM, 256);
+    l.head = head;
+    for (int i = 0; i < 6; ++i) {
+        l.d_head[i] = d;
+        d = align_up(d + 4 * (size_t)head, 256);
+    }
     l.d_ws = d;
     l.dev_bytes = d + ws;
     size_t h = 0;
@@ -1027,7 +1214,9 @@ BatchLayout batch_layout(hp_ctx *ctx, uint32_t E, uint64_t N, bool labels)
         h = align_up(h + 4 * N, 256);
     }
     l.h_label = h;
-    if (labels) h = align_up(h + 4 * N, 256);
+    if (labels) h = align_up(h + (compact ? 2 : 4) * N, 256);
+    l.h_ifirst = h;
+    if (compact) h = align_up(h + 4 * EM, 256);
     l.h_table = h;
     h = align_up(h + sizeof(hp::GatherEntry) * E, 256);
     l.host_bytes = h;
@@ -1041,8 +1230,9 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     const uint64_t t_start = now_ns();
     uint64_t N = 0;
     for (hp_event *r : take) N += r->N;
-    const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
-    const BatchLayout l = batch_layout(ctx, E, N, labels);
+    const int lmode = label_mode(sv->cfg.flags | ctx->cfg.flags);
+    const bool labels = lmode != 0, compact = lmode == 2;
+    const BatchLayout l = batch_layout(ctx, E, N, lmode, head_count(ctx, N));
     Batch *b = new (std::nothrow) Batch();
     auto give_up = [&](hp_status st) {
         {
@@ -1059,11 +1249,16 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->N = N;
     b->labels = labels;
     b->reqs = take;
-    if (ctx->dpool.alloc(round_pow2(l.dev_bytes), &b->dev, kServeRatio) != HP_OK) {
+    b->rec.t_admit = t_start;
+    b->rec.n_events = E;
+    b->rec.n_digis = N;
+    b->rec.t_first_submit = ~0ull;
+    for (hp_event *r : take) b->rec.t_first_submit = std::min<uint64_t>(b->rec.t_first_submit, r->t_enq);
+    if (ctx->dpool.alloc(round_pow2(l.dev_bytes), &b->dev, kAnyRatio) != HP_OK) {
         delete b;
         return give_up(HP_ENOMEM);
     }
-    if (ctx->hpool.alloc(round_pow2(l.host_bytes), &b->host, kServeRatio) != HP_OK) {
+    if (ctx->hpool.alloc(round_pow2(l.host_bytes), &b->host, kAnyRatio) != HP_OK) {
         ctx->dpool.free(b->dev);
         delete b;
         return give_up(HP_ENOMEM);
@@ -1071,6 +1266,7 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->dev_charge = round_pow2(l.dev_bytes);
     ctx->dev_in_use.fetch_add(b->dev_charge);
     b->refs.store(E + 1);
+    b->rec.t_pooled = now_ns();
     for (hp_event *r : take) {
         r->batch = b;
         r->path = HP_PATH_SERVING;
@@ -1088,7 +1284,9 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     b->h_npix = reinterpret_cast<int32_t *>(hb + l.h_arr[3]);
     b->h_x = reinterpret_cast<float *>(hb + l.h_arr[4]);
     b->h_y = reinterpret_cast<float *>(hb + l.h_arr[5]);
-    b->h_label = labels ? reinterpret_cast<int32_t *>(hb + l.h_label) : nullptr;
+    b->h_label = labels && !compact ? reinterpret_cast<int32_t *>(hb + l.h_label) : nullptr;
+    b->h_label16 = compact ? reinterpret_cast<uint16_t *>(hb + l.h_label) : nullptr;
+    b->h_ifirst = compact ? reinterpret_cast<uint32_t *>(hb + l.h_ifirst) : nullptr;
     hp::GatherEntry *table = reinterpret_cast<hp::GatherEntry *>(hb + l.h_table);
     b->h_offs[0] = 0;
     uint32_t n_gather = 0;
@@ -1121,17 +1319,48 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     L.out.y = reinterpret_cast<float *>(hd + l.h_arr[5]);
     L.out.cluster_offsets = reinterpret_cast<uint64_t *>(hd + l.h_coff);
     L.out.event_status = reinterpret_cast<int32_t *>(hd + l.h_status);
-    L.out.label = labels ? reinterpret_cast<int32_t *>(db + l.d_label) : nullptr;
+    L.out.label = labels && !compact ? reinterpret_cast<int32_t *>(db + l.d_label) : nullptr;
+    if (compact) {
+        L.out.label16 = reinterpret_cast<uint16_t *>(db + l.d_label16);
+        L.out.item_first = reinterpret_cast<uint32_t *>(db + l.d_ifirst);
+    }
+    L.out.head = {reinterpret_cast<uint32_t *>(db + l.d_head[0]), reinterpret_cast<int32_t *>(db + l.d_head[1]),
+                  reinterpret_cast<int32_t *>(db + l.d_head[2]), reinterpret_cast<int32_t *>(db + l.d_head[3]),
+                  reinterpret_cast<float *>(db + l.d_head[4]), reinterpret_cast<float *>(db + l.d_head[5])};
+    L.out.head_n = l.head;
     hp::carve_workspace(db + l.d_ws, E, ctx->cfg.n_modules, N, ctx->cfg.rows, ctx->cfg.cols, l.sh.grid, l.sh.tune,
                         &L.ws, ctx->sm_count);
     L.cc_grid = l.sh.grid;
-    L.copy_grid = ctx->sm_count * 8;
+    L.copy_grid = copy_grid(ctx, true);
     L.sm_count = ctx->sm_count;
     L.tune = l.sh.tune;
 
-    const uint32_t si = ctx->next_stream.fetch_add(1) % (uint32_t)ctx->streams.size();
+    // the stream with the fewest batches in flight, so that a batch does not
+    // queue behind another while a stream is idle
+    uint32_t si = 0;
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        for (uint32_t i = 1; i < (uint32_t)sv->stream_load.size(); ++i)
+            if (sv->stream_load[i] < sv->stream_load[si]) si = i;
+        sv->stream_load[si]++;
+    }
+    b->si = si;
     cudaStream_t s = ctx->streams[si];
     uint64_t nk = 0;
+    bool traced;
+    {
+        std::lock_guard<std::mutex> g(ctx->trace_mu);
+        traced = ctx->trace.size() < ctx->trace_cap;
+    }
+    for (int i = 0; traced && i < 4; ++i)
+        if (cudaEventCreate(&b->tev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            b->tev[i] = nullptr;
+        }
+    auto mark = [&](int i) {
+        if (b->tev[i]) cudaEventRecord(b->tev[i], s);
+    };
+    mark(0);
     cudaError_t err = cudaMemcpyAsync(db + l.d_offs, b->h_offs, 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
     uint32_t *dw = reinterpret_cast<uint32_t *>(db + l.d_words);
     uint16_t *dm = reinterpret_cast<uint16_t *>(db + l.d_mods);
@@ -1147,18 +1376,40 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
                                 dm, s);
         ++nk;
     }
+    b->rec.t_inputs = now_ns();
+    mark(1);
     if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
-    if (err == cudaSuccess && labels && N)
+    mark(2);
+    b->rec.t_kernels = now_ns();
+    const uint64_t EM = (uint64_t)E * ctx->cfg.n_modules;
+    if (err == cudaSuccess && l.head) { // the leading clusters, by DMA (see head_count)
+        void *dst[6] = {b->h_module, b->h_id, b->h_charge, b->h_npix, b->h_x, b->h_y};
+        for (int i = 0; i < 6 && err == cudaSuccess; ++i)
+            err = cudaMemcpyAsync(dst[i], db + l.d_head[i], 4 * (size_t)l.head, cudaMemcpyDeviceToHost, s);
+        ctx->d2h.fetch_add(24ull * l.head);
+    }
+    if (err == cudaSuccess && compact) {
+        if (N) err = cudaMemcpyAsync(b->h_label16, db + l.d_label16, 2 * N, cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(b->h_ifirst, db + l.d_ifirst, 4 * EM, cudaMemcpyDeviceToHost, s);
+    } else if (err == cudaSuccess && labels && N) {
         err = cudaMemcpyAsync(b->h_label, db + l.d_label, 4 * N, cudaMemcpyDeviceToHost, s);
+    }
+    mark(3);
+    b->rec.stream = si;
+    b->rec.t_launched = now_ns();
     if (err == cudaSuccess) err = cudaLaunchHostFunc(s, batch_done, b);
     if (err != cudaSuccess) {
         cudaGetLastError();
         fail(ctx);
         for (hp_event *r : take) r->batch = nullptr; // the batch's memory is not reclaimed: the context is failed
+        {
+            std::lock_guard<std::mutex> g(sv->mu);
+            sv->stream_load[si]--;
+        }
         return give_up(HP_ECUDA);
     }
     ctx->h2d.fetch_add(6 * N + 8 * (uint64_t)(E + 1));
-    if (labels) ctx->d2h.fetch_add(4 * N);
+    if (labels) ctx->d2h.fetch_add(compact ? 2 * N + 4 * EM : 4 * N);
     ctx->kernels.fetch_add(nk);
     ctx->serve_batches.fetch_add(1);
     ctx->serve_launch_ns.fetch_add(now_ns() - t_start);
@@ -1174,7 +1425,7 @@ void admitter_main(hp_ctx *ctx, Serve *sv)
     const uint64_t max_digis = sv->cfg.max_batch_digis ? sv->cfg.max_batch_digis : (32ull << 20);
     const uint32_t max_batches = sv->cfg.max_inflight_batches ? sv->cfg.max_inflight_batches : 3;
     const size_t budget = sv->cfg.device_budget_bytes;
-    const bool labels = ((sv->cfg.flags | ctx->cfg.flags) & HP_WANT_LABELS) != 0;
+    const int lmode = label_mode(sv->cfg.flags | ctx->cfg.flags);
     for (;;) {
         std::vector<hp_event *> take;
         {
@@ -1193,7 +1444,7 @@ void admitter_main(hp_ctx *ctx, Serve *sv)
                 sv->pending.pop_front();
             }
             if (budget) {
-                const size_t need = round_pow2(batch_layout(ctx, (uint32_t)take.size(), nd, labels).dev_bytes);
+                const size_t need = round_pow2(batch_layout(ctx, (uint32_t)take.size(), nd, lmode, head_count(ctx, nd)).dev_bytes);
                 sv->cv.wait(lk, [&] {
                     return sv->inflight_batches == 0 || ctx->dev_in_use.load() + need <= budget;
                 });
@@ -1202,6 +1453,40 @@ void admitter_main(hp_ctx *ctx, Serve *sv)
         }
         launch_batch(ctx, sv, take);
     }
+}
+
+// Before the loop starts: one cached block of the largest batch the loop
+// can form, per in-flight batch (within the device budget), in the device
+// and the pinned host pool, so that no batch of the loop calls cudaMalloc
+// (which synchronises the device) or cudaHostAlloc (milliseconds for large
+// blocks) on the admitter thread while every request waits.  Best effort: a
+// block that cannot be reserved is left to the loop.
+void reserve_serving(hp_ctx *ctx, const hp_serve_config &cfg)
+{
+    const uint32_t max_events = cfg.max_batch_events ? cfg.max_batch_events : 256;
+    const uint64_t max_digis = cfg.max_batch_digis ? cfg.max_batch_digis : (32ull << 20);
+    const uint32_t max_batches = cfg.max_inflight_batches ? cfg.max_inflight_batches : 3;
+    const BatchLayout l = batch_layout(ctx, max_events, max_digis, label_mode(cfg.flags | ctx->cfg.flags),
+                                       (uint32_t)(max_digis / 4)); // the largest head (head_count)
+    // the workspace of another clustering setting may be larger (its 64-bit
+    // moment scratch scales with tile and grid): leave room for the largest
+    const size_t dev = round_pow2(l.dev_bytes + 16ull * hp::kMaxTileSlots * (size_t)ctx->sm_count * 3);
+    const size_t host = round_pow2(l.host_bytes);
+    uint32_t n = max_batches;
+    if (cfg.device_budget_bytes) n = (uint32_t)std::min<uint64_t>(n, cfg.device_budget_bytes / dev);
+    // A batch's host block (its results) stays taken until its requests are
+    // released, which is after its slot frees up (the completion host
+    // function hands the slot to the admitter before it runs the requests'
+    // callbacks): two more host blocks cover the batches that complete while
+    // the admitter launches the next ones.
+    const uint32_t nh = max_batches + 2;
+    std::vector<Block> d(n), h(nh);
+    for (uint32_t i = 0; i < n; ++i)
+        if (ctx->dpool.alloc(dev, &d[i]) != HP_OK) d[i] = Block();
+    for (uint32_t i = 0; i < nh; ++i)
+        if (ctx->hpool.alloc(host, &h[i]) != HP_OK) h[i] = Block();
+    for (uint32_t i = 0; i < n; ++i) ctx->dpool.free(d[i]);
+    for (uint32_t i = 0; i < nh; ++i) ctx->hpool.free(h[i]);
 }
 
 hp_status serve_stop(hp_ctx *ctx)
@@ -1447,6 +1732,10 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
             ctx->cc_major = prop.major;
             ctx->cc_minor = prop.minor;
         }
+        int pageable = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, cfg->device) != cudaSuccess)
+            cudaGetLastError();
+        ctx->pageable_access = pageable != 0;
     }
     load_tuning(ctx);
     const size_t M = cfg->n_modules;
@@ -1494,6 +1783,7 @@ hp_status hp_destroy(hp_ctx *ctx)
     for (auto &r : ctx->prof_used)
         for (cudaEvent_t e : r.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    clear_trace_marks(ctx);
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
     for (cudaStream_t s : ctx->aux_streams) cudaStreamDestroy(s);
     for (void *p : ctx->placements) cudaFree(p);
@@ -1557,6 +1847,8 @@ hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *v)
     v->x = ev->h_x;
     v->y = ev->h_y;
     v->label = ev->h_label;
+    v->label16 = ev->h_label16;
+    v->item_first = ev->h_ifirst;
     return ev->status;
 }
 
@@ -2112,6 +2404,8 @@ hp_status hp_serve_start(hp_ctx *ctx, const hp_serve_config *cfg)
     Serve *sv = new (std::nothrow) Serve();
     if (!sv) return HP_ENOMEM;
     sv->cfg = *cfg;
+    sv->stream_load.assign(ctx->streams.size(), 0);
+    reserve_serving(ctx, *cfg);
     try {
         sv->admitter = std::thread(admitter_main, ctx, sv);
     } catch (...) {
@@ -2151,11 +2445,16 @@ hp_status hp_submit(hp_ctx *ctx, const uint32_t *words, const uint16_t *module_i
     ev->tag = tag;
     ev->flags = sv->cfg.flags | ctx->cfg.flags;
     if (ev->flags & HP_INPUT_NOCOPY) {
-        // the caller's buffers stay where they are until the batch copies
-        // them (one cudaMemcpyAsync each: DMA from pinned memory)
-        ev->in_words = words;
-        ev->in_mods = module_ids;
-        ev->in_direct = true;
+        // the caller's buffers stay where they are until the batch reads
+        // them: in place by its gather kernel where the device can address
+        // them, else by one cudaMemcpyAsync each.  (Two DMA commands per
+        // request made large batches queue hundreds of small copies, and the
+        // copy engines then fell behind.)
+        const void *dw = n_digis ? device_view(ctx, words) : nullptr;
+        const void *dm = n_digis ? device_view(ctx, module_ids) : nullptr;
+        ev->in_direct = !(dw && dm);
+        ev->in_words = ev->in_direct ? words : static_cast<const uint32_t *>(dw);
+        ev->in_mods = ev->in_direct ? module_ids : static_cast<const uint16_t *>(dm);
     } else {
         const size_t wbytes = align_up(4 * n_digis, 256);
         if (ctx->hpool.alloc(round_pow2(wbytes + 2 * n_digis + 256), &ev->staging, kServeRatio) != HP_OK) {
@@ -2334,6 +2633,41 @@ hp_status hp_get_stats(hp_ctx *ctx, hp_stats *o)
     o->consumer_stream_reuses = ctx->consumer_reuses.load();
     o->consumer_stream_waits = ctx->consumer_waits.load();
     return ctx->failed.load() ? HP_ECUDA : HP_OK;
+}
+
+hp_status hp_serve_trace_enable(hp_ctx *ctx, uint64_t cap)
+{
+    if (!ctx) return HP_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->trace_mu);
+    clear_trace_marks(ctx);
+    ctx->trace.clear();
+    ctx->trace.reserve(cap);
+    ctx->trace_cap = cap;
+    return HP_OK;
+}
+
+hp_status hp_serve_trace_read(hp_ctx *ctx, hp_serve_trace_record *out, uint64_t cap, uint64_t *n)
+{
+    if (!ctx || !n || (cap && !out)) return HP_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->trace_mu);
+    *n = ctx->trace.size();
+    cudaEvent_t base = nullptr; // the first traced batch's start
+    for (auto &a : ctx->trace_ev)
+        if (a[0]) {
+            base = a[0];
+            break;
+        }
+    for (uint64_t i = 0; i < cap && i < ctx->trace.size(); ++i) {
+        out[i] = ctx->trace[i];
+        int64_t *g[4] = {&out[i].gpu_start, &out[i].gpu_inputs, &out[i].gpu_kernels, &out[i].gpu_outputs};
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            const cudaEvent_t e = ctx->trace_ev[i][k];
+            *g[k] = base && e && cudaEventElapsedTime(&ms, base, e) == cudaSuccess ? (int64_t)(ms * 1e6) : -1;
+        }
+    }
+    cudaGetLastError();
+    return HP_OK;
 }
 
 hp_status hp_profile_enable(hp_ctx *ctx, uint32_t max_launches)

@@ -22,6 +22,7 @@ HP_OK, HP_EAGAIN, HP_ENOTREADY, HP_EINVAL, HP_EBADDIGI, HP_EDUP, HP_ECAPACITY, H
 HP_WANT_LABELS = 0x1
 HP_INPUT_NOCOPY = 0x2
 HP_KEEP_ON_DEVICE = 0x4
+HP_LABELS_U16 = 0x8
 HP_TRANSFER_CLUSTERS = 0x1
 HP_TRANSFER_LABELS = 0x2
 
@@ -34,7 +35,7 @@ EXPORTS = ("hp_status_string", "hp_create", "hp_destroy", "hp_enqueue_event", "h
            "hp_serve_stop", "hp_serve_replay", "hp_set_geometry", "hp_enqueue_hits", "hp_fetch_hits",
            "hp_hits_device", "hp_graph_capture", "hp_graph_launch", "hp_graph_destroy", "hp_tuning_candidates",
            "hp_get_tuning", "hp_set_tuning", "hp_autotune", "hp_event_device_clusters", "hp_enqueue_transfer",
-           "hp_debug_expire_waits", "hp_event_provenance")
+           "hp_debug_expire_waits", "hp_event_provenance", "hp_serve_trace_enable", "hp_serve_trace_read")
 
 
 class HPError(RuntimeError):
@@ -55,7 +56,7 @@ class ClustersView(ctypes.Structure):
                 ("tag", ctypes.c_uint64), ("cluster_offsets", ctypes.c_void_p), ("event_status", ctypes.c_void_p),
                 ("module", ctypes.c_void_p), ("id", ctypes.c_void_p), ("charge", ctypes.c_void_p),
                 ("npix", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
-                ("label", ctypes.c_void_p)]
+                ("label", ctypes.c_void_p), ("label16", ctypes.c_void_p), ("item_first", ctypes.c_void_p)]
 
 
 class DeviceClusters(ctypes.Structure):
@@ -136,6 +137,8 @@ def load(path: str = LIB_PATH):
             "hp_reconstruct_device_noalloc": (I, [V, U32, U64, V, V, V, P(DeviceClusters), V]),
             "hp_get_stats": (I, [V, P(Stats)]),
             "hp_profile_enable": (I, [V, U32]),
+            "hp_serve_trace_enable": (I, [V, U64]),
+            "hp_serve_trace_read": (I, [V, V, U64, P(U64)]),
             "hp_profile_read": (I, [V, U32, P(ctypes.c_char_p), P(ctypes.c_double), P(U64), P(U32)]),
             "hp_debug_fail_allocations": (I, [V, U32]),
             "hp_debug_expire_waits": (I, [V, U32]),
@@ -191,10 +194,29 @@ class Result:
     y: np.ndarray
     label: np.ndarray | None
     tag: int
+    label16: np.ndarray | None = None     # HP_LABELS_U16: rank of the digi's cluster in its module
+    item_first: np.ndarray | None = None  # HP_LABELS_U16: [E * M] first cluster of (e, m) from e's first
 
     @property
     def n_clusters(self) -> int:
         return len(self.id)
+
+    def labels_from_compact(self, digi_offsets, modules) -> np.ndarray:
+        """The int32 labels (cluster id, -1, -2) that the compact form
+        stands for: digi i of event e on module m is in cluster
+        cluster_offsets[e] + item_first[e * M + m] + label16[i]."""
+        N = len(self.label16)
+        M = len(self.item_first) // max(1, self.n_events)
+        offs = np.asarray(digi_offsets, np.int64)
+        ev = np.repeat(np.arange(self.n_events), np.diff(offs))
+        l16 = self.label16.astype(np.int64)
+        out = np.where(l16 == 0xFFFE, -2, -1).astype(np.int32)
+        keep = l16 < 0xFFFE
+        k = (self.cluster_offsets[ev[keep]].astype(np.int64) +
+             self.item_first[ev[keep] * M + np.asarray(modules, np.int64)[keep]].astype(np.int64) + l16[keep])
+        out[keep] = self.id[k]
+        assert len(out) == N
+        return out
 
     def event(self, e: int) -> "Result":
         a, b = int(self.cluster_offsets[e]), int(self.cluster_offsets[e + 1])
@@ -319,7 +341,9 @@ class Event:
         return Result(st, E, a(v.cluster_offsets, E + 1, np.uint64), a(v.event_status, E, np.int32),
                       a(v.module, C, np.uint32), a(v.id, C, np.int32), a(v.charge, C, np.int32),
                       a(v.npix, C, np.int32), a(v.x, C, np.float32), a(v.y, C, np.float32),
-                      a(v.label, N, np.int32) if v.label else None, int(v.tag))
+                      a(v.label, N, np.int32) if v.label else None, int(v.tag),
+                      a(v.label16, N, np.uint16) if v.label16 else None,
+                      a(v.item_first, E * self._ctx.n_modules, np.uint32) if v.item_first else None)
 
     def transfer(self, what: int = HP_TRANSFER_CLUSTERS) -> "Event":
         """Queue the transfer module of a HP_KEEP_ON_DEVICE event (hp_enqueue_transfer)."""
@@ -493,10 +517,11 @@ class Context:
                                         d_hy, d_hz, ctypes.c_void_p(stream)), "hp_hits_device")
 
     def serve_start(self, budget_bytes=0, max_batch_events=0, max_batch_digis=0, max_inflight_batches=0,
-                    max_pending=0, want_labels=False, nocopy=False):
+                    max_pending=0, want_labels=False, nocopy=False, compact_labels=False):
         """Start the continuous-batching serving loop (see hp_serve_start)."""
         cfg = ServeConfig(budget_bytes, max_batch_events, max_batch_digis, max_inflight_batches, max_pending,
-                          (HP_WANT_LABELS if want_labels else 0) | (HP_INPUT_NOCOPY if nocopy else 0))
+                          (HP_WANT_LABELS if want_labels else 0) | (HP_INPUT_NOCOPY if nocopy else 0) |
+                          (HP_LABELS_U16 if compact_labels else 0))
         _check(self._lib.hp_serve_start(self._h, ctypes.byref(cfg)), "hp_serve_start")
 
     def try_submit(self, words, modules, tag=0):
@@ -535,6 +560,25 @@ class Context:
                                          pn.ctypes.data, lat.ctypes.data, st.ctypes.data, ctypes.byref(span)),
                "hp_serve_replay")
         return lat * 1e-9, st, span.value * 1e-9
+
+    def serve_trace_enable(self, cap: int):
+        """Record the next `cap` serving batches (hp_serve_trace_enable; 0 stops and clears)."""
+        _check(self._lib.hp_serve_trace_enable(self._h, cap), "hp_serve_trace_enable")
+
+    def serve_trace(self) -> np.ndarray:
+        """The serving trace records (hp_serve_trace_read), as a structured array."""
+        dt = np.dtype([("t_first_submit", np.uint64), ("t_admit", np.uint64), ("t_launched", np.uint64),
+                       ("t_done_start", np.uint64), ("t_done_end", np.uint64), ("n_digis", np.uint64),
+                       ("n_events", np.uint32), ("stream", np.uint32), ("t_pooled", np.uint64),
+                       ("t_inputs", np.uint64), ("t_kernels", np.uint64), ("gpu_start", np.int64),
+                       ("gpu_inputs", np.int64), ("gpu_kernels", np.int64), ("gpu_outputs", np.int64)])
+        n = ctypes.c_uint64()
+        _check(self._lib.hp_serve_trace_read(self._h, None, 0, ctypes.byref(n)), "hp_serve_trace_read")
+        out = np.zeros(n.value, dt)
+        if n.value:
+            _check(self._lib.hp_serve_trace_read(self._h, out.ctypes.data, n.value, ctypes.byref(n)),
+                   "hp_serve_trace_read")
+        return out[:n.value]
 
     def serve_stop(self):
         """Launch what is queued and wait for every batch."""

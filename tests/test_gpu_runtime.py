@@ -238,11 +238,14 @@ def test_labels_cross_the_link_only_when_asked(tiny):
         assert ev.wait(30) == hp.HP_OK and ev.fetch().label is None
         ev.release()
         d1 = ctx.stats()["d2h_bytes"]
-        assert d1 == d0
+        # what was copied is leading cluster records (24 bytes each, at most
+        # a quarter of the digis' worth: the DMA part of the cluster output)
+        assert (d1 - d0) % 24 == 0 and d1 - d0 <= 24 * (N // 4)
         ev = ctx.enqueue_batch(tiny.words, tiny.modules, tiny.offsets, flags=hp.HP_WANT_LABELS)
         assert ev.wait(30) == hp.HP_OK and ev.fetch().label is not None
         ev.release()
-        assert ctx.stats()["d2h_bytes"] - d1 == 4 * N
+        d2 = ctx.stats()["d2h_bytes"]
+        assert d2 - d1 >= 4 * N and (d2 - d1 - 4 * N) % 24 == 0 and d2 - d1 - 4 * N <= 24 * (N // 4)
 
 
 def test_events_in_flight_use_different_streams(tiny):

@@ -60,6 +60,7 @@ def test_autotune_keeps_the_fastest_and_results_stay_exact(torch_cuda):
     ref = oracle.reconstruct_workload(w)
     with hp.Context(w.n_modules, w.gain, w.pedestal, want_labels=True) as ctx:
         default = ctx.get_tuning(w.n_events, w.n_digis)
+        far = ctx.get_tuning(1, 10)
         _, (d_offs, d_words, d_mods, out) = _run(torch, ctx, w, dev)
         best, best_ms, ms = ctx.autotune(w.n_events, w.n_digis, d_offs.data_ptr(), d_words.data_ptr(),
                                          d_mods.data_ptr(), out, reps=2)
@@ -71,7 +72,7 @@ def test_autotune_keeps_the_fastest_and_results_stay_exact(torch_cuda):
         got, _ = _run(torch, ctx, w, dev)
         assert_batch_matches(got, ref, w.offsets)
         # another bucket is untouched; clearing restores the defaults
-        assert ctx.get_tuning(1, 10) == default
+        assert ctx.get_tuning(1, 10) == far
         ctx.set_tuning(w.n_events, w.n_digis, None)
         assert ctx.get_tuning(w.n_events, w.n_digis) == default
         bad = dict(default, blocks_per_sm=5)
@@ -103,5 +104,23 @@ def test_cache_file_round_trip_and_off_switch(torch_cuda, tmp_path, monkeypatch)
         assert ctx.get_tuning(w.n_events, w.n_digis) == other
     monkeypatch.setenv("HP_TUNE", "off")
     with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
-        assert ctx.get_tuning(w.n_events, w.n_digis)["ticket_items"] == 16
+        off = ctx.get_tuning(w.n_events, w.n_digis)
+    assert off != other
+    monkeypatch.delenv("HP_TUNE")
+    monkeypatch.delenv("HP_TUNE_CACHE")
+    with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:  # nothing tuned: the same size default
+        assert ctx.get_tuning(w.n_events, w.n_digis) == off
     os.remove(path)
+
+
+def test_untuned_buckets_take_the_nearest_tuned_entry(torch_cuda):
+    w = synth.workload("batched", n_events=8)
+    with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
+        small = ctx.get_tuning(1, 10)  # one digi per item on average: the plain default
+        assert small == {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 16, "warp_max": 64}
+        big = ctx.get_tuning(w.n_events, w.n_digis)  # over a thousand digis per item: single-block tile
+        assert big["blocks_per_sm"] == 1 and big["tile_slots"] > 4096
+        pick = {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 8, "warp_max": 32}
+        ctx.set_tuning(w.n_events, w.n_digis, pick)
+        assert ctx.get_tuning(2 * w.n_events, 2 * w.n_digis) == pick  # one bucket away
+        assert ctx.get_tuning(1, 10) == small  # far away: still the default
