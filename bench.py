@@ -69,9 +69,14 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--device-only", action="store_true",
                    help="only the device-resident timed loop (for profiler captures)")
-    p.add_argument("--serving-rates", default="5000,20000,50000",
+    p.add_argument("--serving-rates", default="1000,2000,5000,10000,20000,50000",
                    help="Poisson arrival rates (events/s) of the serving measurement")
-    p.add_argument("--serving-events", type=int, default=2000, help="requests per serving rate")
+    p.add_argument("--serving-events", type=int, default=100000,
+                   help="most requests per serving rate (fewer at low rates, see --serving-seconds)")
+    p.add_argument("--serving-seconds", type=float, default=8.0,
+                   help="requests per rate: rate x this many seconds, at most --serving-events")
+    p.add_argument("--no-extra-configs", action="store_true",
+                   help="skip the per-event (cfg1, cfg2, cfg3 events one at a time) and high-occupancy lines")
     p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
     p.add_argument("--e2e-depth", type=int, default=2, help="batches in flight in the end-to-end measurement")
     p.add_argument("--tuning", default="",
@@ -263,9 +268,9 @@ def run_reference(a):
     if rank != 0:
         return
     w = synth.workload(a.workload)
-    sample = list(range(min(32, w.n_events)))
+    sample = list(range(w.n_events))  # every event of the workload, each step (the same config as ours)
     for _ in range(a.warmup):
-        cpu_oracle(w, sample[:2])
+        cpu_oracle(w, sample[:16])
     vals = []
     t_all = 0.0
     for _ in range(a.steps):
@@ -278,7 +283,8 @@ def run_reference(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t_all / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
             "data": "synthetic",
-            "config": {"workload": f"{a.workload} (first {len(sample)} of {w.n_events} events per step)",
+            "config": {"workload": f"{a.workload}: {WORKLOAD_TEXT.get(a.workload, '')}; {w.n_events} events, "
+                                   f"{w.n_modules} modules of 160x416, {w.n_digis} digis, labels on",
                        "events_per_step": len(sample), "digis_per_step": nd, "n_modules": w.n_modules},
             "mdigis_per_s": nd * a.steps / t_all / 1e6,
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
@@ -304,24 +310,6 @@ def run_ours(a):
     seed = rank_seed(rank, world)
     w = synth.workload(a.workload, n_events=a.events or None, seed=seed)
     E, N, M = w.n_events, w.n_digis, w.n_modules
-
-    cpu = None
-    if rank == 0 and not a.no_cpu_baseline and not a.device_only:
-        # whole passes over the workload until about 10-15 CPU-seconds of work
-        # (0.75 s of wall time on all host threads), 20 passes at most
-        passes, t_cpu, cores = 0, 0.0, 1
-        while passes < 1 or (t_cpu < 0.75 and passes < 20):
-            _, _, dt, cores = cpu_oracle(w)
-            passes += 1
-            t_cpu += dt
-        cpu = {"value": passes * E / t_cpu, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"{passes} passes over all {E} events ({N} digis a pass) of the {a.workload} workload, "
-                         f"{cores} threads (one oracle call per event)",
-               "mdigis_per_s": passes * N / t_cpu / 1e6, "seconds": t_cpu}
-        # and on one core: the median of three passes over the first 8 events
-        one = sorted((cpu_oracle(w, list(range(min(8, E))), threads=1) for _ in range(3)), key=lambda r: r[0])[1]
-        cpu["single_core"] = {"value": one[0], "unit": "events/s", "mdigis_per_s": one[1],
-                              "sample": f"first {min(8, E)} events, one thread, median of 3 passes"}
 
     ctx = hp.Context(M, w.gain, w.pedestal, device=local, want_labels=True)
     d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
@@ -405,13 +393,38 @@ def run_ours(a):
     chain = _chain(a, ctx, w, out, n_clusters, dev, stream, step, barrier, world)
     clk = clocks.stop()
 
-    e2e = per_event = serving = None
+    e2e = per_event = serving = occupancy = None
     if not a.device_only:
         e2e, per_event = _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world)
     ctx.close()
+    if not a.device_only and not a.no_extra_configs:
+        # the batched workload's own events, one launch each: the same work as a batched step
+        per_event["batched"] = _per_event(a, a.workload, dev, stream, barrier, n_events=E)
+        occupancy = _device_config(a, "occupancy", dev, stream, barrier, world)
     if not a.device_only and rank == 0:
         serving = run_serving(local, [float(x) for x in a.serving_rates.split(",") if x], a.serving_events,
-                              nocopy=not a.serving_staging, inflight=a.serving_inflight)
+                              nocopy=not a.serving_staging, inflight=a.serving_inflight,
+                              seconds=a.serving_seconds)
+
+    # the CPU oracle last, after every GPU measurement: its host threads and
+    # memory churn stay out of the timed GPU and serving regions
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline and not a.device_only:
+        # whole passes over the workload until about 10-15 CPU-seconds of work
+        # (0.75 s of wall time on all host threads), 20 passes at most
+        passes, t_cpu, cores = 0, 0.0, 1
+        while passes < 1 or (t_cpu < 0.75 and passes < 20):
+            _, _, dt, cores = cpu_oracle(w)
+            passes += 1
+            t_cpu += dt
+        cpu = {"value": passes * E / t_cpu, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{passes} passes over all {E} events ({N} digis a pass) of the {a.workload} workload, "
+                         f"{cores} threads (one oracle call per event)",
+               "mdigis_per_s": passes * N / t_cpu / 1e6, "seconds": t_cpu}
+        # and on one core: the median of three passes over the first 8 events
+        one = sorted((cpu_oracle(w, list(range(min(8, E))), threads=1) for _ in range(3)), key=lambda r: r[0])[1]
+        cpu["single_core"] = {"value": one[0], "unit": "events/s", "mdigis_per_s": one[1],
+                              "sample": f"first {min(8, E)} events, one thread, median of 3 passes"}
 
     if rank == 0:
         line = {
@@ -435,7 +448,11 @@ def run_ours(a):
             "tuning": tuning,
             "chain": chain,
             "per_event": per_event,
-            "batched_vs_per_event": value / per_event["value"] if per_event else None,
+            "batched_vs_per_event": (value / per_event["batched"]["value"])
+            if per_event and "batched" in per_event else None,
+            "batched_vs_per_event_note": "the batched step against the same 256 events launched one at a time "
+                                         "(device-resident, one stream)",
+            "occupancy": occupancy,
             "serving": serving,
             "gpu_launches": gpu_launches,
             "clocks": clk,
@@ -498,88 +515,183 @@ def _e2e_and_per_event(a, ctx, w, n_clusters, dev, stream, barrier, world):
     from paper_2004_04334_gb300 import hp
 
     E, N = w.n_events, w.n_digis
-    local = dev.index
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     # end to end through the public enqueue API: pinned host inputs, H2D, pass, results in host memory
     pw = torch.from_numpy(w.words.view(np.int32)).pin_memory()
     pm = torch.from_numpy(w.modules.view(np.int16)).pin_memory()
     depth = a.e2e_depth  # batches in flight: the next batch's copies overlap this one's kernels
-    for _ in range(2):  # warm the pools at the timed depth (one device + pinned block per batch in flight)
-        evs = [ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY) for _ in range(depth)]
-        for ev in evs:
-            ev.wait(120)
-            ev.release()
-    # three timed runs of K steps each (a run is tens of ms of host wall time, so
-    # one scheduling hiccup moves it); the median run is reported
-    runs = []
-    for _ in range(3):
-        barrier()
-        t0 = time.perf_counter()
-        inflight = []
-        for _ in range(a.steps):
-            inflight.append(ctx.enqueue_batch(pw, pm, w.offsets, flags=hp.HP_INPUT_NOCOPY))
-            if len(inflight) >= depth:
-                ev = inflight.pop(0)
+
+    def run(flags):
+        for _ in range(2):  # warm the pools at the timed depth (one device + pinned block per batch in flight)
+            evs = [ctx.enqueue_batch(pw, pm, w.offsets, flags=flags) for _ in range(depth)]
+            for ev in evs:
+                ev.wait(120)
+                ev.release()
+        # three timed runs of K steps each (a run is tens of ms of host wall time, so
+        # one scheduling hiccup moves it); the median run is reported
+        runs = []
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            inflight = []
+            for _ in range(a.steps):
+                inflight.append(ctx.enqueue_batch(pw, pm, w.offsets, flags=flags))
+                if len(inflight) >= depth:
+                    ev = inflight.pop(0)
+                    ev.wait(120)
+                    r = ev.fetch(copy=False)
+                    nc, st = r.n_clusters, r.status
+                    ev.release()
+            for ev in inflight:
                 ev.wait(120)
                 r = ev.fetch(copy=False)
                 nc, st = r.n_clusters, r.status
                 ev.release()
-        for ev in inflight:
-            ev.wait(120)
-            r = ev.fetch(copy=False)
-            nc, st = r.n_clusters, r.status
-            ev.release()
-        barrier()
-        t_run = time.perf_counter() - t0
-        assert st == hp.HP_OK and nc == n_clusters
-        runs.append(max_over_ranks(t_run, world, dev))
-    t_e2e = sorted(runs)[1]
+            barrier()
+            t_run = time.perf_counter() - t0
+            assert st == hp.HP_OK and nc == n_clusters
+            runs.append(max_over_ranks(t_run, world, dev))
+        return sorted(runs)[1], runs
+
+    # labels in the compact form (2 bytes a digi and 4 an item), then as int32 ids
+    t_e2e, runs = run(hp.HP_INPUT_NOCOPY | hp.HP_LABELS_U16)
+    t_i32, runs_i32 = run(hp.HP_INPUT_NOCOPY | hp.HP_WANT_LABELS)
+    base_d2h = 24 * n_clusters + 8 * (E + 1) + 4 * E
     e2e = {"value": job_value(E, a.steps, t_e2e, world), "unit": "events/s", "batches_in_flight": depth,
+           "labels": "compact (HP_LABELS_U16: rank in the module, item offsets)",
            "h2d_bytes_per_step": 6 * N + 8 * (E + 1),
-           "d2h_bytes_per_step": 4 * N + 24 * n_clusters + 8 * (E + 1) + 4 * E,
+           "d2h_bytes_per_step": 2 * N + 4 * E * w.n_modules + base_d2h,
            "mdigis_per_s": world * N * a.steps / t_e2e / 1e6,
-           "runs_events_per_s": [job_value(E, a.steps, t, world) for t in runs], "reported": "median of the runs"}
+           "runs_events_per_s": [job_value(E, a.steps, t, world) for t in runs], "reported": "median of the runs",
+           "int32_labels": {"value": job_value(E, a.steps, t_i32, world), "unit": "events/s",
+                            "d2h_bytes_per_step": 4 * N + base_d2h,
+                            "runs_events_per_s": [job_value(E, a.steps, t, world) for t in runs_i32]}}
 
-    # plain per-event path: one full-size event per launch, one stream
-    pe = synth.workload("full")
-    pctx = hp.Context(pe.n_modules, pe.gain, pe.pedestal, device=local, want_labels=True)
-    pw1, pm1 = pe.event(0)
-    dw = torch.from_numpy(pw1.view(np.int32)).to(dev)
-    dm = torch.from_numpy(pm1.view(np.int16)).to(dev)
-    do = torch.from_numpy(pe.offsets.view(np.int64)).to(dev)
-    pout = hp.DeviceOutputs(1, len(pw1), dev)
-
-    def pstep():
-        pctx.reconstruct_device(1, len(pw1), do.data_ptr(), dw.data_ptr(), dm.data_ptr(), pout, stream.cuda_stream)
-
-    with torch.cuda.stream(stream):
-        for _ in range(10):
-            pstep()
-    barrier()
-    e0.record(stream)
-    for _ in range(a.per_event_steps):
-        pstep()
-    e1.record(stream)
-    barrier()
-    t_pe = e0.elapsed_time(e1) / 1000.0
-    lat = []
-    for i in range(a.per_event_steps):
-        ev = pctx.enqueue_event(pw1, pm1)
-        ev.wait(60)
-        lat.append(ev.latency_ns / 1e6)
-        ev.release()
-    per_event = {"workload": f"full: 1 event, {pe.n_modules} modules, {len(pw1)} digis",
-                 "value": a.per_event_steps / t_pe, "unit": "events/s",
-                 "mdigis_per_s": a.per_event_steps * len(pw1) / t_pe / 1e6,
-                 "e2e_latency_ms_p50": float(np.percentile(lat, 50)),
-                 "e2e_latency_ms_p99": float(np.percentile(lat, 99))}
-    pctx.close()
+    per_event = {name: _per_event(a, name, dev, stream, barrier) for name in ("full", "tiny")}
     return e2e, per_event
 
 
+def _per_event(a, name, dev, stream, barrier, n_events=1):
+    """The plain per-event path on one workload: every event its own launch
+    on one stream, device-resident (events/s), and every event through
+    hp_enqueue_event one at a time (events/s and enqueue-to-completion
+    p50/p99 from pinned host buffers)."""
+    import torch
+
+    from paper_2004_04334_gb300 import hp
+
+    w = synth.workload(name, n_events=n_events if n_events > 1 else None)
+    E = w.n_events
+    ctx = hp.Context(w.n_modules, w.gain, w.pedestal, device=dev.index, want_labels=True)
+    d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
+    d_mods = torch.from_numpy(w.modules.view(np.int16)).to(dev)
+    sizes = (w.offsets[1:] - w.offsets[:-1]).astype(np.int64)
+    per_offs = torch.from_numpy(np.stack([np.zeros(E, np.int64), sizes], 1).copy()).to(dev)
+    out = hp.DeviceOutputs(1, int(sizes.max()), dev)
+
+    def launch(e):
+        o = int(w.offsets[e])
+        ctx.reconstruct_device(1, int(sizes[e]), per_offs[e].data_ptr(), d_words.data_ptr() + 4 * o,
+                               d_mods.data_ptr() + 2 * o, out, stream.cuda_stream)
+
+    reps = max(1, a.per_event_steps // E)
+    order = [e for _ in range(reps) for e in range(E)]
+    with torch.cuda.stream(stream):
+        for e in order[:max(10, E)]:
+            launch(e)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for e in order:
+        launch(e)
+    e1.record(stream)
+    barrier()
+    t_dev = e0.elapsed_time(e1) / 1000.0
+    pw = torch.from_numpy(w.words.view(np.int32).copy()).pin_memory().numpy().view(np.uint32)
+    pm = torch.from_numpy(w.modules.view(np.int16).copy()).pin_memory().numpy().view(np.uint16)
+    for e in range(min(E, 10)):  # warm the pools
+        o = int(w.offsets[e])
+        ev = ctx.enqueue_event(pw[o:o + int(sizes[e])], pm[o:o + int(sizes[e])])
+        ev.wait(60)
+        ev.release()
+    lat = []
+    t0 = time.perf_counter()
+    for e in order:
+        o = int(w.offsets[e])
+        ev = ctx.enqueue_event(pw[o:o + int(sizes[e])], pm[o:o + int(sizes[e])])
+        ev.wait(60)
+        lat.append(ev.latency_ns / 1e6)
+        ev.release()
+    t_host = time.perf_counter() - t0
+    ctx.close()
+    nd = int(sizes.sum()) * reps
+    return {"workload": f"{name}: {E} event(s) of {w.n_modules} modules, {int(sizes.mean())} digis on average",
+            "events": len(order), "value": len(order) / t_dev, "unit": "events/s",
+            "mdigis_per_s": nd / t_dev / 1e6, "what": "device-resident, one launch per event on one stream",
+            "enqueue_one_at_a_time": {"value": len(order) / t_host, "unit": "events/s",
+                                      "latency_ms_p50": float(np.percentile(lat, 50)),
+                                      "latency_ms_p99": float(np.percentile(lat, 99)),
+                                      "what": "hp_enqueue_event from pinned buffers, wait, release; one in flight"}}
+
+
+def _device_config(a, name, dev, stream, barrier, world, n_events=0):
+    """Another workload device-resident (autotuned, CUDA-graph replay), with
+    its dominant kernel's roofline from the stage timers."""
+    import torch
+
+    from paper_2004_04334_gb300 import hp
+
+    w = synth.workload(name, n_events=n_events or None)
+    E, N, M = w.n_events, w.n_digis, w.n_modules
+    ctx = hp.Context(M, w.gain, w.pedestal, device=dev.index, want_labels=True)
+    d_words = torch.from_numpy(w.words.view(np.int32)).to(dev)
+    d_mods = torch.from_numpy(w.modules.view(np.int16)).to(dev)
+    d_offs = torch.from_numpy(w.offsets.view(np.int64)).to(dev)
+    out = hp.DeviceOutputs(E, N, dev)
+    tuned, _, _ = ctx.autotune(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out, reps=2)
+    steps = max(3, a.steps // 4)
+    graph = ctx.graph_capture(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out)
+    for _ in range(3):
+        graph.launch(stream.cuda_stream)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.launch(stream.cuda_stream)
+    e1.record(stream)
+    barrier()
+    t_dev = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, dev)
+    graph.destroy()
+    n_clusters = int(out.cluster_offsets[-1].item())
+    assert int((out.event_status != 0).sum().item()) == 0, "device reported an error status"
+    ctx.profile_enable(steps)
+    for _ in range(steps):
+        ctx.reconstruct_device(E, N, d_offs.data_ptr(), d_words.data_ptr(), d_mods.data_ptr(), out,
+                               stream.cuda_stream)
+    barrier()
+    prof = ctx.profile_read()
+    ctx.profile_enable(0)
+    ctx.close()
+    kname, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_s = ms / max(cnt, 1) / 1000.0
+    kb = kernel_bytes(kname, N, E, M, n_clusters)
+    peak, peak_kind = _peaks()
+    return {"workload": f"{name}: {WORKLOAD_TEXT.get(name, '')}; {E} events, {M} modules, {N} digis",
+            "value": job_value(E, steps, t_dev, world), "unit": "events/s",
+            "mdigis_per_s": world * N * steps / t_dev / 1e6, "ms_per_step": 1000 * t_dev / steps,
+            "steps": steps, "clusters_per_step": n_clusters, "tuning": tuned,
+            "path_algorithmic_GBps": algorithmic_bytes(N, E, M, n_clusters) * steps / t_dev / 1e9,
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": kb / per_launch_s / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": kb / per_launch_s / 1e9 / peak, "peak_kind": peak_kind,
+                         "traffic": _traffic(kname, N), "algorithmic_bytes_per_launch": kb,
+                         "mean_launch_ms": per_launch_s * 1000,
+                         "kernel_shares": {k: round(v[1] / max(1e-12, sum(x[1] for x in prof.values())), 4)
+                                           for k, v in prof.items()}}}
+
+
 def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=16 << 30, nocopy=False,
-                profile=False, inflight=0):
+                profile=False, inflight=0, seconds=0.0):
     """Serving workload: Poisson arrivals at each rate, event sizes lognormal
     (median 80k digis, sigma 0.8, capped at 500k), 4 native submitter threads
     with completion callbacks (hp_serve_replay), a 16 GB device budget,
@@ -601,7 +713,10 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
         ctx.serve_start(budget_bytes=budget, want_labels=True, nocopy=nocopy, max_inflight_batches=inflight)
         # warm the pools with every pool event, a few at a time and all at once
         ctx.serve_replay(pool, np.zeros(2 * len(pool)), np.arange(2 * len(pool)) % len(pool), submitters)
+        n_max = n_requests
         for k, rate in enumerate(rates):
+            # about `seconds` of arrivals at this rate, at most n_max requests
+            n_requests = int(min(n_max, max(1000, rate * seconds))) if seconds > 0 else n_max
             gaps = synth.exponential(synth.child_seed(synth.BASE_SEED + 5, 1000 + k), n_requests, rate)
             arrival = np.cumsum(gaps) - gaps[0]
             idx = np.arange(n_requests) % len(pool)
@@ -622,6 +737,7 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
                         "mdigis_per_s": nd / span / 1e6,
                         "latency_ms_p50": float(np.percentile(lat, 50) * 1e3),
                         "latency_ms_p99": float(np.percentile(lat, 99) * 1e3),
+                        "latency_ms_max": float(np.max(lat) * 1e3),
                         "errors": int((st != 0).sum()),
                         "mean_batch": n_requests / nb,
                         "submit_us_per_request": (s1["serve_submit_ns"] - s0["serve_submit_ns"]) / n_requests / 1e3,
@@ -673,8 +789,8 @@ def main():
         from paper_2004_04334_gb300 import build
         build.build()
         print(json.dumps(run_serving(local, [float(x) for x in a.serving_rates.split(",") if x],
-                                     a.serving_events, nocopy=not a.serving_staging,
-                                     profile=a.serving_profile, inflight=a.serving_inflight)), flush=True)
+                                     a.serving_events, nocopy=not a.serving_staging, profile=a.serving_profile,
+                                     inflight=a.serving_inflight, seconds=a.serving_seconds)), flush=True)
     else:
         run_ours(a)
 
