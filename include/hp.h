@@ -206,15 +206,32 @@ typedef struct hp_serve_config {
 const char *hp_status_string(hp_status st);
 
 /*
- * Create a context on cfg->device: stream pool, caching allocator, device
- * copies of the calibration tables.  *out receives the context.
+ * Create a context on cfg->device: the stream pool and the caching device
+ * and pinned-host allocators from which every event draws its memory
+ * (Sec. 4.1: no allocation or synchronisation on the event path once the
+ * pools are warm), and device copies of the calibration tables.  *out
+ * receives the context.
+ *
+ * The choice of technology (Sec. 3, the SwitchProducer) is made here, at
+ * run time: where no CUDA device cfg->device is usable, or the environment
+ * variable HP_FORCE_CPU is set to anything but "0", the context is a CPU
+ * context.  It produces the same hp_clusters (same fields, order, labels in
+ * either form, per-event statuses) with the host's cores (HP_CPU_THREADS
+ * threads; default one per hardware thread), and each product's provenance
+ * says HP_PATH_CPU and names the host.  A CPU context takes hp_enqueue_event,
+ * hp_enqueue_batch (not HP_KEEP_ON_DEVICE), hp_on_complete, hp_event_query,
+ * hp_fetch_clusters, hp_release_event, hp_event_provenance, hp_get_stats and
+ * hp_destroy; the device entries, graphs, the autotuner, serving, hits and
+ * transfers return HP_EINVAL.  Its events run in submission order, each
+ * spread over the threads; callbacks run on the context's dispatcher thread.
  * Errors: HP_EINVAL (see hp_config), HP_ENOMEM, HP_ECUDA.
  */
 hp_status hp_create(const hp_config *cfg, hp_ctx **out);
 
 /*
  * Drain every in-flight event (this blocks: teardown is outside event
- * processing), then free all memory.  Events not yet released are released.
+ * processing), then free all memory, the pools of Sec. 4.1 included.
+ * Events not yet released are released.
  */
 hp_status hp_destroy(hp_ctx *ctx);
 
@@ -266,11 +283,11 @@ hp_status hp_event_query(hp_event *ev);
 hp_status hp_fetch_clusters(hp_event *ev, hp_clusters *view);
 
 /*
- * Return the event's buffers to the pool.  Before completion the release is
- * deferred until the event completes (after its callback), and while
- * consumers (hits, transfers) still read its outputs, until they have run.
- * The event pointer and its views are invalid afterwards.  Makes no CUDA
- * call.
+ * Return the event's buffers to the pool (Sec. 4.1).  This ends the product
+ * holder's lifetime of Sec. 2: before completion the release is deferred
+ * until the event completes (after its callback), and while consumers (hits,
+ * transfers) still read its outputs, until they have run.  The event
+ * pointer and its views are invalid afterwards.  Makes no CUDA call.
  */
 hp_status hp_release_event(hp_event *ev);
 
@@ -286,6 +303,7 @@ hp_status hp_release_event(hp_event *ev);
 #define HP_PATH_SERVING 3u  /* a serving request (hp_submit) */
 #define HP_PATH_HITS 4u     /* hp_enqueue_hits */
 #define HP_PATH_TRANSFER 5u /* hp_enqueue_transfer */
+#define HP_PATH_CPU 6u      /* the CPU case (Sec. 3): hp_enqueue_event / _batch on a context without a GPU */
 typedef struct hp_provenance {
     char device_name[64];
     int device;

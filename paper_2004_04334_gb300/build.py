@@ -15,9 +15,10 @@ LIBDIR = os.path.join(HERE, "_lib")
 BUILDDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(LIBDIR, "libhp.so")
 
-SOURCES = ["hp_kernels.cu", "hp_runtime.cpp", "hp_serving.cpp", "hp_tuning.cpp", "hp_noalloc.cu", "hp_hits.cu",
-           "hp_transfer.cu"]
-HEADERS = [os.path.join(CSRC, "hp_internal.h"), os.path.join(CSRC, "hp_runtime.h"), os.path.join(INCLUDE, "hp.h")]
+SOURCES = ["hp_kernels.cu", "hp_runtime.cpp", "hp_serving.cpp", "hp_tuning.cpp", "hp_switch.cpp", "hp_cpu.cpp",
+           "hp_noalloc.cu", "hp_hits.cu", "hp_transfer.cu"]
+HEADERS = [os.path.join(CSRC, "hp_internal.h"), os.path.join(CSRC, "hp_runtime.h"),
+           os.path.join(CSRC, "hp_cpu.h"), os.path.join(INCLUDE, "hp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

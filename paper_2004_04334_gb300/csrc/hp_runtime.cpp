@@ -40,7 +40,7 @@ void destroy_event(hp_event *ev)
             ctx->dev_in_use.fetch_sub(ev->dout_charge);
         }
         std::lock_guard<std::mutex> g(ctx->cev_mu);
-        ctx->cev_free.push_back(ev->done);
+        if (ev->done) ctx->cev_free.push_back(ev->done);
     }
     {
         std::lock_guard<std::mutex> g(ctx->live_mu);
@@ -285,6 +285,7 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     const bool nocopy = (flags & HP_INPUT_NOCOPY) != 0;
     const bool keep = (flags & HP_KEEP_ON_DEVICE) != 0;
     if (compact && keep) return HP_EINVAL;
+    if (ctx->cpu) return cpu_enqueue(ctx, E, offsets, N, words, mods, tag, flags, out);
 
     // device block: inputs, labels, workspace
     const Shape sh = shape_for(ctx, E, N);
@@ -620,7 +621,7 @@ template <class T> T *device_alias(const Block &b, T *host)
 hp_status check_device_args(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
                             const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out)
 {
-    if (!ctx || !out || !d_offsets || n_events < 1) return HP_EINVAL;
+    if (!ctx || !out || !d_offsets || n_events < 1 || ctx->cpu) return HP_EINVAL;
     if (ctx->failed.load()) return HP_ECUDA;
     if (n_digis >= 0xFFFFFFFFull) return HP_EINVAL;
     if (n_digis > 0 && (!d_words || !d_module_ids)) return HP_EINVAL;
@@ -727,6 +728,24 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
     ctx->cfg.gain = nullptr;
     ctx->cfg.pedestal = nullptr;
     ctx->device = cfg->device;
+    // the SwitchProducer's choice (Sec. 3): the GPU case where a device is
+    // usable, else (or with HP_FORCE_CPU) the CPU case
+    {
+        const char *force = std::getenv("HP_FORCE_CPU");
+        int ndev = 0;
+        const bool no_gpu = cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev;
+        cudaGetLastError();
+        if ((force && *force && std::strcmp(force, "0") != 0) || no_gpu) {
+            const hp_status cs = cpu_create(ctx, cfg);
+            if (cs != HP_OK) {
+                cpu_destroy(ctx);
+                delete ctx;
+                return cs;
+            }
+            *out = ctx;
+            return HP_OK;
+        }
+    }
     auto bail = [&](hp_status s) {
         if (ctx->d_gain) cudaFree(ctx->d_gain);
         for (cudaStream_t x : ctx->streams) cudaStreamDestroy(x);
@@ -771,6 +790,17 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
 hp_status hp_destroy(hp_ctx *ctx)
 {
     if (!ctx) return HP_EINVAL;
+    if (ctx->cpu) {
+        cpu_destroy(ctx); // completes what is queued
+        std::vector<hp_event *> left;
+        {
+            std::lock_guard<std::mutex> g(ctx->live_mu);
+            left.assign(ctx->live.begin(), ctx->live.end());
+        }
+        for (hp_event *ev : left) destroy_event(ev);
+        delete ctx;
+        return HP_OK;
+    }
     serve_stop(ctx); // drains a running serving loop (no-op otherwise)
     cudaSetDevice(ctx->device);
     for (hp_graph *g : ctx->graphs) destroy_graph(g);
@@ -885,7 +915,8 @@ hp_status hp_event_provenance(const hp_event *ev, hp_provenance *o)
     o->cc_minor = ctx->cc_minor;
     o->library = kLibraryId;
     o->path = ev->path;
-    if (ev->path != HP_PATH_HITS && ev->path != HP_PATH_TRANSFER) to_public(ev->tune_used, &o->tuning);
+    if (ev->path != HP_PATH_HITS && ev->path != HP_PATH_TRANSFER && ev->path != HP_PATH_CPU)
+        to_public(ev->tune_used, &o->tuning);
     return HP_OK;
 }
 
@@ -900,7 +931,7 @@ uint64_t hp_event_latency_ns(const hp_event *ev)
 
 hp_status hp_set_geometry(hp_ctx *ctx, const float *origin, const float *rot, float pitch_row, float pitch_col)
 {
-    if (!ctx || !origin || !rot) return HP_EINVAL;
+    if (!ctx || !origin || !rot || ctx->cpu) return HP_EINVAL;
     if (!(pitch_row > 0.f) || !(pitch_col > 0.f) || !std::isfinite(pitch_row) || !std::isfinite(pitch_col))
         return HP_EINVAL;
     if (ctx->failed.load()) return HP_ECUDA;
@@ -940,7 +971,7 @@ hp_status hp_set_geometry(hp_ctx *ctx, const float *origin, const float *rot, fl
 hp_status hp_enqueue_hits(hp_event *prod, uint32_t flags, hp_event **out)
 {
     hp::NvtxRange range("hp_enqueue_hits");
-    if (!prod || !out || flags != 0) return HP_EINVAL;
+    if (!prod || !out || flags != 0 || prod->ctx->cpu) return HP_EINVAL;
     if (prod->request || prod->hits || prod->transfer) return HP_EINVAL;
     hp_ctx *ctx = prod->ctx;
     if (ctx->failed.load()) return HP_ECUDA;
@@ -1145,7 +1176,7 @@ hp_status hp_hits_device(hp_ctx *ctx, uint32_t n_events, uint64_t capacity, cons
                          const uint32_t *d_module, const float *d_x, const float *d_y, float *d_hx, float *d_hy,
                          float *d_hz, void *stream)
 {
-    if (!ctx || !d_cluster_offsets) return HP_EINVAL;
+    if (!ctx || !d_cluster_offsets || ctx->cpu) return HP_EINVAL;
     if (capacity > 0 && (!d_module || !d_x || !d_y || !d_hx || !d_hy || !d_hz)) return HP_EINVAL;
     if (ctx->failed.load()) return HP_ECUDA;
     hp::Placement place;

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <set>
@@ -25,6 +26,7 @@
 #include <utility>
 
 #include "hp.h"
+#include "hp_cpu.h"
 #include "hp_internal.h"
 
 namespace hp {
@@ -271,6 +273,17 @@ struct hp_ctx {
     // captured device passes (hp_graph_capture), destroyed with the context
     std::mutex graph_mu;
     std::set<hp_graph *> graphs;
+    // CPU case (Sec. 3, the SwitchProducer): no usable GPU, or HP_FORCE_CPU.
+    // Enqueued events run in order on one dispatcher thread, each spread
+    // over the host thread pool; completion callbacks run on the dispatcher.
+    bool cpu = false;
+    std::vector<int32_t> h_gain, h_ped;
+    std::unique_ptr<hp::cpu::ThreadPool> cpu_pool;
+    std::mutex cpu_mu;
+    std::condition_variable cpu_cv;
+    std::deque<hp_event *> cpu_jobs;
+    bool cpu_stop = false, cpu_busy = false;
+    std::thread cpu_thread;
 };
 
 struct hp_graph {
@@ -331,6 +344,12 @@ struct hp_event {
     hp_event *product = nullptr;
     uint32_t *h_hmodule = nullptr;
     float *h_hx = nullptr, *h_hy = nullptr, *h_hz = nullptr;
+    // CPU case (Sec. 3): the job's offsets, inputs (copied unless
+    // HP_INPUT_NOCOPY) and outputs in plain host memory
+    std::vector<uint64_t> cpu_offsets;
+    std::vector<uint32_t> cpu_words;
+    std::vector<uint16_t> cpu_mods;
+    std::vector<unsigned char> cpu_out;
 };
 
 namespace hp {
@@ -355,6 +374,10 @@ bool pinned_host(const void *p);
 const void *device_view(const hp_ctx *ctx, const void *p);
 int copy_grid(const hp_ctx *ctx, bool host_outputs);
 cudaEvent_t *profile_marks(hp_ctx *ctx);
+hp_status cpu_create(hp_ctx *ctx, const hp_config *cfg);
+void cpu_destroy(hp_ctx *ctx);
+hp_status cpu_enqueue(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_t N, const uint32_t *words,
+                      const uint16_t *mods, uint64_t tag, uint32_t flags, hp_event **out);
 hp_status check_device_args(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,
                             const uint32_t *d_words, const uint16_t *d_module_ids, const hp_device_clusters *out);
 cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const uint64_t *d_offsets,

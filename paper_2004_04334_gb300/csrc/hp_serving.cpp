@@ -501,7 +501,7 @@ extern "C" {
 
 hp_status hp_serve_start(hp_ctx *ctx, const hp_serve_config *cfg)
 {
-    if (!ctx || !cfg) return HP_EINVAL;
+    if (!ctx || !cfg || ctx->cpu) return HP_EINVAL;
     if (ctx->failed.load()) return HP_ECUDA;
     std::lock_guard<std::mutex> g(ctx->serve_mu);
     if (ctx->serve) return HP_EINVAL;

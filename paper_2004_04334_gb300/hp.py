@@ -88,7 +88,8 @@ class Provenance(ctypes.Structure):
                 ("tuning", Tuning)]
 
 
-PATHS = {1: "event", 2: "batch", 3: "serving", 4: "hits", 5: "transfer"}
+PATHS = {1: "event", 2: "batch", 3: "serving", 4: "hits", 5: "transfer", 6: "cpu"}
+HP_PATH_CPU = 6
 
 
 class HitsView(ctypes.Structure):
