@@ -78,11 +78,13 @@ def _args():
     p.add_argument("--no-extra-configs", action="store_true",
                    help="skip the per-event (cfg1, cfg2, cfg3 events one at a time) and high-occupancy lines")
     p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
-    p.add_argument("--e2e-depth", type=int, default=2, help="batches in flight in the end-to-end measurement")
+    p.add_argument("--e2e-depth", type=int, default=3, help="batches in flight in the end-to-end measurement")
     p.add_argument("--tuning", default="",
                    help="tile_slots,blocks_per_sm,ticket_items,warp_max: use these clustering settings instead of "
                         "autotuning (for profiler captures of one configuration)")
     p.add_argument("--serving-inflight", type=int, default=0, help="serving batches in flight (0: library default)")
+    p.add_argument("--serving-max-batch", type=int, default=0, help="events per serving batch, at most (0: library "
+                                                                      "default)")
     p.add_argument("--serving-profile", action="store_true",
                    help="diagnostic: stage timers on every serving batch (summed kernel time)")
     p.add_argument("--serving-staging", action="store_true",
@@ -402,9 +404,7 @@ def run_ours(a):
         per_event["batched"] = _per_event(a, a.workload, dev, stream, barrier, n_events=E)
         occupancy = _device_config(a, "occupancy", dev, stream, barrier, world)
     if not a.device_only and rank == 0:
-        serving = run_serving(local, [float(x) for x in a.serving_rates.split(",") if x], a.serving_events,
-                              nocopy=not a.serving_staging, inflight=a.serving_inflight,
-                              seconds=a.serving_seconds)
+        serving = _serving_in_fresh_process(a, local)
 
     # the CPU oracle last, after every GPU measurement: its host threads and
     # memory churn stay out of the timed GPU and serving regions
@@ -691,7 +691,7 @@ def _device_config(a, name, dev, stream, barrier, world, n_events=0):
 
 
 def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=16 << 30, nocopy=False,
-                profile=False, inflight=0, seconds=0.0):
+                profile=False, inflight=0, seconds=0.0, max_batch=0):
     """Serving workload: Poisson arrivals at each rate, event sizes lognormal
     (median 80k digis, sigma 0.8, capped at 500k), 4 native submitter threads
     with completion callbacks (hp_serve_replay), a 16 GB device budget,
@@ -710,7 +710,8 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
     out = []
     with hp.Context(w.n_modules, w.gain, w.pedestal, device=local, want_labels=True, n_streams=4) as ctx:
         tuned = pretune_batches(ctx, w, local)
-        ctx.serve_start(budget_bytes=budget, want_labels=True, nocopy=nocopy, max_inflight_batches=inflight)
+        ctx.serve_start(budget_bytes=budget, want_labels=True, nocopy=nocopy, max_inflight_batches=inflight,
+                        max_batch_events=max_batch)
         # warm the pools with every pool event, a few at a time and all at once
         ctx.serve_replay(pool, np.zeros(2 * len(pool)), np.arange(2 * len(pool)) % len(pool), submitters)
         n_max = n_requests
@@ -755,6 +756,28 @@ def run_serving(local, rates, n_requests, pool_events=200, submitters=4, budget=
             "rates": out}
 
 
+def _serving_in_fresh_process(a, local):
+    """The serving measurement in a process of its own, as a server runs:
+    started from this script (--serving-only) on the same GPU, so that none
+    of this process's earlier measurements (their contexts, pools, pinned
+    buffers and caches) shares its address space.  Its JSON line is returned."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serving-only", "--serving-rates", a.serving_rates,
+           "--serving-events", str(a.serving_events), "--serving-seconds", str(a.serving_seconds),
+           "--serving-inflight", str(a.serving_inflight), "--serving-max-batch", str(a.serving_max_batch)]
+    if a.serving_staging:
+        cmd.append("--serving-staging")
+    env = dict(os.environ, LOCAL_RANK=str(local))  # the same GPU, as a single process
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    p = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError("serving measurement failed: " + p.stderr[-2000:])
+    line = [l for l in p.stdout.splitlines() if l.startswith("{")][-1]
+    out = json.loads(line)
+    out["process"] = "a fresh process of its own (bench.py --serving-only)"
+    return out
+
+
 def pretune_batches(ctx, w, local, sizes=(1, 2, 4, 8, 16, 32, 64, 128, 256), reps=2):
     """Autotune the shape buckets that serving batches fall in: for each batch
     size, random samples of the event pool as device-resident batches (the
@@ -790,7 +813,8 @@ def main():
         build.build()
         print(json.dumps(run_serving(local, [float(x) for x in a.serving_rates.split(",") if x],
                                      a.serving_events, nocopy=not a.serving_staging, profile=a.serving_profile,
-                                     inflight=a.serving_inflight, seconds=a.serving_seconds)), flush=True)
+                                     inflight=a.serving_inflight, seconds=a.serving_seconds,
+                                     max_batch=a.serving_max_batch)), flush=True)
     else:
         run_ours(a)
 
