@@ -76,6 +76,8 @@ typedef enum hp_status {
 #define HP_KEEP_ON_DEVICE 0x4u /* enqueue: keep the clusters (and labels) in device
                                   memory until release; nothing but per-event status
                                   and offsets goes to the host (see hp_enqueue_transfer) */
+#define HP_ALLOW_CPU 0x10u /* hp_config.flags: where no CUDA device is usable, hp_create makes a CPU
+                              context (the CPU case of Sec. 3) instead of failing with HP_ECUDA */
 #define HP_LABELS_U16 0x8u /* labels in the compact form (implies HP_WANT_LABELS):
                               hp_clusters.label16 and .item_first instead of .label,
                               2 bytes a digi instead of 4 over the host link; not with
@@ -213,9 +215,11 @@ const char *hp_status_string(hp_status st);
  * receives the context.
  *
  * The choice of technology (Sec. 3, the SwitchProducer) is made here, at
- * run time: where no CUDA device cfg->device is usable, or the environment
- * variable HP_FORCE_CPU is set to anything but "0", the context is a CPU
- * context.  It produces the same hp_clusters (same fields, order, labels in
+ * run time, when the caller asks for it: with HP_ALLOW_CPU in cfg->flags
+ * and no usable CUDA device cfg->device, or with the environment variable
+ * HP_FORCE_CPU set to anything but "0", the context is a CPU context.
+ * Without either, a missing device is an error (HP_ECUDA): the library
+ * never falls back to the host on its own.  It produces the same hp_clusters (same fields, order, labels in
  * either form, per-event statuses) with the host's cores (HP_CPU_THREADS
  * threads; default one per hardware thread), and each product's provenance
  * says HP_PATH_CPU and names the host.  A CPU context takes hp_enqueue_event,

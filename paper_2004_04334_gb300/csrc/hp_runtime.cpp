@@ -728,14 +728,17 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
     ctx->cfg.gain = nullptr;
     ctx->cfg.pedestal = nullptr;
     ctx->device = cfg->device;
-    // the SwitchProducer's choice (Sec. 3): the GPU case where a device is
-    // usable, else (or with HP_FORCE_CPU) the CPU case
+    // the SwitchProducer's choice (Sec. 3), made only when asked for: the
+    // CPU case with HP_FORCE_CPU, or with HP_ALLOW_CPU where no device is
+    // usable.  Without either, a missing device fails here (HP_ECUDA): the
+    // library never falls back to the host on its own.
     {
         const char *force = std::getenv("HP_FORCE_CPU");
         int ndev = 0;
         const bool no_gpu = cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev;
         cudaGetLastError();
-        if ((force && *force && std::strcmp(force, "0") != 0) || no_gpu) {
+        const bool forced = force && *force && std::strcmp(force, "0") != 0;
+        if (forced || (no_gpu && (cfg->flags & HP_ALLOW_CPU))) {
             const hp_status cs = cpu_create(ctx, cfg);
             if (cs != HP_OK) {
                 cpu_destroy(ctx);

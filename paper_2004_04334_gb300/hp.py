@@ -23,6 +23,7 @@ HP_WANT_LABELS = 0x1
 HP_INPUT_NOCOPY = 0x2
 HP_KEEP_ON_DEVICE = 0x4
 HP_LABELS_U16 = 0x8
+HP_ALLOW_CPU = 0x10
 HP_TRANSFER_CLUSTERS = 0x1
 HP_TRANSFER_LABELS = 0x2
 
@@ -394,7 +395,8 @@ class Context:
     """A libhp context on one device (see hp_create)."""
 
     def __init__(self, n_modules, gain, pedestal, *, device=0, rows=160, cols=416, pixel_thr=1000,
-                 cluster_thr=4000, budget_bytes=0, max_inflight=0, n_streams=0, want_labels=False):
+                 cluster_thr=4000, budget_bytes=0, max_inflight=0, n_streams=0, want_labels=False,
+                 allow_cpu=False):
         self._lib = load()
         self.n_modules = int(n_modules)
         self.gain = np.ascontiguousarray(gain, np.int32)
@@ -403,7 +405,7 @@ class Context:
             raise ValueError("gain/pedestal must have n_modules entries")
         cfg = Config(device, self.n_modules, rows, cols, pixel_thr, cluster_thr, self.gain.ctypes.data,
                      self.pedestal.ctypes.data, budget_bytes, max_inflight, n_streams,
-                     HP_WANT_LABELS if want_labels else 0)
+                     (HP_WANT_LABELS if want_labels else 0) | (HP_ALLOW_CPU if allow_cpu else 0))
         h = ctypes.c_void_p()
         _check(self._lib.hp_create(ctypes.byref(cfg), ctypes.byref(h)), "hp_create")
         self._h = h

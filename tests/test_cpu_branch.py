@@ -116,3 +116,21 @@ def test_calls_a_cpu_context_refuses():
         rot = np.zeros(9 * w.n_modules, np.float32)
         assert lib.hp_set_geometry(h, o.ctypes.data, rot.ctypes.data, ctypes.c_float(0.01),
                                    ctypes.c_float(0.015)) == hp.HP_EINVAL
+
+
+def test_no_silent_fallback_to_the_host(monkeypatch):
+    """Without HP_FORCE_CPU or HP_ALLOW_CPU a context on a host without a
+    usable GPU is an error, never a CPU context; with HP_ALLOW_CPU it is the
+    CPU case (the runtime choice of Sec. 3, asked for by the caller)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the missing-device case cannot be made here")
+    monkeypatch.delenv("HP_FORCE_CPU")
+    w = synth.workload("tiny", n_events=1)
+    with pytest.raises(hp.HPError) as e:
+        hp.Context(w.n_modules, w.gain, w.pedestal)
+    assert e.value.status == hp.HP_ECUDA
+    with hp.Context(w.n_modules, w.gain, w.pedestal, allow_cpu=True) as ctx:
+        ev = ctx.enqueue_batch(w.words, w.modules, w.offsets)
+        assert ev.wait(60) == hp.HP_OK and ev.provenance()["path"] == "cpu"
+        ev.release()
