@@ -415,7 +415,7 @@ hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const ui
 
 /*
  * CUDA-graph form of the device-resident entry: hp_graph_capture records
- * one hp_reconstruct_device pass (a memset and five kernels) for fixed
+ * one hp_reconstruct_device pass (a memset and six kernels) for fixed
  * arguments into an executable CUDA graph with its own scratch;
  * hp_graph_launch replays it on `stream` (one cudaGraphLaunch, no
  * allocation, no host work per launch).  The graph keeps the pointers and
