@@ -1293,7 +1293,7 @@ __device__ __forceinline__ void stage_cluster(const Launch &L, const ItemCtx &it
 //   5 labels; kept roots balloted per 32-slot chunk
 //   6 kept roots compacted in slot (= id) order, then staged
 // Both bitmaps are left zeroed for the next item.
-template <int kD>
+template <int kD, bool kCompact>
 __device__ uint32_t block_item_reg(const Launch &L, const ItemCtx &it, uint32_t *abits, uint32_t *sbits,
                                    uint32_t *spre, const Tile &t, BlockShared &bs)
 {
@@ -1550,7 +1550,7 @@ __device__ uint32_t block_item_reg(const Launch &L, const ItemCtx &it, uint32_t 
         }
     }
     // 7: compact labels, once every kept root's ordinal is in t.np
-    if (it.label16_e) {
+    if (kCompact) {
         __syncthreads();
         const uint32_t *bi = L.ws.bucket_i + it.b;
 #pragma unroll
@@ -1749,7 +1749,10 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                     const ItemCtx it = make_item(L, s_rec[i], s_b[i], n);
                     uint32_t K;
                     if (n <= (uint32_t)kD * kCCThreads && n <= T) {
-                        K = block_item_reg<kD>(L, it, abits, sbits, spre, sm, bs);
+                        // (compact labels keep each digi's root slot live through the
+                        // staging: a separate instance, so the other keeps its registers)
+                        K = it.label16_e ? block_item_reg<kD, true>(L, it, abits, sbits, spre, sm, bs)
+                                         : block_item_reg<kD, false>(L, it, abits, sbits, spre, sm, bs);
                     } else if (n <= T) {
                         K = block_item<false>(L, it, abits, sbits, spre, sm, bs);
                     } else {
