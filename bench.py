@@ -240,6 +240,35 @@ def _traffic(kernel, n_units):
     return int(e["dram_bytes_per_unit"] * n_units)
 
 
+def _cpu_case(w, passes=3):
+    """The library's CPU case (HP_FORCE_CPU: the same product on the host's
+    cores) on the workload: events/s over `passes` whole batches, median."""
+    from paper_2004_04334_gb300 import hp
+
+    old = os.environ.get("HP_FORCE_CPU")
+    os.environ["HP_FORCE_CPU"] = "1"
+    try:
+        ts = []
+        with hp.Context(w.n_modules, w.gain, w.pedestal, want_labels=True) as ctx:
+            for _ in range(passes + 1):
+                t0 = time.perf_counter()
+                ev = ctx.enqueue_batch(w.words, w.modules, w.offsets)
+                assert ev.wait(600) == hp.HP_OK
+                prov = ev.provenance()
+                ev.release()
+                ts.append(time.perf_counter() - t0)
+    finally:
+        if old is None:
+            os.environ.pop("HP_FORCE_CPU", None)
+        else:
+            os.environ["HP_FORCE_CPU"] = old
+    t = statistics.median(ts[1:])
+    return {"value": w.n_events / t, "unit": "events/s", "mdigis_per_s": w.n_digis / t / 1e6,
+            "host": prov["device_name"], "path": prov["path"],
+            "what": f"hp_enqueue_batch on a CPU context (HP_FORCE_CPU), median of {passes} passes over the "
+                    f"{w.n_events}-event workload, labels on"}
+
+
 def cpu_oracle(w, events=None, threads=None):
     """Time the CPU oracle over events of w (one oracle call per event, run on
     `threads` host threads; the oracle releases the GIL)."""
@@ -406,8 +435,10 @@ def run_ours(a):
     if not a.device_only and rank == 0:
         serving = _serving_in_fresh_process(a, local)
 
-    # the CPU oracle last, after every GPU measurement: its host threads and
-    # memory churn stay out of the timed GPU and serving regions
+    # the CPU case of the library (Sec. 3) and the CPU oracle last, after
+    # every GPU measurement: their host threads and memory churn stay out of
+    # the timed GPU and serving regions
+    cpu_case = _cpu_case(w) if rank == 0 and not a.device_only else None
     cpu = None
     if rank == 0 and not a.no_cpu_baseline and not a.device_only:
         # whole passes over the workload until about 10-15 CPU-seconds of work
@@ -457,6 +488,7 @@ def run_ours(a):
             "gpu_launches": gpu_launches,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "cpu_case": cpu_case,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

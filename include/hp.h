@@ -603,7 +603,7 @@ typedef struct hp_serve_trace_record {
     uint64_t t_pooled;  /* the batch's blocks taken from the pools */
     uint64_t t_inputs;  /* its input copies queued */
     uint64_t t_kernels; /* its kernels queued */
-    /* device times (CUDA events on the batch's stream, ns from the first
+    /* device times (CUDA events on the batch's stream, ns from the earliest
      * traced batch's start; -1 if not taken): the batch's start, its inputs
      * copied, its kernels done, its outputs copied */
     int64_t gpu_start, gpu_inputs, gpu_kernels, gpu_outputs;

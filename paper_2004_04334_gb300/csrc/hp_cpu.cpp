@@ -31,6 +31,7 @@
 #include <cstring>
 #include <deque>
 #include <functional>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -73,11 +74,11 @@ struct Cluster {
 // Scratch of one worker: the module's occupancy grid (digi of each pixel,
 // or -1) and per-item arrays, reused across items.
 struct Scratch {
-    std::vector<int32_t> grid;
-    std::vector<uint32_t> touched;
-    std::vector<uint32_t> order;  // kept pixels (item digi index) in raster order
-    std::vector<int32_t> slot;    // item digi index -> position in `order`, or -1
-    std::vector<uint32_t> parent; // union-find over positions in `order`
+    std::vector<int32_t> grid;    // the module's pixels: item digi index, or -1
+    std::vector<uint32_t> lin, kpos; // per item digi: linear index; position among the kept pixels, or ~0
+    std::vector<int32_t> q;          // per item digi: calibrated charge
+    std::vector<uint64_t> keys;      // kept pixels as (linear index << 32 | item digi index), raster order
+    std::vector<uint32_t> parent;    // union-find over positions in `keys`
     std::vector<long long> sq, sr, sc;
     std::vector<int32_t> np, rank;
 };
@@ -162,12 +163,13 @@ void reconstruct(const Geometry &g, uint32_t E, const uint64_t *offsets, const u
     const uint64_t N = offsets[E];
     const uint64_t EM = (uint64_t)E * M;
     // 1: per event, validate the digis and list them by module (stable)
-    std::vector<uint32_t> item_start(EM + E); // per event M + 1 starts into `bucket`
-    std::vector<uint32_t> bucket(N);          // in-event digi indices, module by module
+    // (not zeroed up front: every entry used is written first, in parallel)
+    std::unique_ptr<uint32_t[]> item_start(new uint32_t[EM + E]); // per event M + 1 starts into `bucket`
+    std::unique_ptr<uint32_t[]> bucket(new uint32_t[N + 1]);       // in-event digi indices, module by module
     std::vector<std::atomic<int32_t>> status(E);
     pool.parallel_for(E, [&](uint64_t e, unsigned) {
         const uint64_t a = offsets[e], n = offsets[e + 1] - a;
-        uint32_t *st = item_start.data() + e * (M + 1);
+        uint32_t *st = item_start.get() + e * (M + 1);
         std::fill(st, st + M + 1, 0u);
         int32_t s = 0;
         for (uint64_t i = 0; i < n && !s; ++i) {
@@ -184,56 +186,50 @@ void reconstruct(const Geometry &g, uint32_t E, const uint64_t *offsets, const u
     // 2: per item, the clusters (kept in item order) and the labels
     std::vector<std::vector<Cluster>> found(EM);
     std::vector<Scratch> scratch(pool.size());
-    pool.parallel_for(EM, [&](uint64_t item, unsigned w) {
+    auto one_item = [&](uint64_t item, unsigned w) {
         const uint32_t e = (uint32_t)(item / M), m = (uint32_t)(item % M);
         if (status[e].load()) return;
         const uint64_t a = offsets[e];
-        const uint32_t *st = item_start.data() + (uint64_t)e * (M + 1);
-        const uint32_t *list = bucket.data() + a + st[m];
+        const uint32_t *st = item_start.get() + (uint64_t)e * (M + 1);
+        const uint32_t *list = bucket.get() + a + st[m];
         const uint32_t n = st[m + 1] - st[m];
         if (n == 0) return;
         Scratch &s = scratch[w];
         if (s.grid.size() != (size_t)R * C) s.grid.assign((size_t)R * C, -1);
-        s.touched.clear();
-        s.order.clear();
-        s.slot.assign(n, -1);
-        std::vector<int32_t> q(n);
+        s.lin.resize(n);
+        s.q.resize(n);
+        s.kpos.assign(n, ~0u);
+        s.keys.clear();
         bool dup = false;
         for (uint32_t k = 0; k < n; ++k) {
             const Decoded d = decode(words[a + list[k]], R, C);
             const uint32_t lin = d.row * C + d.col;
+            s.lin[k] = lin;
             if (s.grid[lin] >= 0) dup = true;
-            else {
-                s.grid[lin] = (int32_t)k;
-                s.touched.push_back(lin);
-            }
-            q[k] = (int32_t)d.adc * g.gain[m] - g.ped[m];
-            if (q[k] >= g.pixel_thr) s.order.push_back(k);
+            else s.grid[lin] = (int32_t)k;
+            s.q[k] = (int32_t)d.adc * g.gain[m] - g.ped[m];
+            if (s.q[k] >= g.pixel_thr) s.keys.push_back((uint64_t)lin << 32 | k);
         }
-        auto lin_of = [&](uint32_t k) {
-            const Decoded d = decode(words[a + list[k]], R, C);
-            return d.row * C + d.col;
-        };
         if (dup) {
             status[e].store(kStatusDup);
         } else {
-            std::sort(s.order.begin(), s.order.end(), [&](uint32_t x, uint32_t y) { return lin_of(x) < lin_of(y); });
-            const uint32_t P = (uint32_t)s.order.size();
+            std::sort(s.keys.begin(), s.keys.end()); // raster order
+            const uint32_t P = (uint32_t)s.keys.size();
             s.parent.resize(P);
             for (uint32_t i = 0; i < P; ++i) {
                 s.parent[i] = i;
-                s.slot[s.order[i]] = (int32_t)i;
+                s.kpos[(uint32_t)s.keys[i]] = i;
             }
             // raster pass: join each kept pixel with its kept neighbours already visited
             for (uint32_t i = 0; i < P; ++i) {
-                const uint32_t lin = lin_of(s.order[i]), r = lin / C, c = lin % C;
+                const uint32_t lin = (uint32_t)(s.keys[i] >> 32), r = lin / C, c = lin - r * C;
                 const int dr[4] = {0, -1, -1, -1}, dc[4] = {-1, -1, 0, 1};
                 for (int t = 0; t < 4; ++t) {
                     const int rr = (int)r + dr[t], cc = (int)c + dc[t];
                     if (rr < 0 || cc < 0 || cc >= (int)C) continue;
                     const int32_t k = s.grid[(uint32_t)rr * C + (uint32_t)cc];
-                    if (k < 0 || s.slot[k] < 0) continue;
-                    uint32_t x = find(s.parent, i), y = find(s.parent, (uint32_t)s.slot[k]);
+                    if (k < 0 || s.kpos[k] == ~0u) continue;
+                    uint32_t x = find(s.parent, i), y = find(s.parent, s.kpos[k]);
                     if (x == y) continue;
                     if (x < y) std::swap(x, y);
                     s.parent[x] = y; // the smaller position (smaller linear index) represents the set
@@ -245,8 +241,8 @@ void reconstruct(const Geometry &g, uint32_t E, const uint64_t *offsets, const u
             s.np.assign(P, 0);
             s.rank.assign(P, -1);
             for (uint32_t i = 0; i < P; ++i) {
-                const uint32_t root = find(s.parent, i), lin = lin_of(s.order[i]);
-                const long long qi = q[s.order[i]];
+                const uint32_t root = find(s.parent, i), lin = (uint32_t)(s.keys[i] >> 32);
+                const long long qi = s.q[(uint32_t)s.keys[i]];
                 s.sq[root] += qi;
                 s.sr[root] += qi * (long long)(lin / C);
                 s.sc[root] += qi * (long long)(lin % C);
@@ -256,17 +252,17 @@ void reconstruct(const Geometry &g, uint32_t E, const uint64_t *offsets, const u
             for (uint32_t i = 0; i < P; ++i) {
                 if (s.parent[i] != i || s.sq[i] < g.cluster_thr) continue;
                 s.rank[i] = (int32_t)out.size();
-                out.push_back({(int32_t)lin_of(s.order[i]), (int32_t)s.sq[i], s.np[i], ratio(s.sr[i], s.sq[i]),
+                out.push_back({(int32_t)(s.keys[i] >> 32), (int32_t)s.sq[i], s.np[i], ratio(s.sr[i], s.sq[i]),
                                ratio(s.sc[i], s.sq[i])});
             }
             for (uint32_t k = 0; k < n; ++k) {
                 const uint64_t at = a + list[k];
                 int32_t lab = -1;
                 uint16_t lab16 = 0xFFFFu;
-                if (s.slot[k] >= 0) {
-                    const uint32_t root = find(s.parent, (uint32_t)s.slot[k]);
+                if (s.kpos[k] != ~0u) {
+                    const uint32_t root = find(s.parent, s.kpos[k]);
                     if (s.rank[root] >= 0) {
-                        lab = (int32_t)lin_of(s.order[root]);
+                        lab = (int32_t)(s.keys[root] >> 32);
                         lab16 = (uint16_t)s.rank[root];
                     } else {
                         lab = -2;
@@ -277,8 +273,17 @@ void reconstruct(const Geometry &g, uint32_t E, const uint64_t *offsets, const u
                 if (o.label16) o.label16[at] = lab16;
             }
         }
-        for (uint32_t lin : s.touched) s.grid[lin] = -1;
-    });
+        for (uint32_t k = 0; k < n; ++k) s.grid[s.lin[k]] = -1;
+    };
+    // An event's labels interleave its modules' digis, so with enough events
+    // a worker takes whole events (no two workers write the same label
+    // lines); a few large events spread their modules over the workers.
+    if (E >= 2 * pool.size())
+        pool.parallel_for(E, [&](uint64_t e, unsigned w) {
+            for (uint32_t m = 0; m < M; ++m) one_item(e * M + m, w);
+        });
+    else
+        pool.parallel_for(EM, one_item);
 
     // 3: ordered output (a prefix over the items' cluster counts), statuses,
     // and an invalid event's labels

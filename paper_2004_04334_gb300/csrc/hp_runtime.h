@@ -349,7 +349,7 @@ struct hp_event {
     std::vector<uint64_t> cpu_offsets;
     std::vector<uint32_t> cpu_words;
     std::vector<uint16_t> cpu_mods;
-    std::vector<unsigned char> cpu_out;
+    std::unique_ptr<unsigned char[]> cpu_out; // not zeroed: the reconstruction writes every used byte
 };
 
 namespace hp {

@@ -736,14 +736,23 @@ hp_status hp_serve_trace_read(hp_ctx *ctx, hp_serve_trace_record *out, uint64_t 
             base = a[0];
             break;
         }
-    for (uint64_t i = 0; i < cap && i < ctx->trace.size(); ++i) {
-        out[i] = ctx->trace[i];
-        int64_t *g[4] = {&out[i].gpu_start, &out[i].gpu_inputs, &out[i].gpu_kernels, &out[i].gpu_outputs};
+    // times from `base`, then shifted so that the earliest traced start is 0
+    // (records are in completion order, which need not be launch order)
+    const uint64_t n_out = std::min<uint64_t>(cap, ctx->trace.size());
+    std::vector<std::array<int64_t, 4>> t(n_out);
+    int64_t t0 = INT64_MAX;
+    for (uint64_t i = 0; i < n_out; ++i)
         for (int k = 0; k < 4; ++k) {
             float ms = 0.f;
             const cudaEvent_t e = ctx->trace_ev[i][k];
-            *g[k] = base && e && cudaEventElapsedTime(&ms, base, e) == cudaSuccess ? (int64_t)(ms * 1e6) : -1;
+            const bool ok = base && e && cudaEventElapsedTime(&ms, base, e) == cudaSuccess;
+            t[i][k] = ok ? (int64_t)((double)ms * 1e6) : INT64_MIN;
+            if (ok && k == 0) t0 = std::min(t0, t[i][k]);
         }
+    for (uint64_t i = 0; i < n_out; ++i) {
+        out[i] = ctx->trace[i];
+        int64_t *g[4] = {&out[i].gpu_start, &out[i].gpu_inputs, &out[i].gpu_kernels, &out[i].gpu_outputs};
+        for (int k = 0; k < 4; ++k) *g[k] = t[i][k] == INT64_MIN ? -1 : t[i][k] - t0;
     }
     cudaGetLastError();
     return HP_OK;

@@ -1,6 +1,7 @@
-// The runtime side of the CPU case (Sec. 3, the SwitchProducer): contexts
-// that hp_create makes where no GPU is usable (no device, or HP_FORCE_CPU
-// set to anything but "0"), their job queue and the events they produce.
+// The runtime side of the CPU case (Sec. 3, the SwitchProducer): the
+// contexts hp_create makes when the caller asks for the CPU case
+// (HP_FORCE_CPU set to anything but "0", or HP_ALLOW_CPU where no device is
+// usable), their job queue and the events they produce.
 // The product is the same hp_clusters view as on the GPU, and its
 // provenance says HP_PATH_CPU and names the host, so that a consumer does
 // not depend on the choice and a reader can tell afterwards which one ran.
@@ -110,23 +111,19 @@ hp_status cpu_enqueue(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_t
         }
         // outputs: six cluster columns (capacity N), offsets, statuses, labels
         size_t off = 0;
-        size_t at[11];
-        auto take = [&](int i, size_t bytes) {
-            at[i] = off;
-            off = align_up(off + bytes, 64);
-        };
-        for (int i = 0; i < 6; ++i) take(i, 4 * N);
-        take(6, 8 * (size_t)(E + 1));
-        take(7, 4 * (size_t)E);
-        take(8, labels && !compact ? 4 * N : 0);
-        take(9, compact ? 2 * N : 0);
-        take(10, compact ? 4 * EM : 0);
-        ev->cpu_out.resize(off + 64);
+        auto take = [&](size_t bytes) { off = align_up(off + bytes, 64); };
+        for (int i = 0; i < 6; ++i) take(4 * N);
+        take(8 * (size_t)(E + 1));
+        take(4 * (size_t)E);
+        take(labels && !compact ? 4 * N : 0);
+        take(compact ? 2 * N : 0);
+        take(compact ? 4 * EM : 0);
+        ev->cpu_out.reset(new unsigned char[off + 64]); // laid out below in the same order
     } catch (...) {
         delete ev;
         return HP_ENOMEM;
     }
-    unsigned char *b = ev->cpu_out.data();
+    unsigned char *b = ev->cpu_out.get();
     size_t o = 0;
     auto next = [&](size_t bytes) {
         unsigned char *p = b + o;

@@ -186,3 +186,33 @@ def test_nocopy_serving_reads_pinned_inputs_in_place(pool):
         lat, st, _ = ctx.serve_replay(events, arrival, np.arange(100) % len(events), 4)
         assert np.all(st == 0) and np.all(lat > 0)
         ctx.serve_stop()
+
+
+def test_serving_trace_records_every_batch_in_order(pool):
+    """hp_serve_trace_*: one record per batch with its host timestamps in
+    causal order, the device marks in stream order, and the batches'
+    event counts adding up to the requests; disabling clears it."""
+    w = pool
+    with hp.Context(w.n_modules, w.gain, w.pedestal, n_streams=4) as ctx:
+        ctx.serve_start(budget_bytes=8 << 30, nocopy=False)
+        ctx.serve_trace_enable(1 << 16)
+        n = 60
+        evs = [ctx.submit(*w.event(i % w.n_events)) for i in range(n)]
+        for ev in evs:
+            assert ev.wait(120) == hp.HP_OK
+            ev.release()
+        ctx.serve_stop()
+        tr = ctx.serve_trace()
+        assert len(tr) >= 1 and int(tr["n_events"].sum()) == n
+        assert int(tr["n_digis"].sum()) == sum(len(w.event(i % w.n_events)[0]) for i in range(n))
+        order = ["t_first_submit", "t_admit", "t_pooled", "t_inputs", "t_kernels", "t_launched", "t_done_start",
+                 "t_done_end"]
+        for a, b in zip(order, order[1:]):
+            assert (tr[a].astype(np.int64) <= tr[b].astype(np.int64)).all(), (a, b)
+        marks = ["gpu_start", "gpu_inputs", "gpu_kernels", "gpu_outputs"]
+        assert (tr["gpu_start"] >= 0).all()
+        for a, b in zip(marks, marks[1:]):
+            assert (tr[a] <= tr[b]).all(), (a, b)
+        assert set(int(s) for s in tr["stream"]) <= {0, 1, 2, 3}
+        ctx.serve_trace_enable(0)
+        assert len(ctx.serve_trace()) == 0
