@@ -93,3 +93,28 @@ def test_serving_requests_carry_compact_labels(torch_cuda):
     for i, r in enumerate(results):
         e = i % w.n_events
         _check(r, w.subset([e]), [refs[e]])
+
+
+@pytest.mark.parametrize("name,n", [("occupancy", 1), ("batched", 6)])
+def test_compact_labels_in_every_tier(torch_cuda, name, n):
+    """Every clustering setting (tile sizes that push the hot modules into the
+    shared-memory tile or the global-memory tier, warp-tier limits), compact
+    labels through the host path: the same labels as the oracle."""
+    w = synth.workload(name, n_events=n)
+    refs = oracle_events(w)
+    with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
+        cands = ctx.tuning_candidates()
+        # one setting per (tile, blocks per SM, warp-tier limit): the ticket size does not change the tiers
+        seen = set()
+        for c in cands:
+            key = (c["tile_slots"], c["blocks_per_sm"], c["warp_max"])
+            if key in seen:
+                continue
+            seen.add(key)
+            ctx.set_tuning(w.n_events, w.n_digis, c)
+            ev = ctx.enqueue_batch(w.words, w.modules, w.offsets, flags=hp.HP_LABELS_U16)
+            assert ev.wait(120) == hp.HP_OK
+            r = ev.fetch()
+            ev.release()
+            _check(r, w, refs)
+        assert len(seen) >= 3
