@@ -54,6 +54,15 @@ namespace hp {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Programmatic dependent launch between the pass's kernels: each kernel lets
+// the next one launch as soon as all its own blocks are running (the next
+// kernel's blocks then take free SM slots and wait), and each dependent
+// kernel waits, before its first access to memory, until the previous grid
+// has completed and its writes are visible.  The waits are the hardware's,
+// not spins.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 constexpr uint32_t kSpinLimit = 1u << 24;          // iterations of a blocking wait, at most
 constexpr unsigned long long kWaitNs = 1000000000ull; // and at most one second of it
 
@@ -370,6 +379,7 @@ __global__ void __launch_bounds__(kHistThreads, 3) hist_kernel(const Launch L)
 {
     extern __shared__ uint32_t sh[];
     __shared__ uint32_t s_ev[2];
+    pdl_trigger();
     __shared__ uint64_t s_off[kChunkEvents + 1];
     __shared__ __align__(16) uint16_t pf_m[kChunk];
     // the event offsets must run 0 = o[0] <= o[1] <= ... <= o[E] = N (the
@@ -446,6 +456,8 @@ __global__ void __launch_bounds__(kHistThreads, 3) hist_kernel(const Launch L)
 __global__ void __launch_bounds__(256) scan_kernel(const Launch L)
 {
     __shared__ uint32_t tmp[256 / 32 + 1];
+    pdl_wait();
+    pdl_trigger();
     if (L.ws.ctl[1] & kErrBadOffsets) return;
     const uint32_t e = blockIdx.x, M = L.g.M;
     const uint64_t kb = (uint64_t)e * M;
@@ -481,6 +493,8 @@ static_assert(kChunk * (4 + 4 + 2) >= kHistCap * 4, "the staging area also holds
 __global__ void __launch_bounds__(kHistThreads, 2) scatter_kernel(const Launch L)
 {
     extern __shared__ __align__(16) uint32_t sh[];
+    pdl_wait();
+    pdl_trigger();
     uint32_t *cnt = sh;             // counts: per warp sub-histograms, or one histogram
     uint32_t *bas = sh + kHistCap;  // single-histogram mode: base of each key
     uint32_t *stage_w = sh + kHistCap;                                      // sub mode: block-local sorted words
@@ -1664,6 +1678,8 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ BlockShared bs;
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_n[kGroup], s_b[kGroup];
     __shared__ ItemRec s_rec[kGroup];
     __shared__ uint32_t s_ticket;
@@ -1812,6 +1828,8 @@ __global__ void __launch_bounds__(kOffThreads) offsets_kernel(const Launch L)
 {
     __shared__ uint32_t s_tmp[kOffThreads / 32 + 1];
     __shared__ uint32_t s_chunk;
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long s_prefix;
     const uint32_t tid = threadIdx.x, M = L.g.M;
     const uint64_t EM = (uint64_t)L.E * M;
@@ -1870,6 +1888,7 @@ constexpr int kCopyThreads = 256;
 
 __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const Launch L)
 {
+    pdl_wait();
     const uint32_t lane = threadIdx.x & 31, M = L.g.M;
     const uint64_t gt = (uint64_t)blockIdx.x * kCopyThreads + threadIdx.x;
     const bool bad_offsets = (L.ws.ctl[1] & kErrBadOffsets) != 0;
@@ -2117,6 +2136,23 @@ cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4
 const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel",    "scatter_kernel",
                                                 "cc_kernel",   "offsets_kernel", "copy_kernel"};
 
+// Launch `kern` on `stream` as a programmatic dependent of the kernel before it.
+template <typename K>
+cudaError_t launch_dependent(K kern, unsigned grid, unsigned block, size_t smem, cudaStream_t stream, const Launch &L)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, L);
+}
+
 cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *kernel_count, cudaEvent_t *marks)
 {
     NvtxRange range("hp_launch_reconstruct");
@@ -2135,25 +2171,28 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
         ++nk;
     }
     mark(1);
-    scan_kernel<<<L.E, 256, 0, stream>>>(L);
+    if (err == cudaSuccess) err = launch_dependent(scan_kernel, L.E, 256, 0, stream, L);
     ++nk;
     mark(2);
     if (L.N > 0) {
-        scatter_kernel<<<scat_grid, kHistThreads, kScatterSmem, stream>>>(L);
+        if (err == cudaSuccess) err = launch_dependent(scatter_kernel, scat_grid, kHistThreads, kScatterSmem, stream, L);
         ++nk;
     }
     mark(3);
     const size_t cc_smem = cc_smem_bytes(L.g.R, L.g.C, L.tune.tile_slots);
-    if (L.tune.blocks_per_sm >= 3)
-        cc_kernel<3><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
-    else if (L.tune.blocks_per_sm == 1)
-        cc_kernel<1><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
-    else
-        cc_kernel<2><<<L.cc_grid, kCCThreads, cc_smem, stream>>>(L);
+    if (err == cudaSuccess) {
+        if (L.tune.blocks_per_sm >= 3)
+            err = launch_dependent(cc_kernel<3>, L.cc_grid, kCCThreads, cc_smem, stream, L);
+        else if (L.tune.blocks_per_sm == 1)
+            err = launch_dependent(cc_kernel<1>, L.cc_grid, kCCThreads, cc_smem, stream, L);
+        else
+            err = launch_dependent(cc_kernel<2>, L.cc_grid, kCCThreads, cc_smem, stream, L);
+    }
     ++nk;
     mark(4);
     const uint64_t EM = (uint64_t)L.E * L.g.M;
-    offsets_kernel<<<(unsigned)((EM + kOffItems - 1) / kOffItems), kOffThreads, 0, stream>>>(L);
+    if (err == cudaSuccess)
+        err = launch_dependent(offsets_kernel, (unsigned)((EM + kOffItems - 1) / kOffItems), kOffThreads, 0, stream, L);
     ++nk;
     mark(5);
     {   // a warp per output chunk (at most copy_grid blocks, looping), and a thread per event status and offset
@@ -2161,7 +2200,7 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
         const uint64_t by_events = ((uint64_t)L.E + kCopyThreads) / kCopyThreads; // E + 1 offsets
         const uint64_t blocks =
             std::max<uint64_t>(1, std::max<uint64_t>(by_events, std::min<uint64_t>(by_items, (uint64_t)L.copy_grid)));
-        copy_kernel<<<(unsigned)blocks, kCopyThreads, 0, stream>>>(L);
+        if (err == cudaSuccess) err = launch_dependent(copy_kernel, (unsigned)blocks, kCopyThreads, 0, stream, L);
     }
     ++nk;
     mark(6);
