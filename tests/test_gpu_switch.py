@@ -55,3 +55,16 @@ def test_both_cases_give_the_same_product(torch_cuda, monkeypatch, name, n, per_
             for f in ("x", "y"):
                 d = np.abs(getattr(g, f).astype(np.float64) - getattr(c, f))
                 assert d.size == 0 or d.max() <= 1e-4, (f, d.max())
+
+
+def test_allow_cpu_still_takes_the_gpu_when_there_is_one(torch_cuda, monkeypatch):
+    """HP_ALLOW_CPU only permits the CPU case where no device is usable: on a
+    host with a GPU the context is the GPU case."""
+    monkeypatch.delenv("HP_FORCE_CPU", raising=False)
+    w = synth.workload("tiny", n_events=2)
+    with hp.Context(w.n_modules, w.gain, w.pedestal, allow_cpu=True) as ctx:
+        ev = ctx.enqueue_batch(w.words, w.modules, w.offsets)
+        assert ev.wait(60) == hp.HP_OK
+        prov = ev.provenance()
+        ev.release()
+    assert prov["path"] == "batch" and prov["device"] >= 0
