@@ -85,7 +85,8 @@ uint32_t head_count(const hp_ctx *ctx, uint64_t N)
 {
     const uint64_t expect = (N * ctx->clus_ratio.load(std::memory_order_relaxed)) >> 16;
     const uint64_t h = std::min<uint64_t>(N / 4, expect - expect / 16);
-    return (uint32_t)(h & ~(uint64_t)(hp::kOutChunk - 1));
+    // below ~100 KB of records one DMA costs more than the stores it saves
+    return h < kMinHead ? 0u : (uint32_t)(h & ~(uint64_t)(hp::kOutChunk - 1));
 }
 
 void note_clusters(hp_ctx *ctx, uint64_t clusters, uint64_t N)
@@ -499,10 +500,9 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
     }
     uint64_t nk = 0;
     if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
-    if (err == cudaSuccess && head) { // the leading clusters, by DMA (see head_count)
-        void *dst[6] = {ev->h_module, ev->h_id, ev->h_charge, ev->h_npix, ev->h_x, ev->h_y};
-        for (int i = 0; i < 6 && err == cudaSuccess; ++i)
-            err = cudaMemcpyAsync(dst[i], db + d_head[i], 4 * (size_t)head, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess && head) { // the leading clusters, by DMA (see head_count): one 2D copy of six rows
+        err = cudaMemcpy2DAsync(ev->h_module, h_arr[1] - h_arr[0], db + d_head[0], d_head[1] - d_head[0],
+                                4 * (size_t)head, 6, cudaMemcpyDeviceToHost, s);
         ctx->d2h.fetch_add(24ull * head);
     }
     if (err == cudaSuccess && labels && !keep) {

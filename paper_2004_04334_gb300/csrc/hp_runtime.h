@@ -51,6 +51,7 @@ inline uint64_t now_ns()
 // request behind it for tens of milliseconds.
 constexpr size_t kServeRatio = 256;
 constexpr size_t kAnyRatio = 0; // Pool::alloc: any cached block that fits
+constexpr uint64_t kMinHead = 4096; // fewer leading clusters than this go straight to the host (see head_count)
 inline size_t round_pow2(size_t bytes)
 {
     size_t p = 4096;

@@ -364,10 +364,9 @@ void launch_batch(hp_ctx *ctx, Serve *sv, std::vector<hp_event *> &take)
     mark(2);
     b->rec.t_kernels = now_ns();
     const uint64_t EM = (uint64_t)E * ctx->cfg.n_modules;
-    if (err == cudaSuccess && l.head) { // the leading clusters, by DMA (see head_count)
-        void *dst[6] = {b->h_module, b->h_id, b->h_charge, b->h_npix, b->h_x, b->h_y};
-        for (int i = 0; i < 6 && err == cudaSuccess; ++i)
-            err = cudaMemcpyAsync(dst[i], db + l.d_head[i], 4 * (size_t)l.head, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess && l.head) { // the leading clusters, by DMA (see head_count): one 2D copy of six rows
+        err = cudaMemcpy2DAsync(b->h_module, l.h_arr[1] - l.h_arr[0], db + l.d_head[0], l.d_head[1] - l.d_head[0],
+                                4 * (size_t)l.head, 6, cudaMemcpyDeviceToHost, s);
         ctx->d2h.fetch_add(24ull * l.head);
     }
     if (err == cudaSuccess && compact) {
