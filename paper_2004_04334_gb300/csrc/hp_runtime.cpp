@@ -492,11 +492,19 @@ hp_status enqueue_impl(hp_ctx *ctx, uint32_t E, const uint64_t *offsets, uint64_
         ctx->live.insert(ev);
     }
     uint64_t h2d = 8ull * (E + 1);
-    cudaError_t err = cudaMemcpyAsync(db + d_offs, hoffs, 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
-    if (err == cudaSuccess && N && !dev_input) {
-        err = cudaMemcpyAsync(db + d_words, src_words, 4 * N, cudaMemcpyHostToDevice, s);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(db + d_mods, src_mods, 2 * N, cudaMemcpyHostToDevice, s);
+    cudaError_t err = cudaSuccess;
+    if (!nocopy && d_words == h_words && d_mods == h_mods && d_offs == h_offs) {
+        // staged words, module ids and offsets sit at the same offsets in
+        // the pinned and the device block: one copy for all three
+        err = cudaMemcpyAsync(db, hb, h_offs + 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
         h2d += 6 * N;
+    } else {
+        err = cudaMemcpyAsync(db + d_offs, hoffs, 8 * (size_t)(E + 1), cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess && N && !dev_input) {
+            err = cudaMemcpyAsync(db + d_words, src_words, 4 * N, cudaMemcpyHostToDevice, s);
+            if (err == cudaSuccess) err = cudaMemcpyAsync(db + d_mods, src_mods, 2 * N, cudaMemcpyHostToDevice, s);
+            h2d += 6 * N;
+        }
     }
     uint64_t nk = 0;
     if (err == cudaSuccess) err = hp::launch_reconstruct(L, s, &nk, profile_marks(ctx));
