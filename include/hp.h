@@ -380,8 +380,9 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
  *                  the largest tile; 3 caps the kernel at 40 registers a
  *                  thread and needs a smaller tile);
  *   ticket_items   (event, module) items per work-queue ticket, 16, 8, 4
- *                  or 2 (halved down to 4 for launches too small to fill the
- *                  GPU);
+ *                  or 2 (halved for launches too small to fill the GPU: down
+ *                  to 4 for items of under 64 digis on average, to 1 for
+ *                  larger ones);
  *   warp_max       largest item (digis) clustered by a single warp, 32 or 64.
  * Labels and clusters are the same for every setting; only speed differs.
  * Settings are kept per shape bucket (log2 of n_events * n_modules, log2 of

@@ -45,13 +45,24 @@ struct Tuning {
     uint32_t warp_max = kWarpMax;     // 32 or 64: largest item of the warp tier
 };
 
+// Whether a launch of N digis in EM items has block-tier items on average
+// (64 digis or more an item) rather than warp-tier ones.
+__host__ __device__ inline bool large_items(uint64_t N, uint64_t EM) { return N >= 64ull * EM; }
+
 // Items per work-queue ticket of a launch of EM items on `grid` clustering
-// blocks: `gmax`, halved (down to 4) while there would be fewer than two
-// tickets per block, so that large items of small launches spread over blocks.
-__host__ __device__ inline uint32_t ticket_items(uint64_t EM, unsigned grid, uint32_t gmax)
+// blocks: `gmax`, halved while a launch would have too few tickets per
+// block.  Warp-tier items (small on average) keep at least four a ticket, so
+// that a block's warps work on several at once, and want two tickets a
+// block; block-tier items go down to one a ticket and want four a block, so
+// that a small launch's large items spread over blocks instead of queueing
+// in one ticket (one per block: the grid is sized to match, see the runtime).
+__host__ __device__ inline uint32_t ticket_items(uint64_t EM, unsigned grid, uint32_t gmax, uint64_t N)
 {
+    const bool large = large_items(N, EM);
+    const uint32_t least = large ? 1u : 4u;
+    const uint64_t want = (large ? 4ull : 2ull) * grid;
     uint32_t g = gmax;
-    while (g > 4 && (EM + g - 1) / g < 2ull * grid) g >>= 1;
+    while (g > least && (EM + g - 1) / g < want) g >>= 1;
     return g;
 }
 

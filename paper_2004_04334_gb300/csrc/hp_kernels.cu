@@ -1699,7 +1699,7 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
     uint32_t *spre = sbits + nwords;
 
     const uint64_t EM = (uint64_t)L.E * M;
-    const uint32_t G = ticket_items(EM, gridDim.x, L.tune.ticket_max);
+    const uint32_t G = ticket_items(EM, gridDim.x, L.tune.ticket_max, L.N);
     const uint64_t ngroups = (EM + G - 1) / G;
     // items of the register tier: kD digis a thread
     constexpr int kD = kMinBlocks >= 3 ? 5 : 8;

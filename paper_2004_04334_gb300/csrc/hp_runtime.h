@@ -388,7 +388,7 @@ cudaError_t device_pass(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const 
 
 // hp_tuning.cpp
 std::pair<int, int> tune_bucket(const hp_ctx *ctx, uint32_t E, uint64_t N);
-Shape shape_with(const hp_ctx *ctx, uint32_t E, const hp::Tuning &t);
+Shape shape_with(const hp_ctx *ctx, uint32_t E, uint64_t N, const hp::Tuning &t);
 Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N);
 bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t);
 std::vector<hp::Tuning> tuning_candidates(const hp_ctx *ctx);

@@ -16,12 +16,14 @@ std::pair<int, int> tune_bucket(const hp_ctx *ctx, uint32_t E, uint64_t N)
     return {63 - __builtin_clzll((unsigned long long)EM), 63 - __builtin_clzll((unsigned long long)per)};
 }
 
-Shape shape_with(const hp_ctx *ctx, uint32_t E, const hp::Tuning &t)
+Shape shape_with(const hp_ctx *ctx, uint32_t E, uint64_t N, const hp::Tuning &t)
 {
     Shape sh;
     sh.tune = t;
-    // enough blocks for tickets of the smallest size (see ticket_items)
-    const uint64_t groups = ((uint64_t)E * ctx->cfg.n_modules + 3) / 4;
+    // enough blocks for tickets of the smallest size (see ticket_items): one
+    // item for block-tier items, four for warp-tier ones
+    const uint64_t EM = (uint64_t)E * ctx->cfg.n_modules;
+    const uint64_t groups = hp::large_items(N, EM) ? EM : (EM + 3) / 4;
     const uint64_t resident = (uint64_t)ctx->sm_count * t.blocks_per_sm;
     sh.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(groups, resident));
     return sh;
@@ -65,7 +67,7 @@ Shape shape_for(hp_ctx *ctx, uint32_t E, uint64_t N)
         auto it = ctx->tune_mode != 0 ? ctx->tuned.find(b) : ctx->tuned.end();
         t = it != ctx->tuned.end() ? it->second : untuned_default(ctx, b);
     }
-    return shape_with(ctx, E, t);
+    return shape_with(ctx, E, N, t);
 }
 
 bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t)
@@ -222,7 +224,7 @@ hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const ui
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx);
     size_t need = 0;
     for (const hp::Tuning &t : cands) {
-        const Shape sh = shape_with(ctx, n_events, t);
+        const Shape sh = shape_with(ctx, n_events, n_digis, t);
         need = std::max(need, hp::carve_workspace(nullptr, n_events, ctx->cfg.n_modules, n_digis, ctx->cfg.rows,
                                                   ctx->cfg.cols, sh.grid, sh.tune, nullptr, ctx->sm_count));
     }
@@ -249,7 +251,7 @@ hp_status hp_autotune(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const ui
     size_t bi = 0;
     uint64_t nk = 0;
     for (size_t i = 0; i < cands.size(); ++i) {
-        const Shape sh = shape_with(ctx, n_events, cands[i]);
+        const Shape sh = shape_with(ctx, n_events, n_digis, cands[i]);
         cudaError_t err = device_pass(ctx, n_events, n_digis, d_offsets, d_words, d_module_ids, out, sh, ws, s, &nk,
                                       nullptr); // warm-up
         if (err == cudaSuccess) err = cudaEventRecord(e0, s);
