@@ -80,7 +80,8 @@ def _args():
     p.add_argument("--serving-only", action="store_true", help="only the serving measurement")
     p.add_argument("--e2e-depth", type=int, default=3, help="batches in flight in the end-to-end measurement")
     p.add_argument("--tuning", default="",
-                   help="tile_slots,blocks_per_sm,ticket_items,warp_max: use these clustering settings instead of "
+                   help="tile_slots,blocks_per_sm,ticket_items,warp_max[,label_store,item_threads]: use these "
+                        "clustering settings instead of "
                         "autotuning (for profiler captures of one configuration)")
     p.add_argument("--serving-inflight", type=int, default=0, help="serving batches in flight (0: library default)")
     p.add_argument("--serving-max-batch", type=int, default=0, help="events per serving batch, at most (0: library "
@@ -362,7 +363,7 @@ def run_ours(a):
     # autotuner: pick the clustering kernel's settings for this launch shape (before any
     # other pass, so that every later launch, warm-up included, runs with them)
     if a.tuning:
-        keys = ("tile_slots", "blocks_per_sm", "ticket_items", "warp_max")
+        keys = ("tile_slots", "blocks_per_sm", "ticket_items", "warp_max", "label_store", "item_threads")
         ctx.set_tuning(E, N, dict(zip(keys, (int(x) for x in a.tuning.split(",")))))
         tuning = {"chosen": ctx.get_tuning(E, N), "candidates": "not searched (--tuning)"}
     else:

@@ -167,7 +167,12 @@ typedef struct hp_tuning {
     uint32_t blocks_per_sm;
     uint32_t ticket_items;
     uint32_t warp_max;
+    uint32_t label_store;  /* HP_STORE_BITMAP or HP_STORE_HASH */
+    uint32_t item_threads; /* threads per item: 512 with the bitmap store; 128, 256 or 512 with the hash store */
 } hp_tuning;
+
+#define HP_STORE_BITMAP 0u
+#define HP_STORE_HASH 1u
 
 /* Counters of the context (monotonic unless stated). */
 typedef struct hp_stats {
@@ -383,15 +388,29 @@ hp_status hp_reconstruct_device_noalloc(hp_ctx *ctx, uint32_t n_events, uint64_t
  *                  or 2 (halved for launches too small to fill the GPU: down
  *                  to 4 for items of under 64 digis on average, to 1 for
  *                  larger ones);
- *   warp_max       largest item (digis) clustered by a single warp, 32 or 64.
+ *   warp_max       largest item (digis) clustered by a single warp, 32 or 64;
+ *   label_store    how the items above the warp tier look up a pixel's
+ *                  neighbours: HP_STORE_BITMAP,
+ *                  module-sized occupancy and survivor bitmaps with
+ *                  row-major slots, one block (512 threads) an item; or
+ *                  HP_STORE_HASH, an open-addressing table keyed by linear
+ *                  pixel index with two slots a digi, so that its memory
+ *                  follows the item's size, for items up to the hash
+ *                  store's capacity (larger ones take the bitmap tiers);
+ *   item_threads   threads clustering one item of the hash store, 128, 256
+ *                  or 512 (a block runs 512 / item_threads items side by
+ *                  side, each in its share of the block's shared memory;
+ *                  the capacity is what that share holds at 28 bytes a digi,
+ *                  at most 8 digis a thread, 5 at three blocks per SM).
  * Labels and clusters are the same for every setting; only speed differs.
  * Settings are kept per shape bucket (log2 of n_events * n_modules, log2 of
  * the mean digis per item) and used by every later launch in the bucket
  * (host, device, graph and serving paths).  A bucket without an entry takes
  * the entry of the nearest tuned bucket (distance |d items_log2| +
  * 4 |d digis_per_item_log2|, at most 8), else the defaults: 4096 slots, 2
- * blocks, 16 items, 64 digis, or, for a mean of 1024 digis per item or
- * more, the single-block tile with 4 items a ticket and 32 digis.
+ * blocks, 16 items, 64 digis, bitmap store, or, for a mean of 1024 digis
+ * per item or more, the single-block tile with 4 items a ticket and 32
+ * digis, bitmap store.
  *
  * hp_autotune times every candidate (hp_tuning_candidates) on the given
  * device-resident inputs, `reps` passes each after one warm-up, on a private

@@ -43,7 +43,40 @@ struct Tuning {
     uint32_t blocks_per_sm = 2;       // 1 (largest tile), 2 (up to 64 registers a thread) or 3 (up to 40, smaller tile)
     uint32_t ticket_max = kGroup;     // items per ticket before halving for small launches (<= kGroup)
     uint32_t warp_max = kWarpMax;     // 32 or 64: largest item of the warp tier
+    uint32_t label_store = 0;         // kStoreBitmap or kStoreHash: pixel lookup of the items above the warp tier
+    uint32_t item_threads = kCCThreads; // threads clustering one item of the hash store: 128, 256 or 512
 };
+
+// Pixel lookup of the clustering items above the warp tier: module-sized
+// occupancy and survivor bitmaps (one block an item), or an open-addressing
+// hash table keyed by linear pixel index, sized by the item's digi count
+// (item_threads threads an item, several items of a block side by side).
+constexpr uint32_t kStoreBitmap = 0;
+constexpr uint32_t kStoreHash = 1;
+// Digi index bits of the hash store's packed keys (items of at most 4096 digis).
+constexpr uint32_t kHashIdxBits = 12;
+
+// Digis a clustering thread holds in registers in the register tier and
+// the hash store: fewer at three resident blocks per SM (40 registers).
+__host__ __device__ constexpr int cc_digis_per_thread(int blocks_per_sm) { return blocks_per_sm >= 3 ? 5 : 8; }
+
+// Largest item (digis) of the hash store: each of the block's
+// kCCThreads / item_threads groups takes an equal 16-byte-aligned slice of
+// the clustering kernel's dynamic shared memory (`smem` bytes) for 28 bytes
+// a digi (accumulators, parent, two table slots) plus 256 row counters, and
+// a slice of the block's 64-bit moment scratch (2 * tile_slots entries);
+// each thread holds at most `per_thread` digis in registers.
+__host__ __device__ inline uint32_t hash_capacity(size_t smem, uint32_t tile_slots, uint32_t item_threads,
+                                                  uint32_t per_thread)
+{
+    const uint32_t groups = (uint32_t)kCCThreads / item_threads;
+    const size_t slice = (smem / groups) & ~(size_t)15;
+    size_t cap = slice > 1024 ? (slice - 1024) / 28 : 0;
+    if (cap > tile_slots / groups) cap = tile_slots / groups;
+    if (cap > (size_t)per_thread * item_threads) cap = (size_t)per_thread * item_threads;
+    if (cap > (1u << kHashIdxBits)) cap = 1u << kHashIdxBits;
+    return (uint32_t)cap;
+}
 
 // Whether a launch of N digis in EM items has block-tier items on average
 // (64 digis or more an item) rather than warp-tier ones.
@@ -183,7 +216,14 @@ __host__ __device__ inline unsigned bucket_grid(uint64_t N, int sm_count)
 // parent, padded to 8-byte multiples so every slot range stays 8-byte aligned.
 constexpr size_t kBigSlotBytes = 8 + 16 + 8 + 4 + 4;
 
-size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots);
+// Dynamic shared memory of a clustering block: the tile's slot arrays (charge,
+// count, 32-bit moments, parent: 20 bytes a slot), then the occupancy and
+// survivor bitmaps and the survivor prefix (a word each per 32 pixels).
+__host__ __device__ inline size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots)
+{
+    const size_t nwords = ((size_t)R * C + 31) / 32;
+    return (size_t)tile_slots * (8 + 8 + 4) + nwords * 4 * 3;
+}
 // Lay out the workspace for (E, M, N) in `base` (nullptr: only compute size).
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
                        const Tuning &tune, Workspace *ws, int sm_count);
@@ -191,7 +231,8 @@ size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t 
 // largest tile (slots) with which b clustering blocks stay resident per SM
 // (0 if b blocks cannot be resident), for b = 1, 2 and 3 (at most
 // kMaxTileSlots for one block, kSmemSlots otherwise); max_tile[0] unused.
-cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4]);
+// hash_tile[b] receives the same for the kernel's hash-store instance.
+cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4], uint32_t hash_tile[4]);
 // Kernels of one launch, in order; marks[i] (if given) is recorded before
 // kernel i and marks[kNumKernels] after the last one.
 constexpr int kNumKernels = 6;

@@ -1579,6 +1579,354 @@ __device__ uint32_t block_item_reg(const Launch &L, const ItemCtx &it, uint32_t 
     return K;
 }
 
+// ---------------------------------------------------------------- hash label store
+
+// The hash store (tuning label_store = kStoreHash) clusters an item with a
+// group of item_threads threads, one of the block's kCCThreads / item_threads
+// groups, each with its own slice of shared memory and its own named
+// barrier, so that several items of a ticket run side by side.  Pixel
+// lookup goes through an open-addressing table keyed by linear pixel index
+// (2n slots for n digis, linear probing) instead of module-sized bitmaps, so
+// the memory an item needs follows its digi count.  Digi j of the item (in
+// bucket order) owns entry j of the accumulator and parent arrays; the
+// union-find links packed keys (lin << kHashIdxBits | j) with atomicMin, so
+// the root of every cluster is its pixel of smallest linear index (the
+// cluster id) with no sort.  Ids are put in order at the end: kept roots are
+// counted per row, the row counts scanned, and each root ranked by column
+// among the kept roots of its own row.
+struct HashMem {
+    int2 *m;           // [cap] root: sum q*row, sum q*col (32-bit, as in the block tiers)
+    int32_t *q;        // [cap] root: charge
+    uint32_t *np;      // [cap] root: pixel count; then its ordinal (compact labels)
+    uint32_t *par;     // [cap] packed parent key; then a kept root's row base
+    uint32_t *rowcnt;  // [256] kept roots per row
+    uint32_t *table;   // [2 cap] (lin + 1) << 13 | surviving << 12 | j, 0 empty; then the row lists
+    unsigned long long *exact; // [2 cap] (global) 64-bit moments of an item with a heavy cluster
+};
+
+__device__ __forceinline__ HashMem hash_mem(unsigned char *dsm, size_t smem, uint32_t groups, uint32_t gid,
+                                            uint32_t cap, unsigned long long *exact)
+{
+    const size_t slice = (smem / groups) & ~(size_t)15;
+    HashMem h;
+    h.m = reinterpret_cast<int2 *>(dsm + slice * gid);
+    h.q = reinterpret_cast<int32_t *>(h.m + cap);
+    h.np = reinterpret_cast<uint32_t *>(h.q + cap);
+    h.par = h.np + cap;
+    h.rowcnt = h.par + cap;
+    h.table = h.rowcnt + 256;
+    h.exact = exact + (size_t)2 * cap * gid;
+    return h;
+}
+
+// Barrier of the `threads` threads of one group (named barrier `id` >= 1;
+// barrier 0 is the block's __syncthreads).  The compiler's own builtin, not
+// inline assembly: like __syncthreads it is convergent, so the compiler
+// never duplicates it into paths that a warp's threads take apart.
+__device__ __forceinline__ void group_sync(uint32_t id, uint32_t threads)
+{
+    __syncwarp();
+    __barrier_sync_count(id, threads);
+}
+
+// Home slot of pixel `lin` in a table of H slots (multiplicative hashing:
+// the high bits of lin times the 32-bit golden ratio, scaled to [0, H)).
+__device__ __forceinline__ uint32_t hash_home(uint32_t lin, uint32_t H) { return __umulhi(lin * 0x9E3779B1u, H); }
+
+// Table entry of pixel `lin` if it is there and survives the pixel
+// threshold, else 0.  The table holds at most H / 2 entries, so a probe
+// always ends at an empty slot.
+__device__ __forceinline__ uint32_t hash_survivor(const uint32_t *table, uint32_t H, uint32_t lin)
+{
+    uint32_t s = hash_home(lin, H);
+    for (uint32_t i = 0; i < H; ++i) {
+        const uint32_t e = table[s];
+        if (e == 0) return 0u;
+        if ((e >> 13) == lin + 1) return (e >> 12) & 1u ? e : 0u;
+        s = s + 1 == H ? 0u : s + 1;
+    }
+    return 0u;
+}
+
+// Packed union-find key of a table entry.
+__device__ __forceinline__ uint32_t hash_key(uint32_t e)
+{
+    return (((e >> 13) - 1u) << kHashIdxBits) | (e & ((1u << kHashIdxBits) - 1u));
+}
+
+// Find on packed keys with path halving (the index of a key is its low
+// kHashIdxBits bits); parents only ever decrease, as in uf_find_halving.
+__device__ __forceinline__ uint32_t hash_find(uint32_t *par, uint32_t x)
+{
+    constexpr uint32_t kIdx = (1u << kHashIdxBits) - 1u;
+    volatile uint32_t *p = par;
+    uint32_t y = p[x & kIdx];
+    while (y != x) {
+        const uint32_t z = p[y & kIdx];
+        if (z != y) p[x & kIdx] = z;
+        x = y;
+        y = z;
+    }
+    return x;
+}
+
+// Lock-free union of the trees of packed keys a and b (the root with the
+// larger key is linked under the smaller with atomicMin; a lost race retries
+// from the new parent), as uf_union on slots.
+__device__ __noinline__ void hash_union(uint32_t *par, uint32_t a, uint32_t b)
+{
+    for (;;) {
+        a = hash_find(par, a);
+        b = hash_find(par, b);
+        if (a == b) return;
+        if (a < b) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        const uint32_t old = atomicMin(&par[a & ((1u << kHashIdxBits) - 1u)], b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// One item of at most hash_capacity digis clustered by the calling group
+// (gt = thread index in the group, GT = its size, bar = its barrier id);
+// gflag and gheavy are the group's shared flag words (zero on entry, left
+// zero).  Thread gt holds digis gt, gt + GT, ... in registers throughout.
+// Phases, one group barrier each:
+//   0 table and row counters emptied (the words load meanwhile)
+//   1 every valid digi into the table (a pixel already there is a
+//     duplicate); parent and accumulators of the survivors
+//   2 unions with the surviving neighbours before the pixel in row-major
+//     order: left L and up U; without U, upper-left UL (unless L, which
+//     reaches UL through its own U) and upper-right UR.  With U, UL and UR
+//     are U's own left and right neighbours, so every 8-adjacency is
+//     covered with at most two unions a pixel.
+//   3 roots, and charge, size and moments per root (32-bit shared atomics;
+//     a cluster heavier than kQSafe32 sends the item through the exact
+//     64-bit pass, as in the block tiers)
+//   4 labels; kept roots counted per row
+//   5 row bases by a scan of the row counts (each warp scans all 256, eight
+//     a lane); every kept root's column into its row's list
+//   6 ordinal = row base + kept roots of the row with a smaller column;
+//     staging; (compact labels) the ordinals read back per digi
+// Returns the number of kept clusters (uniform over the group).
+template <int kD>
+__device__ uint32_t hash_item(const Launch &L, const ItemCtx &it, const HashMem &h, uint32_t gt, uint32_t GT,
+                              uint32_t bar, uint32_t *gflag, uint32_t *gheavy)
+{
+    constexpr uint32_t kIdx = (1u << kHashIdxBits) - 1u;
+    const uint32_t R = L.g.R, C = L.g.C;
+    const int32_t thr = L.g.pixel_thr, cthr = L.g.cluster_thr;
+    const uint32_t n = it.n, lane = threadIdx.x & 31, H = 2 * n;
+    const uint32_t *bw = L.ws.bucket_w + it.b;
+    const uint32_t *bi = L.ws.bucket_i + it.b;
+    const int32_t gain = it.gain, ped = it.ped;
+
+    // 0
+    for (uint32_t i = gt; i < H; i += GT) h.table[i] = 0;
+    for (uint32_t i = gt; i < 256; i += GT) h.rowcnt[i] = 0;
+    uint32_t w[kD], rt[kD];
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        const uint32_t j = gt + k * GT;
+        w[k] = j < n ? __ldg(bw + j) : 0u;
+    }
+    group_sync(bar, GT);
+
+    // 1
+    uint32_t err = 0;
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        rt[k] = kNoSlot;
+        const uint32_t j = gt + k * GT;
+        if (j >= n) continue;
+        const uint32_t x = w[k], r = x & 0xFFu, c = (x >> 8) & 0x1FFu, adc = (x >> 17) & 0xFFu;
+        if (r >= R || c >= C || adc == 0 || (x >> 25) != 0) {
+            err |= kErrBadDigi;
+            continue;
+        }
+        const uint32_t lin = r * C + c;
+        const bool surv = (int32_t)adc * gain - ped >= thr;
+        const uint32_t e = ((lin + 1) << 13) | ((uint32_t)surv << 12) | j;
+        uint32_t s = hash_home(lin, H), i = 0;
+        for (; i < H; ++i) {
+            const uint32_t old = atomicCAS(&h.table[s], 0u, e);
+            if (old == 0) break;
+            if ((old >> 13) == lin + 1) {
+                err |= kErrDup;
+                break;
+            }
+            s = s + 1 == H ? 0u : s + 1;
+        }
+        if (i == H) err |= kErrCapacity; // not reached: at most n entries in 2n slots
+        if (surv) {
+            const uint32_t key = (lin << kHashIdxBits) | j;
+            h.par[j] = key;
+            h.q[j] = 0;
+            h.np[j] = 0;
+            h.m[j] = make_int2(0, 0);
+            rt[k] = key;
+        }
+    }
+    err = __reduce_or_sync(kFull, err);
+    if (err && lane == 0) atomicOr(gflag, err);
+    group_sync(bar, GT);
+    const uint32_t flag = *(volatile uint32_t *)gflag;
+    if (flag) {
+        group_sync(bar, GT); // every thread of the group has read the flag
+        if (gt == 0) {
+            if (flag & (kErrBadDigi | kErrDup)) atomicOr(it.err_e, flag & (kErrBadDigi | kErrDup));
+            if (flag & kErrCapacity) atomicOr(&L.ws.ctl[1], kErrCapacity);
+            *gflag = 0;
+        }
+        return 0;
+    }
+
+    // 2
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        if (rt[k] == kNoSlot) continue;
+        const uint32_t x = w[k], r = x & 0xFFu, c = (x >> 8) & 0x1FFu, lin = r * C + c;
+        const uint32_t eL = c > 0 ? hash_survivor(h.table, H, lin - 1) : 0u;
+        uint32_t e1 = eL, e2 = 0;
+        if (r > 0) {
+            const uint32_t eU = hash_survivor(h.table, H, lin - C);
+            if (eU) {
+                e2 = eU;
+            } else {
+                if (!eL && c > 0) e1 = hash_survivor(h.table, H, lin - C - 1);
+                if (c + 1 < C) e2 = hash_survivor(h.table, H, lin - C + 1);
+            }
+        }
+        if (e1) hash_union(h.par, rt[k], hash_key(e1));
+        if (e2) hash_union(h.par, rt[k], hash_key(e2));
+    }
+    group_sync(bar, GT);
+
+    // 3
+    bool heavy_here = false;
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        if (rt[k] == kNoSlot) continue;
+        const uint32_t root = hash_find(h.par, rt[k]), y = root & kIdx;
+        const uint32_t x = w[k];
+        const int32_t q = (int32_t)((x >> 17) & 0xFFu) * gain - ped;
+        const int32_t old = atomicAdd(&h.q[y], q);
+        if (old + q > kQSafe32) heavy_here = true;
+        atomicAdd(&h.np[y], 1u);
+        atomicAdd(&h.m[y].x, q * (int32_t)(x & 0xFFu));
+        atomicAdd(&h.m[y].y, q * (int32_t)((x >> 8) & 0x1FFu));
+        rt[k] = root;
+    }
+    if (heavy_here) *gheavy = 1;
+    group_sync(bar, GT);
+    const bool heavy = *(volatile uint32_t *)gheavy != 0;
+    if (heavy) {
+        for (uint32_t i = gt; i < 2 * n; i += GT) h.exact[i] = 0;
+        group_sync(bar, GT);
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            if (rt[k] == kNoSlot) continue;
+            const uint32_t x = w[k], y = rt[k] & kIdx;
+            const long long q = (long long)((int32_t)((x >> 17) & 0xFFu) * gain - ped);
+            atomicAdd(&h.exact[2 * y], (unsigned long long)(q * (long long)(x & 0xFFu)));
+            atomicAdd(&h.exact[2 * y + 1], (unsigned long long)(q * (long long)((x >> 8) & 0x1FFu)));
+        }
+        group_sync(bar, GT);
+    }
+
+    // 4
+    uint32_t kr = 0; // bit k: digi k of this thread is a kept root
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        const uint32_t j = gt + k * GT;
+        if (j >= n) continue;
+        int32_t lab = -1;
+        if (rt[k] != kNoSlot) {
+            const bool kept = h.q[rt[k] & kIdx] >= cthr;
+            lab = kept ? (int32_t)(rt[k] >> kHashIdxBits) : -2;
+            const uint32_t x = w[k], r = x & 0xFFu;
+            if (kept && rt[k] == (((r * C + ((x >> 8) & 0x1FFu)) << kHashIdxBits) | j)) {
+                h.par[j] = atomicAdd(&h.rowcnt[r], 1u); // arrival in the row
+                kr |= 1u << k;
+            }
+        }
+        if (it.label_e) it.label_e[__ldg(bi + j)] = lab;
+    }
+    group_sync(bar, GT);
+    if (gt == 0) *gheavy = 0; // read by every thread before the barrier above
+
+    // 5
+    uint32_t K, base8;
+    {
+        uint32_t s8 = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s8 += h.rowcnt[lane * 8 + i];
+        uint32_t incl = s8;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        K = __shfl_sync(kFull, incl, 31);
+        base8 = incl - s8; // kept roots in the rows before this lane's eight
+    }
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        if ((uint32_t)k * GT >= n) break; // uniform over the warp
+        const uint32_t r = w[k] & 0xFFu;
+        uint32_t pre = __shfl_sync(kFull, base8, r >> 3);
+        if ((kr >> k) & 1u) {
+            const uint32_t j = gt + k * GT;
+            for (uint32_t i = r & ~7u; i < r; ++i) pre += h.rowcnt[i];
+            h.table[pre + h.par[j]] = (w[k] >> 8) & 0x1FFu;
+            h.par[j] = pre;
+        }
+    }
+    group_sync(bar, GT);
+
+    // 6
+#pragma unroll
+    for (int k = 0; k < kD; ++k) {
+        if (!((kr >> k) & 1u)) continue;
+        const uint32_t j = gt + k * GT, x = w[k], r = x & 0xFFu, c = (x >> 8) & 0x1FFu;
+        const uint32_t pre = h.par[j], end = pre + h.rowcnt[r];
+        uint32_t ord = pre;
+        for (uint32_t i = pre; i < end; ++i) ord += h.table[i] < c ? 1u : 0u;
+        const int32_t Q = h.q[j];
+        long long mr, mc;
+        if (heavy) {
+            mr = (long long)h.exact[2 * j];
+            mc = (long long)h.exact[2 * j + 1];
+        } else {
+            const int2 mm = h.m[j];
+            mr = mm.x;
+            mc = mm.y;
+        }
+        L.ws.staging.put(it.b + ord, (int32_t)(rt[k] >> kHashIdxBits), Q, (int32_t)h.np[j], centroid_abs(mr, Q),
+                         centroid_abs(mc, Q));
+        if (it.label16_e) h.np[j] = ord; // read back by the compact labels
+    }
+    if (it.label16_e) {
+        group_sync(bar, GT);
+#pragma unroll
+        for (int k = 0; k < kD; ++k) {
+            const uint32_t j = gt + k * GT;
+            if (j >= n) continue;
+            uint16_t v = kLab16Below;
+            if (rt[k] != kNoSlot) {
+                const uint32_t y = rt[k] & kIdx;
+                v = h.q[y] >= cthr ? (uint16_t)h.np[y] : kLab16Dropped;
+            }
+            it.label16_e[__ldg(bi + j)] = v;
+        }
+    }
+    group_sync(bar, GT); // the slice is free for the group's next item
+    return K;
+}
+
 // Ordered output across tickets.  chain[g] holds ticket g's aggregate (the
 // number of clusters it staged, flag bit 62), published by its owner as soon
 // as it is staged, without waiting; chain[ngroups + g] receives its inclusive
@@ -1673,7 +2021,7 @@ __device__ bool chain_resolve(unsigned long long *chain, uint32_t *frontier, uin
     }
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, bool kHash>
 __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch L)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -1701,8 +2049,19 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
     const uint64_t EM = (uint64_t)L.E * M;
     const uint32_t G = ticket_items(EM, gridDim.x, L.tune.ticket_max, L.N);
     const uint64_t ngroups = (EM + G - 1) / G;
-    // items of the register tier: kD digis a thread
-    constexpr int kD = kMinBlocks >= 3 ? 5 : 8;
+    // items of the register tier and the hash store: kD digis a thread
+    constexpr int kD = cc_digis_per_thread(kMinBlocks);
+    // hash store: items of warp_max < n <= hash_max go to groups of GT
+    // threads (0 with the bitmap store)
+    const uint32_t GT = L.tune.item_threads, hgroups = (uint32_t)kCCThreads / GT;
+    const uint32_t hash_max = kHash ? hash_capacity(cc_smem_bytes(R, C, T), T, GT, (uint32_t)kD) : 0u;
+    const uint32_t gid = tid / GT, gtid = tid - gid * GT;
+    const HashMem hm = hash_mem(dsm, cc_smem_bytes(R, C, T), hgroups, gid, hash_max, sm.exact);
+    __shared__ uint32_t s_gflag[kCCThreads / 128], s_gheavy[kCCThreads / 128];
+    if (kHash && tid < (uint32_t)(kCCThreads / 128)) {
+        s_gflag[tid] = 0;
+        s_gheavy[tid] = 0;
+    }
     if (tid == 0) {
         bs.flag = 0;
         bs.heavy = 0;
@@ -1759,9 +2118,28 @@ __global__ void __launch_bounds__(kCCThreads, kMinBlocks) cc_kernel(const Launch
                     }
                 }
                 __syncthreads();
+                if (kHash && hash_max > warp_max) {
+                    // hash store: the items above the warp tier and within
+                    // its capacity, dealt round-robin to the block's groups
+                    uint32_t nh = 0;
+                    for (int i = 0; i < kGroup; ++i) {
+                        const uint32_t n = s_n[i];
+                        if (n <= warp_max || n > hash_max) continue;
+                        if (nh++ % hgroups != gid) continue;
+                        const ItemCtx it = make_item(L, s_rec[i], s_b[i], n);
+                        const uint32_t K = hash_item<kD>(L, it, hm, gtid, GT, 1 + gid, &s_gflag[gid], &s_gheavy[gid]);
+                        if (gtid == 0) kcount[item0 + i] = K;
+                    }
+                    if (nh) { // block-uniform: the slices covered the bitmaps, which the block tier wants zeroed
+                        __syncthreads();
+                        clear_words(abits, nwords);
+                        clear_words(sbits, nwords);
+                        __syncthreads();
+                    }
+                }
                 for (int i = 0; i < kGroup; ++i) { // block tier: larger items one at a time
                     const uint32_t n = s_n[i];
-                    if (n <= warp_max) continue;
+                    if (n <= warp_max || n <= hash_max) continue;
                     const ItemCtx it = make_item(L, s_rec[i], s_b[i], n);
                     uint32_t K;
                     if (n <= (uint32_t)kD * kCCThreads && n <= T) {
@@ -2036,12 +2414,6 @@ cudaError_t launch_gather(const GatherEntry *table, uint32_t n_requests, uint64_
     return cudaGetLastError();
 }
 
-size_t cc_smem_bytes(uint32_t R, uint32_t C, uint32_t tile_slots)
-{
-    const size_t nwords = ((size_t)R * C + 31) / 32;
-    return (size_t)tile_slots * (8 + 8 + 4) + nwords * 4 * 3;
-}
-
 size_t carve_workspace(void *base, uint32_t E, uint32_t M, uint64_t N, uint32_t R, uint32_t C, int cc_grid,
                        const Tuning &tune, Workspace *ws, int sm_count)
 {
@@ -2119,18 +2491,21 @@ cudaError_t fit_tile(K kern, int device, int blocks, uint32_t R, uint32_t C, uin
 
 } // namespace
 
-cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4])
+cudaError_t init_kernels(int device, uint32_t R, uint32_t C, uint32_t max_tile[4], uint32_t hash_tile[4])
 {
     cudaError_t err = cudaSetDevice(device);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (err != cudaSuccess) return err;
-    max_tile[0] = 0;
-    err = fit_tile(cc_kernel<1>, device, 1, R, C, kMaxTileSlots, &max_tile[1]);
-    if (err != cudaSuccess) return err;
-    err = fit_tile(cc_kernel<2>, device, 2, R, C, kSmemSlots, &max_tile[2]);
-    if (err != cudaSuccess) return err;
-    return fit_tile(cc_kernel<3>, device, 3, R, C, kSmemSlots, &max_tile[3]);
+    max_tile[0] = hash_tile[0] = 0;
+    // the bitmap and hash label stores are separate instances of the kernel
+    err = fit_tile(cc_kernel<1, false>, device, 1, R, C, kMaxTileSlots, &max_tile[1]);
+    if (err == cudaSuccess) err = fit_tile(cc_kernel<1, true>, device, 1, R, C, kMaxTileSlots, &hash_tile[1]);
+    if (err == cudaSuccess) err = fit_tile(cc_kernel<2, false>, device, 2, R, C, kSmemSlots, &max_tile[2]);
+    if (err == cudaSuccess) err = fit_tile(cc_kernel<2, true>, device, 2, R, C, kSmemSlots, &hash_tile[2]);
+    if (err == cudaSuccess) err = fit_tile(cc_kernel<3, false>, device, 3, R, C, kSmemSlots, &max_tile[3]);
+    if (err == cudaSuccess) err = fit_tile(cc_kernel<3, true>, device, 3, R, C, kSmemSlots, &hash_tile[3]);
+    return err;
 }
 
 const char *const kKernelNames[kNumKernels] = {"hist_kernel", "scan_kernel",    "scatter_kernel",
@@ -2181,12 +2556,16 @@ cudaError_t launch_reconstruct(const Launch &L, cudaStream_t stream, uint64_t *k
     mark(3);
     const size_t cc_smem = cc_smem_bytes(L.g.R, L.g.C, L.tune.tile_slots);
     if (err == cudaSuccess) {
+        const bool hash = L.tune.label_store == kStoreHash;
         if (L.tune.blocks_per_sm >= 3)
-            err = launch_dependent(cc_kernel<3>, L.cc_grid, kCCThreads, cc_smem, stream, L);
+            err = launch_dependent(hash ? cc_kernel<3, true> : cc_kernel<3, false>, L.cc_grid, kCCThreads, cc_smem,
+                                   stream, L);
         else if (L.tune.blocks_per_sm == 1)
-            err = launch_dependent(cc_kernel<1>, L.cc_grid, kCCThreads, cc_smem, stream, L);
+            err = launch_dependent(hash ? cc_kernel<1, true> : cc_kernel<1, false>, L.cc_grid, kCCThreads, cc_smem,
+                                   stream, L);
         else
-            err = launch_dependent(cc_kernel<2>, L.cc_grid, kCCThreads, cc_smem, stream, L);
+            err = launch_dependent(hash ? cc_kernel<2, true> : cc_kernel<2, false>, L.cc_grid, kCCThreads, cc_smem,
+                                   stream, L);
     }
     ++nk;
     mark(4);

@@ -767,7 +767,7 @@ hp_status hp_create(const hp_config *cfg, hp_ctx **out)
     if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(HP_ECUDA);
     if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
         return bail(HP_ECUDA);
-    if (hp::init_kernels(cfg->device, cfg->rows, cfg->cols, ctx->max_tile) != cudaSuccess) return bail(HP_ECUDA);
+    if (hp::init_kernels(cfg->device, cfg->rows, cfg->cols, ctx->max_tile, ctx->hash_tile) != cudaSuccess) return bail(HP_ECUDA);
     if (ctx->max_tile[2] < (uint32_t)hp::kSmemSlots) return bail(HP_EINVAL); // the default tile must fit
     {
         cudaDeviceProp prop;

@@ -217,6 +217,7 @@ struct hp_ctx {
     int device = 0;
     int sm_count = 0;
     uint32_t max_tile[4] = {0, 0, 0, 0}; // largest tile per resident-blocks count (init_kernels)
+    uint32_t hash_tile[4] = {0, 0, 0, 0}; // the same for the hash label store's kernel instance
     char device_name[256] = {0};
     int cc_major = 0, cc_minor = 0;
     // autotuner (hp_autotune): tuning per launch-shape bucket, optional cache file

@@ -1,5 +1,6 @@
 // Autotuner of libhp's clustering kernel: launch settings (shared-memory
-// tile, resident blocks, items per ticket, warp-tier limit) per launch-shape
+// tile, resident blocks, items per ticket, warp-tier limit, bitmap or hash
+// label store and the hash store's threads per item) per launch-shape
 // bucket, chosen by timing every candidate on device-resident inputs; an
 // optional cache file; untuned buckets take the nearest tuned entry.
 #include "hp_runtime.h"
@@ -75,26 +76,40 @@ bool valid_tuning(const hp_ctx *ctx, const hp::Tuning &t)
     if (t.blocks_per_sm < 1 || t.blocks_per_sm > 3) return false;
     if (t.tile_slots < 256 || t.tile_slots > ctx->max_tile[t.blocks_per_sm] || t.tile_slots % 256) return false;
     if (t.ticket_max != 2 && t.ticket_max != 4 && t.ticket_max != 8 && t.ticket_max != 16) return false;
-    return t.warp_max == 32 || t.warp_max == 64;
+    if (t.warp_max != 32 && t.warp_max != 64) return false;
+    if (t.label_store == hp::kStoreBitmap) return t.item_threads == (uint32_t)hp::kCCThreads; // a block an item
+    if (t.label_store != hp::kStoreHash || t.tile_slots > ctx->hash_tile[t.blocks_per_sm]) return false;
+    return t.item_threads == 128 || t.item_threads == 256 || t.item_threads == 512;
 }
 
 // The autotuner's search space on this device: the default tile at two
 // resident blocks per SM, the largest tile that keeps three resident, and
-// the largest tile of a single block, each with tickets of 16, 8, 4 or 2
-// items and a warp tier up to 64 or 32 digis.
+// the largest tile of a single block, each with the bitmap label store
+// (tickets of 16, 8, 4 or 2 items, a warp tier up to 64 or 32 digis) and
+// with the hash label store at 128, 256 or 512 threads an item (tickets of
+// 16 or 4 items, a warp tier up to 64 digis).
 std::vector<hp::Tuning> tuning_candidates(const hp_ctx *ctx)
 {
     std::vector<hp::Tuning> c;
     for (uint32_t b = 1; b <= 3; ++b) {
         const uint32_t tile = b == 2 ? (uint32_t)hp::kSmemSlots : ctx->max_tile[b];
         if (tile < 256) continue;
+        hp::Tuning t;
+        t.tile_slots = tile;
+        t.blocks_per_sm = b;
         for (uint32_t tk : {16u, 8u, 4u, 2u})
             for (uint32_t wm : {64u, 32u}) {
-                hp::Tuning t;
-                t.tile_slots = tile;
-                t.blocks_per_sm = b;
                 t.ticket_max = tk;
                 t.warp_max = wm;
+                c.push_back(t);
+            }
+        if (tile > ctx->hash_tile[b]) continue; // the hash instance keeps fewer blocks resident with this tile
+        t.label_store = hp::kStoreHash;
+        t.warp_max = 64;
+        for (uint32_t it : {128u, 256u, 512u})
+            for (uint32_t tk : {16u, 4u}) {
+                t.item_threads = it;
+                t.ticket_max = tk;
                 c.push_back(t);
             }
     }
@@ -142,6 +157,9 @@ void load_tuning(hp_ctx *ctx)
         t.blocks_per_sm = (uint32_t)json_number(line, "blocks_per_sm");
         t.ticket_max = (uint32_t)json_number(line, "ticket_items");
         t.warp_max = (uint32_t)json_number(line, "warp_max");
+        const double store = json_number(line, "label_store"), threads = json_number(line, "item_threads");
+        if (store >= 0) t.label_store = (uint32_t)store;
+        if (threads >= 0) t.item_threads = (uint32_t)threads;
         const int a = (int)json_number(line, "items_log2"), b = (int)json_number(line, "digis_per_item_log2");
         if (a < 0 || b < 0 || !valid_tuning(ctx, t)) continue;
         ctx->tuned[{a, b}] = t; // later lines win
@@ -157,9 +175,9 @@ void save_tuning(hp_ctx *ctx, std::pair<int, int> bucket, const hp::Tuning &t, d
     std::fprintf(f,
                  "{\"device\": \"%s\", \"rows\": %u, \"cols\": %u, \"items_log2\": %d, "
                  "\"digis_per_item_log2\": %d, \"tile_slots\": %u, \"blocks_per_sm\": %u, \"ticket_items\": %u, "
-                 "\"warp_max\": %u, \"ms\": %.4f}\n",
+                 "\"warp_max\": %u, \"label_store\": %u, \"item_threads\": %u, \"ms\": %.4f}\n",
                  ctx->device_name, ctx->cfg.rows, ctx->cfg.cols, bucket.first, bucket.second, t.tile_slots,
-                 t.blocks_per_sm, t.ticket_max, t.warp_max, ms);
+                 t.blocks_per_sm, t.ticket_max, t.warp_max, t.label_store, t.item_threads, ms);
     std::fclose(f);
 }
 
@@ -169,6 +187,8 @@ void to_public(const hp::Tuning &t, hp_tuning *o)
     o->blocks_per_sm = t.blocks_per_sm;
     o->ticket_items = t.ticket_max;
     o->warp_max = t.warp_max;
+    o->label_store = t.label_store;
+    o->item_threads = t.item_threads;
 }
 
 } // namespace rt
@@ -206,6 +226,8 @@ hp_status hp_set_tuning(hp_ctx *ctx, uint32_t n_events, uint64_t n_digis, const 
     x.blocks_per_sm = t->blocks_per_sm;
     x.ticket_max = t->ticket_items;
     x.warp_max = t->warp_max;
+    x.label_store = t->label_store;
+    x.item_threads = t->item_threads;
     if (!valid_tuning(ctx, x)) return HP_EINVAL;
     ctx->tuned[bucket] = x;
     return HP_OK;

@@ -75,9 +75,12 @@ class Stats(ctypes.Structure):
         "serve_launch_ns", "serve_complete_ns", "serve_max_batch")]
 
 
+HP_STORE_BITMAP, HP_STORE_HASH = 0, 1
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_slots", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("ticket_items", ctypes.c_uint32),
-                ("warp_max", ctypes.c_uint32)]
+                ("warp_max", ctypes.c_uint32), ("label_store", ctypes.c_uint32), ("item_threads", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -486,7 +489,7 @@ class Context:
         """Set (dict) or clear (None) the settings of this shape's bucket; returns the status."""
         if tuning is None:
             return self._lib.hp_set_tuning(self._h, n_events, n_digis, None)
-        t = Tuning(**tuning)
+        t = Tuning(**dict({"label_store": HP_STORE_BITMAP, "item_threads": 512}, **tuning))
         return self._lib.hp_set_tuning(self._h, n_events, n_digis, ctypes.byref(t))
 
     def set_tuning(self, n_events, n_digis, tuning):

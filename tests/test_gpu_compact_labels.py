@@ -98,7 +98,8 @@ def test_serving_requests_carry_compact_labels(torch_cuda):
 @pytest.mark.parametrize("name,n", [("occupancy", 1), ("batched", 6)])
 def test_compact_labels_in_every_tier(torch_cuda, name, n):
     """Every clustering setting (tile sizes that push the hot modules into the
-    shared-memory tile or the global-memory tier, warp-tier limits), compact
+    shared-memory tile or the global-memory tier, warp-tier limits, the hash
+    label store at each group size), compact
     labels through the host path: the same labels as the oracle."""
     w = synth.workload(name, n_events=n)
     refs = oracle_events(w)
@@ -107,7 +108,7 @@ def test_compact_labels_in_every_tier(torch_cuda, name, n):
         # one setting per (tile, blocks per SM, warp-tier limit): the ticket size does not change the tiers
         seen = set()
         for c in cands:
-            key = (c["tile_slots"], c["blocks_per_sm"], c["warp_max"])
+            key = (c["tile_slots"], c["blocks_per_sm"], c["warp_max"], c["label_store"], c["item_threads"])
             if key in seen:
                 continue
             seen.add(key)

@@ -1,7 +1,9 @@
 """GPU tests of the autotuner: every candidate setting of the clustering
 kernel gives the oracle's results (on shapes that exercise the warp tier,
-the shared-memory tile and the global-memory tier), hp_autotune keeps the
-fastest per shape bucket, and the cache file round-trips across contexts."""
+the hash label store at each group size, the shared-memory tile and the
+global-memory tier), hp_autotune keeps the fastest per shape bucket, and the
+cache file round-trips across contexts."""
+import json
 import os
 
 import numpy as np
@@ -34,6 +36,8 @@ def _run(torch, ctx, w, dev):
 
 
 WORKLOADS = [("batched", 12), ("full", 2), ("occupancy", 1)]
+DEFAULT = {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 16, "warp_max": 64,
+           "label_store": hp.HP_STORE_BITMAP, "item_threads": 512}
 
 
 @pytest.mark.parametrize("name,n_events", WORKLOADS)
@@ -45,7 +49,10 @@ def test_every_candidate_matches_the_oracle(torch_cuda, name, n_events):
     with hp.Context(w.n_modules, w.gain, w.pedestal, want_labels=True) as ctx:
         cands = ctx.tuning_candidates()
         assert len(cands) >= 4
-        assert {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 16, "warp_max": 64} in cands
+        assert dict(DEFAULT) in cands
+        # both label stores, and the hash store at every group size
+        assert {(c["label_store"], c["item_threads"]) for c in cands} == \
+            {(hp.HP_STORE_BITMAP, 512), (hp.HP_STORE_HASH, 128), (hp.HP_STORE_HASH, 256), (hp.HP_STORE_HASH, 512)}
         for c in cands:
             ctx.set_tuning(w.n_events, w.n_digis, c)
             assert ctx.get_tuning(w.n_events, w.n_digis) == c
@@ -79,6 +86,14 @@ def test_autotune_keeps_the_fastest_and_results_stay_exact(torch_cuda):
         assert ctx.try_set_tuning(w.n_events, w.n_digis, bad) == hp.HP_EINVAL
         assert ctx.try_set_tuning(w.n_events, w.n_digis, dict(default, tile_slots=100)) == hp.HP_EINVAL
         assert ctx.try_set_tuning(w.n_events, w.n_digis, dict(default, warp_max=48)) == hp.HP_EINVAL
+        assert ctx.try_set_tuning(w.n_events, w.n_digis, dict(default, label_store=2)) == hp.HP_EINVAL
+        # the bitmap store takes a block an item; the hash store 128, 256 or 512 threads
+        assert ctx.try_set_tuning(w.n_events, w.n_digis,
+                                  dict(default, label_store=hp.HP_STORE_BITMAP, item_threads=256)) == hp.HP_EINVAL
+        assert ctx.try_set_tuning(w.n_events, w.n_digis,
+                                  dict(default, label_store=hp.HP_STORE_HASH, item_threads=64)) == hp.HP_EINVAL
+        assert ctx.try_set_tuning(w.n_events, w.n_digis,
+                                  dict(default, label_store=hp.HP_STORE_HASH, item_threads=256)) == hp.HP_OK
 
 
 def test_cache_file_round_trip_and_off_switch(torch_cuda, tmp_path, monkeypatch):
@@ -93,13 +108,13 @@ def test_cache_file_round_trip_and_off_switch(torch_cuda, tmp_path, monkeypatch)
                                   out, reps=1)
     lines = open(path).read().splitlines()
     assert len(lines) == 1 and '"tile_slots"' in lines[0]
+    entry = json.loads(lines[0])
+    assert {k: entry[k] for k in best} == best
     # force a non-default choice into the file so that the reload is visible
-    other = {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 8, "warp_max": 32}
+    other = {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 8, "warp_max": 64,
+             "label_store": hp.HP_STORE_HASH, "item_threads": 256}
     with open(path, "a") as f:
-        f.write(lines[0].replace('"ticket_items": %d' % best["ticket_items"], '"ticket_items": 8')
-                .replace('"warp_max": %d' % best["warp_max"], '"warp_max": 32')
-                .replace('"tile_slots": %d' % best["tile_slots"], '"tile_slots": 4096')
-                .replace('"blocks_per_sm": %d' % best["blocks_per_sm"], '"blocks_per_sm": 2') + "\n")
+        f.write(json.dumps(dict(entry, **other)) + "\n")
     with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
         assert ctx.get_tuning(w.n_events, w.n_digis) == other
     monkeypatch.setenv("HP_TUNE", "off")
@@ -117,10 +132,10 @@ def test_untuned_buckets_take_the_nearest_tuned_entry(torch_cuda):
     w = synth.workload("batched", n_events=8)
     with hp.Context(w.n_modules, w.gain, w.pedestal) as ctx:
         small = ctx.get_tuning(1, 10)  # one digi per item on average: the plain default
-        assert small == {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 16, "warp_max": 64}
+        assert small == DEFAULT
         big = ctx.get_tuning(w.n_events, w.n_digis)  # over a thousand digis per item: single-block tile
         assert big["blocks_per_sm"] == 1 and big["tile_slots"] > 4096
-        pick = {"tile_slots": 4096, "blocks_per_sm": 2, "ticket_items": 8, "warp_max": 32}
+        pick = dict(DEFAULT, ticket_items=8, warp_max=32)
         ctx.set_tuning(w.n_events, w.n_digis, pick)
         assert ctx.get_tuning(2 * w.n_events, 2 * w.n_digis) == pick  # one bucket away
         assert ctx.get_tuning(1, 10) == small  # far away: still the default
