@@ -19,7 +19,9 @@
 //                   clustered by one warp in registers, larger items by the
 //                   whole block on a shared-memory pixel bitmap with
 //                   rank-addressed union-find (items beyond the tile keep
-//                   their slot arrays in global scratch); kept clusters are
+//                   their slot arrays in global scratch), or, with the hash
+//                   label store (a tuning choice), by groups of 128-512
+//                   threads on a hash table of the item's pixels; kept clusters are
 //                   staged per item and written in (event, module, id) order
 //                   once their ticket's prefix is known (a cooperative
 //                   frontier over the tickets' cluster counts)
