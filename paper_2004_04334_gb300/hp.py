@@ -108,6 +108,13 @@ class ServeConfig(ctypes.Structure):
                 ("max_pending", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
+# hp_serve_trace_record as a numpy record
+TRACE_DTYPE = np.dtype([("t_first_submit", np.uint64), ("t_admit", np.uint64), ("t_launched", np.uint64),
+                        ("t_done_start", np.uint64), ("t_done_end", np.uint64), ("n_digis", np.uint64),
+                        ("n_events", np.uint32), ("stream", np.uint32), ("t_pooled", np.uint64),
+                        ("t_inputs", np.uint64), ("t_kernels", np.uint64), ("gpu_start", np.int64),
+                        ("gpu_inputs", np.int64), ("gpu_kernels", np.int64), ("gpu_outputs", np.int64)])
+
 CALLBACK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int)
 
 _lib = None
@@ -573,11 +580,7 @@ class Context:
 
     def serve_trace(self) -> np.ndarray:
         """The serving trace records (hp_serve_trace_read), as a structured array."""
-        dt = np.dtype([("t_first_submit", np.uint64), ("t_admit", np.uint64), ("t_launched", np.uint64),
-                       ("t_done_start", np.uint64), ("t_done_end", np.uint64), ("n_digis", np.uint64),
-                       ("n_events", np.uint32), ("stream", np.uint32), ("t_pooled", np.uint64),
-                       ("t_inputs", np.uint64), ("t_kernels", np.uint64), ("gpu_start", np.int64),
-                       ("gpu_inputs", np.int64), ("gpu_kernels", np.int64), ("gpu_outputs", np.int64)])
+        dt = TRACE_DTYPE
         n = ctypes.c_uint64()
         _check(self._lib.hp_serve_trace_read(self._h, None, 0, ctypes.byref(n)), "hp_serve_trace_read")
         out = np.zeros(n.value, dt)

@@ -106,3 +106,48 @@ def test_header_is_plain_c():
     r = subprocess.run([gcc, "-fsyntax-only", "-std=c11", "-x", "c", os.path.join(ROOT, "include", "hp.h")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+# Structures the binding mirrors: (C type in include/hp.h, binding class or
+# numpy record).
+_MIRRORS = [("hp_config", "Config"), ("hp_clusters", "ClustersView"), ("hp_device_clusters", "DeviceClusters"),
+            ("hp_stats", "Stats"), ("hp_tuning", "Tuning"), ("hp_provenance", "Provenance"), ("hp_hits", "HitsView"),
+            ("hp_serve_config", "ServeConfig"), ("hp_serve_trace_record", "TRACE_DTYPE")]
+
+
+def _binding_layout(name):
+    m = getattr(hp, name)
+    if isinstance(m, np.dtype):
+        return m.itemsize, [(f, m.fields[f][1]) for f in m.names]
+    return ctypes.sizeof(m), [(f, getattr(m, f).offset) for f, _ in m._fields_]
+
+
+def test_binding_structures_match_the_header_layout(tmp_path):
+    """Every structure the binding mirrors has the header's size and field
+    offsets, as the host C compiler lays them out (field names must match)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "hp.h"', "int main(void) {"]
+    for ctype, name in _MIRRORS:
+        _, fields = _binding_layout(name)
+        lines.append(f'printf("{name} size %zu\\n", sizeof({ctype}));')
+        for f, _ in fields:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({ctype}, {f}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for _, name in _MIRRORS:
+        size, fields = _binding_layout(name)
+        assert got[(name, "size")] == size, name
+        for f, off in fields:
+            assert got[(name, f)] == off, (name, f)
