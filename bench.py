@@ -815,14 +815,15 @@ def pretune_batches(ctx, w, local, sizes=(1, 2, 4, 8, 16, 32, 64, 128, 256), rep
     """Autotune the shape buckets that serving batches fall in: for each batch
     size, random samples of the event pool as device-resident batches (the
     settings stay in the context for every later launch of those buckets).
-    Returns the number of (size, sample) pairs tuned."""
+    Returns, per (size, sample) pair tuned, the events, digis and the chosen
+    setting (which label store, how many threads an item, tile and blocks)."""
     import torch
 
     from paper_2004_04334_gb300 import hp
 
     dev = torch.device(f"cuda:{local}")
     rng = np.random.default_rng(synth.child_seed(synth.BASE_SEED + 5, 77))
-    n = 0
+    chosen = []
     for E in sizes:
         for _ in range(reps):
             sub = w.subset(rng.integers(0, w.n_events, E))
@@ -830,10 +831,11 @@ def pretune_batches(ctx, w, local, sizes=(1, 2, 4, 8, 16, 32, 64, 128, 256), rep
             dm = torch.from_numpy(sub.modules.view(np.int16)).to(dev)
             do = torch.from_numpy(sub.offsets.view(np.int64)).to(dev)
             out = hp.DeviceOutputs(sub.n_events, sub.n_digis, dev, labels=False)
-            ctx.autotune(sub.n_events, sub.n_digis, do.data_ptr(), dw.data_ptr(), dm.data_ptr(), out, reps=2)
-            n += 1
+            best, best_ms, _ = ctx.autotune(sub.n_events, sub.n_digis, do.data_ptr(), dw.data_ptr(), dm.data_ptr(),
+                                            out, reps=2)
+            chosen.append(dict(best, events=int(sub.n_events), digis=int(sub.n_digis), ms=round(best_ms, 4)))
     torch.cuda.synchronize(dev)
-    return n
+    return chosen
 
 
 def main():
