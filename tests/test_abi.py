@@ -151,3 +151,31 @@ def test_binding_structures_match_the_header_layout(tmp_path):
         assert got[(name, "size")] == size, name
         for f, off in fields:
             assert got[(name, f)] == off, (name, f)
+
+
+def test_hash_store_capacity_formula_matches_the_kernel_header(tmp_path):
+    """The GPU tests place items at the hash store's capacity with a Python
+    copy of the formula; it must agree with hash_capacity in the kernels'
+    header for every tile, block count and group size the tuner offers."""
+    import shutil
+    import subprocess
+
+    from tests.test_gpu_hash_store import _capacity
+
+    cxx = shutil.which("g++")
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which("nvcc") or "/x/x"))),
+                            "include")
+    if not cxx or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
+        pytest.skip("no host C++ compiler or CUDA headers")
+    cases = [(t, b, it) for b, tiles in ((1, (4096, 10240)), (2, (2048, 4096)), (3, (1536, 2304, 2560)))
+             for t in tiles for it in (128, 256, 512)]
+    body = "\n".join(f'printf("%u\\n", hp::hash_capacity(hp::cc_smem_bytes(160, 416, {t}), {t}, {it}, '
+                     f'hp::cc_digis_per_thread({b})));' for t, b, it in cases)
+    src = tmp_path / "cap.cpp"
+    src.write_text('#include <cstdio>\n#include "hp_internal.h"\nint main() {\n' + body + "\nreturn 0; }\n")
+    exe = tmp_path / "cap"
+    subprocess.run([cxx, "-std=c++17", "-I", os.path.join(ROOT, "paper_2004_04334_gb300", "csrc"), "-I", cuda_inc,
+                    str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [_capacity({"tile_slots": t, "blocks_per_sm": b, "item_threads": it}) for t, b, it in cases]
+    assert got == want
